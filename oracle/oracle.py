@@ -1,0 +1,220 @@
+"""ctypes front end of the FP64 improved-QFT oracle (``qft_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline / reference legs of ``bench.py``.  The GPU library never
+imports it.
+
+Every function here marshals numpy arrays into the C oracle, which follows the
+eight recursive functions of Sec. 5 of the paper in FP64 (see the C file's
+header for the readings of the paper it takes).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qft_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_qft_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False, out: str | None = None, extra_flags=()) -> str:
+    """Compile qft_oracle.c into a shared library (gcc, OpenMP if available)."""
+    out = out or _LIB_PATH
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
+    base = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", _SRC, "-o", out, "-lm", *extra_flags]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       stdout=subprocess.PIPE, stderr=subprocess.PIPE)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True)
+    return out
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = build()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L = ctypes.c_long
+        lib.oracle_cdft.argtypes = [L, L, dp, dp, ctypes.c_int]
+        lib.oracle_icdft.argtypes = [L, L, dp, dp, ctypes.c_int]
+        lib.oracle_rdft.argtypes = [L, L, dp, dp, ctypes.c_int]
+        lib.oracle_irdft.argtypes = [L, L, dp, dp, ctypes.c_int]
+        lib.oracle_rdft_adjoint.argtypes = [L, L, dp, dp, ctypes.c_int]
+        lib.oracle_dct0.argtypes = [L, dp, dp]
+        lib.oracle_dst0.argtypes = [L, dp, dp]
+        lib.oracle_function.argtypes = [ctypes.c_int, L, dp, dp]
+        lib.oracle_counts.argtypes = [ctypes.c_int, L, ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_longlong)]
+        lib.oracle_constants_used.argtypes = [L, ctypes.POINTER(ctypes.c_ubyte),
+                                              ctypes.POINTER(ctypes.c_int)]
+        lib.oracle_constants_used.restype = L
+        lib.oracle_secant_table.argtypes = [L, dp]
+        lib.oracle_brute_dft.argtypes = [L, dp, dp]
+        lib.oracle_max_threads.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c128(x) -> np.ndarray:
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+    return x
+
+
+def _check(rc):
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def cdft(z, threads: int = 0) -> np.ndarray:
+    """Forward DFT (eq qft_0A) of each row of z [..., N] by the improved QFT."""
+    z = _c128(z)
+    N = z.shape[-1]
+    batch = z.size // N if N else 0
+    out = np.empty_like(z)
+    _check(_load().oracle_cdft(N, batch, _dp(z.view(np.float64)), _dp(out.view(np.float64)), threads))
+    return out
+
+
+def icdft(X, threads: int = 0) -> np.ndarray:
+    """Inverse DFT, 1/N scaled: swap(cdft(swap(X)))/N."""
+    X = _c128(X)
+    N = X.shape[-1]
+    out = np.empty_like(X)
+    _check(_load().oracle_icdft(N, X.size // N, _dp(X.view(np.float64)), _dp(out.view(np.float64)), threads))
+    return out
+
+
+def rdft(x, threads: int = 0) -> np.ndarray:
+    """Forward real DFT [..., N] -> [..., N/2+1] (rdft_cla of Sec. 4.2)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    N = x.shape[-1]
+    out = np.empty(x.shape[:-1] + (N // 2 + 1,), dtype=np.complex128)
+    _check(_load().oracle_rdft(N, x.size // N, _dp(x), _dp(out.view(np.float64)), threads))
+    return out
+
+
+def irdft(Y, N: int, threads: int = 0) -> np.ndarray:
+    """Inverse real DFT [..., N/2+1] -> [..., N] (1/N scaled) through DCT-0/DST-0."""
+    Y = _c128(Y)
+    assert Y.shape[-1] == N // 2 + 1
+    out = np.empty(Y.shape[:-1] + (N,), dtype=np.float64)
+    _check(_load().oracle_irdft(N, Y.size // (N // 2 + 1), _dp(Y.view(np.float64)), _dp(out), threads))
+    return out
+
+
+def rdft_adjoint(G, N: int, threads: int = 0) -> np.ndarray:
+    """Adjoint of ``rdft`` for the real inner product on (Re, Im) pairs."""
+    G = _c128(G)
+    out = np.empty(G.shape[:-1] + (N,), dtype=np.float64)
+    _check(_load().oracle_rdft_adjoint(N, G.size // (N // 2 + 1), _dp(G.view(np.float64)), _dp(out), threads))
+    return out
+
+
+def cdft_adjoint(g, threads: int = 0) -> np.ndarray:
+    """Adjoint of the forward CDFT: F^H g = conj(F conj(g))."""
+    return np.conj(cdft(np.conj(_c128(g)), threads))
+
+
+def irdft_adjoint(g, threads: int = 0) -> np.ndarray:
+    """Adjoint of ``irdft`` (1/N scaled C2R): (w_k/N) rdft(g), w = 1 at k=0,N/2, 2 elsewhere;
+    the imaginary parts at k = 0 and N/2 do not reach the output, so their gradient is 0."""
+    g = np.asarray(g, dtype=np.float64)
+    N = g.shape[-1]
+    Y = rdft(g, threads)
+    w = np.full(N // 2 + 1, 2.0 / N)
+    w[0] = w[-1] = 1.0 / N
+    Y = Y * w
+    Y[..., 0] = Y[..., 0].real
+    Y[..., -1] = Y[..., -1].real
+    return Y
+
+
+def dct0(c) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
+    N = 2 * (c.shape[-1] - 1)
+    out = np.empty_like(c)
+    _check(_load().oracle_dct0(N, _dp(c), _dp(out)))
+    return out
+
+
+def dst0(d, N: int) -> np.ndarray:
+    """DST-0 of periodization N; d indexed by n in [0, N/2] (ends ignored)."""
+    d = np.ascontiguousarray(np.asarray(d, dtype=np.float64))
+    assert d.shape[-1] == N // 2 + 1
+    out = np.empty_like(d)
+    _check(_load().oracle_dst0(N, _dp(d), _dp(out)))
+    return out
+
+
+FUNCTIONS = {"dct": 0, "dct_ot": 1, "dct_oo": 2, "dst": 3, "dst_ot": 4, "dst_oo": 5}
+
+
+def function(name: str, N: int, s) -> np.ndarray:
+    """Run one recursive function of Sec. 5 on a signal indexed by n (len N/2+1)."""
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.float64))
+    assert s.shape == (N // 2 + 1,)
+    out = np.zeros_like(s)
+    _check(_load().oracle_function(FUNCTIONS[name], N, _dp(s), _dp(out)))
+    return out
+
+
+KINDS = {"cdft": 0, "rdft": 1, "dct0": 2, "dst0": 3}
+
+
+def counts(kind: str, N: int):
+    """(adds, muls) the oracle performs for one transform of size N."""
+    a = ctypes.c_longlong()
+    m = ctypes.c_longlong()
+    _check(_load().oracle_counts(KINDS[kind], N, ctypes.byref(a), ctypes.byref(m)))
+    return int(a.value), int(m.value)
+
+
+def constants_used(N: int):
+    """(used[m] for m in [0, N/4], cos(pi/4) used?) for one CDFT of size N."""
+    used = np.zeros(N // 4 + 1, dtype=np.uint8)
+    c = ctypes.c_int()
+    cnt = _load().oracle_constants_used(N, used.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), ctypes.byref(c))
+    if cnt < 0:
+        raise ValueError("bad N")
+    return used, bool(c.value)
+
+
+def secant_table(N: int) -> np.ndarray:
+    out = np.zeros(N // 4 + 1)
+    _check(_load().oracle_secant_table(N, _dp(out)))
+    return out
+
+
+def brute_dft(z) -> np.ndarray:
+    """O(N^2) DFT of one row straight from eq qft_0A, long-double accumulation."""
+    z = _c128(z)
+    assert z.ndim == 1
+    out = np.empty_like(z)
+    _check(_load().oracle_brute_dft(z.shape[0], _dp(z.view(np.float64)), _dp(out.view(np.float64))))
+    return out
+
+
+if __name__ == "__main__":  # pragma: no cover - manual build helper
+    print(build(force="--force" in sys.argv))

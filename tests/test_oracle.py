@@ -1,0 +1,292 @@
+"""Pins of the FP64 improved-QFT oracle against what the paper and mathematics fix.
+
+The oracle must not be trusted because it agrees with itself: every check here
+compares it with something independent -- a brute-force DFT evaluated straight
+from eq qft_0A in long double, numpy's FFT, closed forms, invariants of the DFT,
+brute-force pruned definitions per signal type (Tab. 1), and the operation
+counts the paper prints (Tab. 2-5).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1301_0763_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+POW2 = [2 ** r for r in range(1, 13)]
+
+
+def rel_l2(a, b):
+    b = np.asarray(b)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - b) / (nb if nb else 1.0)
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("N", [2, 4, 8, 16, 32, 64])
+def test_cdft_vs_brute_force_small(N):
+    z = inputs.uniform_complex(3, N, seed=0).astype(np.complex128)
+    for row in z:
+        assert rel_l2(orc.cdft(row), orc.brute_dft(row)) < 1e-15 * max(1, math.log2(N))
+
+
+@pytest.mark.parametrize("N", [128, 512, 4096])
+def test_cdft_vs_brute_force_larger(N):
+    z = inputs.normal_complex(1, N, seed=7).astype(np.complex128)[0]
+    assert rel_l2(orc.cdft(z), orc.brute_dft(z)) < 2e-15 * math.log2(N)
+
+
+@pytest.mark.parametrize("N", [2 ** r for r in range(1, 17, 3)])
+def test_cdft_vs_numpy_fft(N):
+    z = inputs.normal_complex(2, N, seed=11).astype(np.complex128)
+    assert rel_l2(orc.cdft(z), np.fft.fft(z, axis=-1)) < 2e-15 * math.log2(N) + 1e-16
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("N", [8, 64, 1024])
+def test_closed_forms(N):
+    n = np.arange(N)
+    # delta -> all ones
+    d = np.zeros(N, complex); d[0] = 1
+    assert np.allclose(orc.cdft(d), np.ones(N), atol=1e-14)
+    # shifted delta -> pure phase ramp e^{-2 pi i k n0/N}
+    n0 = 3 % N
+    d = np.zeros(N, complex); d[n0] = 1
+    assert np.allclose(orc.cdft(d), np.exp(-2j * np.pi * n * n0 / N), atol=1e-13)
+    # constant -> N delta(k)
+    ref = np.zeros(N, complex); ref[0] = N
+    assert np.allclose(orc.cdft(np.ones(N, complex)), ref, atol=1e-12)
+    # complex exponential of frequency k0 -> N delta(k - k0)
+    for k0 in (1, N // 4 + 1, N - 1):
+        x = np.exp(2j * np.pi * k0 * n / N)
+        ref = np.zeros(N, complex); ref[k0 % N] = N
+        assert np.abs(orc.cdft(x) - ref).max() < 1e-11 * N
+    # real cosine -> two spikes of N/2
+    k0 = N // 8 + 1
+    X = orc.cdft(np.cos(2 * np.pi * k0 * n / N).astype(complex))
+    ref = np.zeros(N, complex); ref[k0] = N / 2; ref[N - k0] = N / 2
+    assert np.abs(X - ref).max() < 1e-11 * N
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("N", [16, 256, 4096])
+def test_parseval_linearity_hermitian(N):
+    z = inputs.normal_complex(2, N, seed=5).astype(np.complex128)
+    X = orc.cdft(z)
+    assert np.allclose((np.abs(X) ** 2).sum(axis=1), N * (np.abs(z) ** 2).sum(axis=1), rtol=1e-13)
+    a, b = 0.75 - 0.5j, -1.25 + 2j
+    assert rel_l2(orc.cdft(a * z[0] + b * z[1]), a * X[0] + b * X[1]) < 1e-14
+    x = z.real.copy()
+    Xr = orc.cdft(x.astype(complex))
+    k = np.arange(1, N)
+    assert np.allclose(Xr[:, N - k], np.conj(Xr[:, k]), atol=1e-12)
+    # rdft is the Hermitian-pruned half of the same spectrum
+    assert rel_l2(orc.rdft(x), Xr[:, : N // 2 + 1]) < 1e-14
+
+
+@pytest.mark.parametrize("N", [2, 8, 128, 4096])
+def test_inverse_round_trip(N):
+    z = inputs.normal_complex(2, N, seed=6).astype(np.complex128)
+    assert rel_l2(orc.icdft(orc.cdft(z)), z) < 1e-14
+    assert rel_l2(orc.icdft(z), np.fft.ifft(z, axis=-1)) < 1e-14
+
+
+@pytest.mark.parametrize("N", [4, 16, 512, 4096])
+def test_real_inverse(N):
+    x = inputs.normal_real(3, N, seed=8).astype(np.float64)
+    Y = orc.rdft(x)
+    assert rel_l2(orc.irdft(Y, N), x) < 1e-14
+    # independent route: numpy's irfft of a spectrum with arbitrary Im at 0, N/2
+    Y2 = Y + 0.3j
+    assert rel_l2(orc.irdft(Y2, N), np.fft.irfft(Y2, n=N, axis=-1)) < 1e-13
+
+
+def _real_inner(a, b):
+    a = np.asarray(a); b = np.asarray(b)
+    return float(np.sum(a.real * b.real) + np.sum(a.imag * b.imag))
+
+
+@pytest.mark.parametrize("N", [8, 64, 1024])
+def test_adjoint_identities(N):
+    g = inputs.rng(21)
+    x = g.standard_normal((2, N)) + 1j * g.standard_normal((2, N))
+    y = g.standard_normal((2, N)) + 1j * g.standard_normal((2, N))
+    # <F x, y> = <x, F^H y>
+    lhs = _real_inner(orc.cdft(x), y)
+    rhs = _real_inner(x, orc.cdft_adjoint(y))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs) * N
+    # R2C: <rdft(u), v> = <u, rdft^H v>
+    u = g.standard_normal((2, N))
+    v = g.standard_normal((2, N // 2 + 1)) + 1j * g.standard_normal((2, N // 2 + 1))
+    lhs = _real_inner(orc.rdft(u), v)
+    rhs = _real_inner(u, orc.rdft_adjoint(v, N))
+    assert abs(lhs - rhs) < 1e-12 * N * (abs(lhs) + 1)
+    # C2R: <irdft(v), u> = <v, irdft^H u>
+    lhs = _real_inner(orc.irdft(v, N), u)
+    rhs = _real_inner(v, orc.irdft_adjoint(u))
+    assert abs(lhs - rhs) < 1e-12 * N * (abs(lhs) + 1)
+    # ... and the adjoints match dense matrices built from eq qft_0A
+    n = np.arange(N)
+    F = np.exp(-2j * np.pi * np.outer(n, n) / N)
+    assert rel_l2(orc.cdft_adjoint(y[0]), F.conj().T @ y[0]) < 1e-12
+    Fr = F[: N // 2 + 1]
+    gx = (Fr.real.T @ v[0].real) + (Fr.imag.T @ v[0].imag)
+    assert rel_l2(orc.rdft_adjoint(v[0], N), gx) < 1e-12
+
+
+# ------------------------------------------------- per-function definitions
+def _pruned_definition(name, N):
+    """(sto_n, sto_k, kernel) of each function's signal type, Tab. 1."""
+    th = 2 * np.pi / N
+    odd_half = list(range(1, N // 2, 2))
+    odd_quarter = list(range(1, N // 4, 2))
+    table = {
+        "dct": (list(range(0, N // 2 + 1)), list(range(0, N // 2 + 1)), np.cos),
+        "dct_ot": (odd_half, list(range(0, N // 4)), np.cos),
+        "dct_oo": (odd_quarter, odd_quarter, np.cos),
+        "dst": (list(range(1, N // 2)), list(range(1, N // 2)), np.sin),
+        "dst_ot": (odd_half, list(range(1, N // 4 + 1)), np.sin),
+        "dst_oo": (odd_quarter, odd_quarter, np.sin),
+    }
+    sto_n, sto_k, f = table[name]
+    return sto_n, sto_k, (lambda s: {k: sum(s[n] * f(th * n * k) for n in sto_n) for k in sto_k})
+
+
+@pytest.mark.parametrize("name", ["dct", "dct_ot", "dct_oo", "dst", "dst_ot", "dst_oo"])
+@pytest.mark.parametrize("N", [8, 16, 32, 64, 256])
+def test_function_equals_pruned_definition(name, N):
+    """Each recursive function of Sec. 5 computes its pruned DCT-0/DST-0 over
+    Tab. 1's sto_n -> sto_k, reads nothing outside sto_n, writes nothing outside sto_k."""
+    sto_n, sto_k, defn = _pruned_definition(name, N)
+    g = inputs.rng(100 + N)
+    s = np.zeros(N // 2 + 1)
+    s[sto_n] = g.standard_normal(len(sto_n))
+    out = orc.function(name, N, s)
+    ref = defn(s)
+    for k in sto_k:
+        assert abs(out[k] - ref[k]) < 1e-13 * N, (name, N, k)
+    outside_k = [k for k in range(N // 2 + 1) if k not in sto_k]
+    assert np.all(out[outside_k] == 0)
+    # garbage outside sto_n must not change the result
+    s2 = s.copy()
+    outside_n = [n for n in range(N // 2 + 1) if n not in sto_n]
+    s2[outside_n] = 1e6
+    assert np.array_equal(orc.function(name, N, s2), out)
+    # Tab. 1: ln = card(sto_n), lk = card(sto_k), and ln = lk for every improved type
+    assert len(sto_n) == len(sto_k) or name in ("dct", "dst")
+    ln_lk = {"dct": (N // 2 + 1, N // 2 + 1), "dct_ot": (N // 4, N // 4), "dct_oo": (N // 8, N // 8),
+             "dst": (N // 2 - 1, N // 2 - 1), "dst_ot": (N // 4, N // 4), "dst_oo": (N // 8, N // 8)}
+    assert (len(sto_n), len(sto_k)) == ln_lk[name]
+
+
+def test_ln_lk_conservation():
+    """eqs qft_42/43 and 'similar relations hold for any other function' (Sec. 6.1):
+    each improved function's children carry exactly its ln and lk."""
+    for N in [2 ** r for r in range(4, 14)]:
+        ln = {"dc_tt": N // 2 + 1, "dc_ot": N // 4, "dc_oo": N // 8,
+              "ds_tt": N // 2 - 1, "ds_ot": N // 4, "ds_oo": N // 8}
+        # dct(N) -> dct(N/2) + dct_ot(N)
+        assert ln["dc_tt"] == (N // 4 + 1) + N // 4
+        # dct_ot(N) -> dct_ot(N/2) + dct_oo(N)
+        assert ln["dc_ot"] == N // 8 + ln["dc_oo"]
+        # dct_oo(N) -> dct_ot(N/2) [-> dct_ot(N/4) + dct_oo(N/2)]
+        assert ln["dc_oo"] == N // 16 + N // 16
+        # dst(N) -> dst(N/2) + dst_ot(N)
+        assert ln["ds_tt"] == (N // 4 - 1) + N // 4
+        assert ln["ds_ot"] == N // 8 + ln["ds_oo"]
+
+
+# ------------------------------------------------------------ op-count pins
+def _golden_costs():
+    rows = []
+    with open(os.path.join(HERE, "golden", "cost_tables.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(v) for v in line.split()])
+    return rows
+
+
+def test_cdft_counts_match_tables_3_4_5():
+    for (N, a_sr, a_cl, a_new, m_cl, m_new, m_sr, f_sr, f_cl, f_new) in _golden_costs():
+        adds, muls = orc.counts("cdft", N)
+        printed_adds = a_new
+        if N == 512:
+            assert printed_adds == 12290  # printed value (typo)
+            printed_adds = 12292          # Tab. 2 closed form and the SR 3/3 column
+        assert adds == printed_adds, N
+        assert muls == m_new, N
+        assert adds + muls == f_new, N
+        # Sec. 6.2: same adds, muls and flops as split-radix 3add/3mul
+        assert (adds, muls, adds + muls) == (a_sr, m_sr, f_sr), N
+
+
+@pytest.mark.parametrize("N", [2 ** r for r in range(1, 17)])
+def test_counts_match_table_2_formulas(N):
+    L = int(math.log2(N))
+    assert orc.counts("cdft", N) == (3 * N * L - 3 * N + 4, N * L - 3 * N + 4)
+    assert orc.counts("rdft", N) == (3 * N * L // 2 - 5 * N // 2 + 4, N * L // 2 - 3 * N // 2 + 2)
+    a, m = orc.counts("dct0", N)
+    assert 4 * a == 3 * N * L - 7 * N + 4 * L + 12 and 4 * m == N * L - 3 * N + 4
+    if N >= 4:
+        a, m = orc.counts("dst0", N)
+        assert 4 * a == 3 * N * L - 7 * N - 4 * L + 12 and 4 * m == N * L - 3 * N + 4
+
+
+def test_classical_counts_context():
+    """Tab. 5's classical column equals the classical closed form of Sec. 4.7 for
+    N >= 8 (the mul formula gives -1 at N = 4 where the table prints 0)."""
+    for (N, a_sr, a_cl, a_new, m_cl, m_new, m_sr, f_sr, f_cl, f_new) in _golden_costs():
+        L = int(math.log2(N))
+        if N >= 8:
+            assert 4 * m_cl == 4 * N * L - 11 * N + 8
+            assert 2 * a_cl == 7 * N * L - 8 * N
+            assert 4 * f_cl == 18 * N * L - 27 * N + 8
+
+
+# --------------------------------------------------------------- constants
+@pytest.mark.parametrize("N", [16, 64, 1024, 8192])
+def test_trig_constant_count(N):
+    """Sec. 6.1: the improved QFT uses the secants 1/(2 cos(2 pi m/N)) and the
+    base-case constant cos(pi/4).  Its generic secant multiplies use every angle
+    m in [1, N/4) except m = N/8, whose value 1/(2 cos(pi/4)) equals cos(pi/4)
+    itself; so the N/4-1 secant table entries plus cos(pi/4) that the paper
+    enumerates (N/4 constants) hold N/4-1 distinct values -- half of the N/2 of
+    split-radix 3add/3mul."""
+    used, cos_used = orc.constants_used(N)
+    angles = set(np.nonzero(used)[0].tolist())
+    assert angles == set(range(1, N // 4)) - {N // 8}
+    assert cos_used
+    table_entries = (N // 4 - 1) + 1
+    assert table_entries == N // 4
+    sec = orc.secant_table(N)
+    distinct = {float(sec[m]) for m in angles} | {math.cos(math.pi / 4)}
+    assert len(distinct) == N // 4 - 1
+    assert abs(sec[N // 8] - math.cos(math.pi / 4)) <= 2.3e-16 if N >= 16 else True
+
+
+def test_secants_rounded_from_extended_precision():
+    """Sec. 6.3: constants are evaluated above double precision and rounded once."""
+    import sympy as sp
+    N = 256
+    sec = orc.secant_table(N)
+    exact_match = 0
+    for m in range(1, N // 4):
+        v = sp.N(1 / (2 * sp.cos(2 * sp.pi * m / N)), 40)
+        ref = float(v)
+        ulp = math.ulp(ref)
+        assert abs(sec[m] - ref) <= ulp
+        exact_match += sec[m] == ref
+    assert exact_match >= (N // 4 - 1) - 2
+
+
+# ------------------------------------------------------------ accuracy metric
+def test_accuracy_metric_eq44_fp64_level():
+    """eq qft_44 on the paper's inputs (re, im uniform in (-0.5, 0.5)) against the
+    long-double brute force: the FP64 oracle sits at the 1e-16..1e-15 level."""
+    N = 1024
+    z = inputs.uniform_complex(8, N, seed=44, lo=-0.5, hi=0.5).astype(np.complex128)
+    errs = [rel_l2(orc.cdft(r), orc.brute_dft(r)) for r in z]
+    assert 1e-17 < np.mean(errs) < 3e-15
