@@ -1,0 +1,146 @@
+/*
+ * qft_gb300.h -- C ABI of the GB300 (sm_103a) improved-QFT library.
+ *
+ * The library computes batched power-of-two DFTs by the improved Quick
+ * Fourier Transform of L. Pasquini, "Improved QFT algorithm for power-of-two
+ * FFT" (arXiv 1301.0763):
+ *   - forward:  X(k) = sum_n x(n) e^{-2 pi i n k / N}  (eq qft_0A, unscaled),
+ *     computed by the recursion of Sec. 5 (cdft -> rdft -> dct/dst ->
+ *     dct_ot/dct_oo/dst_ot/dst_oo) with the constants of Sec. 6.1;
+ *   - inverse:  x = swap(DFT(swap(X))) / N (swap exchanges re and im); the
+ *     paper is silent on the inverse, this is the reading the library takes;
+ *   - backward: the exact adjoint of the forward map (the transform is linear,
+ *     so a backward pass stores nothing);
+ *   - inverse backward: the exact adjoint of the inverse map.
+ *
+ * Conventions shared by every entry point
+ *   - All data pointers are DEVICE pointers owned by the caller.  Rows are
+ *     contiguous and row-major: [batch][N] complex (interleaved re, im) for
+ *     QFT_KIND_C2C; [batch][N] real and [batch][N/2+1] complex for
+ *     QFT_KIND_R2C.  Outputs are in natural frequency (or time) order.
+ *   - Storage dtype (QFT_DTYPE_*): FP32 (complex64 / float32), FP16 or BF16
+ *     pairs (C2C only).  Arithmetic is always FP32 with round-to-nearest.
+ *   - Pointers must be aligned to their element size (8 bytes for complex64,
+ *     4 bytes otherwise); misaligned pointers return QFT_ERR_ALIGN.
+ *   - Execution is asynchronous and ordered on the CUDA stream passed as
+ *     `stream` (a cudaStream_t; NULL means the legacy default stream).  No
+ *     call synchronises the host except qft_plan_sync_status.
+ *   - C2C transforms may run in place (in == out); R2C may not.
+ *   - Every call returns QFT_OK (0) or a negative QFT_ERR_* code and never
+ *     throws.  CUDA errors are reported as QFT_ERR_CUDA; the CUDA error code is
+ *     kept in the plan (qft_plan_last_cuda_error).
+ *   - Plans are not thread-safe: one plan must not be executed concurrently
+ *     from several host threads.  Different plans are independent.
+ */
+#ifndef QFT_GB300_H
+#define QFT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qft_plan_s* qft_plan;
+
+/* transform kinds */
+#define QFT_KIND_C2C 0 /* complex -> complex, length N */
+#define QFT_KIND_R2C 1 /* forward: real N -> complex N/2+1 (Hermitian-pruned, rdft of Sec. 4.2);
+                          inverse: complex N/2+1 -> real N (1/N scaled)                      */
+
+/* storage dtypes */
+#define QFT_DTYPE_F32 0  /* complex64 (C2C) / float32 real + complex64 spectrum (R2C) */
+#define QFT_DTYPE_F16 1  /* complex stored as two IEEE half values (C2C only)          */
+#define QFT_DTYPE_BF16 2 /* complex stored as two bfloat16 values (C2C only)           */
+
+/* operations for qft_execute */
+#define QFT_OP_FORWARD 0
+#define QFT_OP_INVERSE 1
+#define QFT_OP_FORWARD_ADJOINT 2 /* = backward of the forward transform */
+#define QFT_OP_INVERSE_ADJOINT 3 /* = backward of the inverse transform */
+
+/* status codes */
+#define QFT_OK 0
+#define QFT_ERR_INVALID_N (-1)     /* N not a power of two, or outside the supported range */
+#define QFT_ERR_INVALID_BATCH (-2) /* batch < 0 or too large                                */
+#define QFT_ERR_DTYPE (-3)         /* unknown kind/dtype or unsupported combination          */
+#define QFT_ERR_ALIGN (-4)         /* data pointer not aligned to its element size           */
+#define QFT_ERR_NULLPTR (-5)       /* null plan, output handle or data pointer               */
+#define QFT_ERR_CUDA (-6)          /* a CUDA runtime call failed                             */
+#define QFT_ERR_TIMEOUT (-7)       /* a bounded device-side wait expired                     */
+#define QFT_ERR_DESTROYED (-8)     /* the plan was destroyed                                 */
+#define QFT_ERR_INVALID_ARG (-9)   /* other invalid argument (op code, ragged table, ...)    */
+#define QFT_ERR_INPLACE (-10)      /* in == out where not allowed                            */
+
+/*
+ * qft_plan_create -- plan `batch` transforms of length n (eq qft_0A with N = n).
+ *   out    receives the plan handle (owned by the caller, release with
+ *          qft_plan_destroy).
+ *   n      transform length, a power of two, 2 <= n <= 2^24 (C2C) or
+ *          4 <= n <= 2^24 (R2C).
+ *   batch  number of rows (>= 0; 0 makes every execute a no-op).
+ *   kind   QFT_KIND_C2C or QFT_KIND_R2C; dtype QFT_DTYPE_*.
+ *   flags  reserved, must be 0.
+ * The plan owns the FP32 secant table (Sec. 6.1, N/4 entries) and every
+ * scratch buffer; it allocates them here, on the current CUDA device, and
+ * frees them in qft_plan_destroy.  Executions must run on that device.
+ */
+int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype, unsigned flags);
+
+/*
+ * qft_plan_create_ragged -- plan many independent C2C transforms of uneven
+ * power-of-two lengths, executed by one persistent launch.
+ *   offsets_host  count+1 int64 entries (host memory): row i occupies complex
+ *                 elements [offsets[i], offsets[i+1]) of the packed buffer;
+ *                 offsets[0] == 0 and offsets[i+1]-offsets[i] == 2^log2n[i].
+ *   log2n_host    count int32 entries (host memory), each in [1, 24].
+ * Data layout: one packed complex buffer for input and one for output.
+ * Supported: QFT_KIND_C2C, QFT_DTYPE_F32.
+ */
+int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host, const int32_t* log2n_host,
+                           int64_t count, int kind, int dtype, unsigned flags);
+
+/*
+ * qft_execute -- run operation `op` (QFT_OP_*) of the plan on `in`, writing `out`.
+ * Shapes per op for QFT_KIND_R2C:
+ *   FORWARD:          in real [batch][N]      -> out complex [batch][N/2+1]
+ *   INVERSE:          in complex [batch][N/2+1] -> out real [batch][N] (1/N scaled;
+ *                     the imaginary parts of bins 0 and N/2 are ignored)
+ *   FORWARD_ADJOINT:  in complex [batch][N/2+1] -> out real [batch][N]
+ *                     (g_x(n) = sum_k Re g_k cos(2 pi n k/N) - Im g_k sin(2 pi n k/N))
+ *   INVERSE_ADJOINT:  in real [batch][N] -> out complex [batch][N/2+1]
+ *                     (w_k/N times the forward, w = 1 at k = 0, N/2 and 2 elsewhere,
+ *                     imaginary parts at k = 0, N/2 set to zero)
+ * For QFT_KIND_C2C every op maps [batch][N] complex to [batch][N] complex:
+ *   FORWARD = F, INVERSE = F^-1, FORWARD_ADJOINT = F^H, INVERSE_ADJOINT = F / N.
+ */
+int qft_execute(qft_plan plan, int op, const void* in, void* out, void* stream);
+
+/* Named forms of qft_execute (same arguments, same errors). */
+int qft_execute_forward(qft_plan plan, const void* in, void* out, void* stream);
+int qft_execute_inverse(qft_plan plan, const void* in, void* out, void* stream);
+int qft_execute_backward(qft_plan plan, const void* grad_out, void* grad_in, void* stream);
+
+/* Releases every resource of the plan.  Safe on NULL.  A destroyed plan must
+ * not be used again; the library detects most such uses (QFT_ERR_DESTROYED). */
+int qft_plan_destroy(qft_plan plan);
+
+/* Host-blocking: synchronises the plan's last stream and returns the plan's
+ * device status word (QFT_OK or QFT_ERR_TIMEOUT), then clears it. */
+int qft_plan_sync_status(qft_plan plan);
+
+/* Last CUDA error recorded by the plan (a cudaError_t value, 0 if none). */
+int qft_plan_last_cuda_error(qft_plan plan);
+
+/* Launch geometry chosen for the plan: threads per CTA, CTAs, dynamic shared
+ * memory bytes, and the number of kernel launches one execute issues. */
+int qft_plan_info(qft_plan plan, int* threads, int* ctas, int* smem_bytes, int* launches);
+
+/* Human-readable text of a status code (static storage). */
+const char* qft_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QFT_GB300_H */

@@ -21,8 +21,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qft_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_qft_oracle.so")
+_LIB32_PATH = os.path.join(_HERE, "_qft_oracle_f32.so")
 _lock = threading.Lock()
 _lib = None
+_lib32 = None
 
 
 def build(force: bool = False, out: str | None = None, extra_flags=()) -> str:
@@ -40,33 +42,47 @@ def build(force: bool = False, out: str | None = None, extra_flags=()) -> str:
     return out
 
 
+def _declare(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    L = ctypes.c_long
+    lib.oracle_cdft.argtypes = [L, L, dp, dp, ctypes.c_int]
+    lib.oracle_icdft.argtypes = [L, L, dp, dp, ctypes.c_int]
+    lib.oracle_rdft.argtypes = [L, L, dp, dp, ctypes.c_int]
+    lib.oracle_irdft.argtypes = [L, L, dp, dp, ctypes.c_int]
+    lib.oracle_rdft_adjoint.argtypes = [L, L, dp, dp, ctypes.c_int]
+    lib.oracle_dct0.argtypes = [L, dp, dp]
+    lib.oracle_dst0.argtypes = [L, dp, dp]
+    lib.oracle_function.argtypes = [ctypes.c_int, L, dp, dp]
+    lib.oracle_counts.argtypes = [ctypes.c_int, L, ctypes.POINTER(ctypes.c_longlong),
+                                  ctypes.POINTER(ctypes.c_longlong)]
+    lib.oracle_constants_used.argtypes = [L, ctypes.POINTER(ctypes.c_ubyte),
+                                          ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_constants_used.restype = L
+    lib.oracle_secant_table.argtypes = [L, dp]
+    lib.oracle_brute_dft.argtypes = [L, dp, dp]
+    lib.oracle_max_threads.restype = ctypes.c_int
+    lib.oracle_is_float.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
-        if _lib is not None:
-            return _lib
-        path = build()
-        lib = ctypes.CDLL(path)
-        dp = ctypes.POINTER(ctypes.c_double)
-        L = ctypes.c_long
-        lib.oracle_cdft.argtypes = [L, L, dp, dp, ctypes.c_int]
-        lib.oracle_icdft.argtypes = [L, L, dp, dp, ctypes.c_int]
-        lib.oracle_rdft.argtypes = [L, L, dp, dp, ctypes.c_int]
-        lib.oracle_irdft.argtypes = [L, L, dp, dp, ctypes.c_int]
-        lib.oracle_rdft_adjoint.argtypes = [L, L, dp, dp, ctypes.c_int]
-        lib.oracle_dct0.argtypes = [L, dp, dp]
-        lib.oracle_dst0.argtypes = [L, dp, dp]
-        lib.oracle_function.argtypes = [ctypes.c_int, L, dp, dp]
-        lib.oracle_counts.argtypes = [ctypes.c_int, L, ctypes.POINTER(ctypes.c_longlong),
-                                      ctypes.POINTER(ctypes.c_longlong)]
-        lib.oracle_constants_used.argtypes = [L, ctypes.POINTER(ctypes.c_ubyte),
-                                              ctypes.POINTER(ctypes.c_int)]
-        lib.oracle_constants_used.restype = L
-        lib.oracle_secant_table.argtypes = [L, dp]
-        lib.oracle_brute_dft.argtypes = [L, dp, dp]
-        lib.oracle_max_threads.restype = ctypes.c_int
-        _lib = lib
-        return lib
+        if _lib is None:
+            _lib = _declare(ctypes.CDLL(build()))
+        return _lib
+
+
+def _load32():
+    """The same oracle source built with every arithmetic value in FP32
+    (-DORACLE_REAL=float): the recursion of Sec. 5 evaluated in single
+    precision, operation by operation, with constants rounded once to FP32."""
+    global _lib32
+    with _lock:
+        if _lib32 is None:
+            path = build(out=_LIB32_PATH, extra_flags=("-DORACLE_REAL=float", "-ffp-contract=off"))
+            _lib32 = _declare(ctypes.CDLL(path))
+        return _lib32
 
 
 def _dp(a: np.ndarray):
@@ -87,62 +103,69 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
-def cdft(z, threads: int = 0) -> np.ndarray:
-    """Forward DFT (eq qft_0A) of each row of z [..., N] by the improved QFT."""
+def cdft(z, threads: int = 0, fp32: bool = False) -> np.ndarray:
+    """Forward DFT (eq qft_0A) of each row of z [..., N] by the improved QFT.
+    fp32=True evaluates the same recursion in single precision."""
     z = _c128(z)
     N = z.shape[-1]
     batch = z.size // N if N else 0
     out = np.empty_like(z)
-    _check(_load().oracle_cdft(N, batch, _dp(z.view(np.float64)), _dp(out.view(np.float64)), threads))
+    lib = _load32() if fp32 else _load()
+    _check(lib.oracle_cdft(N, batch, _dp(z.view(np.float64)), _dp(out.view(np.float64)), threads))
     return out
 
 
-def icdft(X, threads: int = 0) -> np.ndarray:
+def icdft(X, threads: int = 0, fp32: bool = False) -> np.ndarray:
     """Inverse DFT, 1/N scaled: swap(cdft(swap(X)))/N."""
     X = _c128(X)
     N = X.shape[-1]
     out = np.empty_like(X)
-    _check(_load().oracle_icdft(N, X.size // N, _dp(X.view(np.float64)), _dp(out.view(np.float64)), threads))
+    lib = _load32() if fp32 else _load()
+    _check(lib.oracle_icdft(N, X.size // N, _dp(X.view(np.float64)), _dp(out.view(np.float64)), threads))
     return out
 
 
-def rdft(x, threads: int = 0) -> np.ndarray:
+def rdft(x, threads: int = 0, fp32: bool = False) -> np.ndarray:
     """Forward real DFT [..., N] -> [..., N/2+1] (rdft_cla of Sec. 4.2)."""
     x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
     N = x.shape[-1]
     out = np.empty(x.shape[:-1] + (N // 2 + 1,), dtype=np.complex128)
-    _check(_load().oracle_rdft(N, x.size // N, _dp(x), _dp(out.view(np.float64)), threads))
+    lib = _load32() if fp32 else _load()
+    _check(lib.oracle_rdft(N, x.size // N, _dp(x), _dp(out.view(np.float64)), threads))
     return out
 
 
-def irdft(Y, N: int, threads: int = 0) -> np.ndarray:
+def irdft(Y, N: int, threads: int = 0, fp32: bool = False) -> np.ndarray:
     """Inverse real DFT [..., N/2+1] -> [..., N] (1/N scaled) through DCT-0/DST-0."""
     Y = _c128(Y)
     assert Y.shape[-1] == N // 2 + 1
     out = np.empty(Y.shape[:-1] + (N,), dtype=np.float64)
-    _check(_load().oracle_irdft(N, Y.size // (N // 2 + 1), _dp(Y.view(np.float64)), _dp(out), threads))
+    lib = _load32() if fp32 else _load()
+    _check(lib.oracle_irdft(N, Y.size // (N // 2 + 1), _dp(Y.view(np.float64)), _dp(out), threads))
     return out
 
 
-def rdft_adjoint(G, N: int, threads: int = 0) -> np.ndarray:
+def rdft_adjoint(G, N: int, threads: int = 0, fp32: bool = False) -> np.ndarray:
     """Adjoint of ``rdft`` for the real inner product on (Re, Im) pairs."""
     G = _c128(G)
     out = np.empty(G.shape[:-1] + (N,), dtype=np.float64)
-    _check(_load().oracle_rdft_adjoint(N, G.size // (N // 2 + 1), _dp(G.view(np.float64)), _dp(out), threads))
+    lib = _load32() if fp32 else _load()
+    _check(lib.oracle_rdft_adjoint(N, G.size // (N // 2 + 1), _dp(G.view(np.float64)), _dp(out), threads))
     return out
 
 
-def cdft_adjoint(g, threads: int = 0) -> np.ndarray:
+def cdft_adjoint(g, threads: int = 0, fp32: bool = False) -> np.ndarray:
     """Adjoint of the forward CDFT: F^H g = conj(F conj(g))."""
-    return np.conj(cdft(np.conj(_c128(g)), threads))
+    return np.conj(cdft(np.conj(_c128(g)), threads, fp32=fp32))
 
 
-def irdft_adjoint(g, threads: int = 0) -> np.ndarray:
+def irdft_adjoint(g, threads: int = 0, fp32: bool = False) -> np.ndarray:
     """Adjoint of ``irdft`` (1/N scaled C2R): (w_k/N) rdft(g), w = 1 at k=0,N/2, 2 elsewhere;
-    the imaginary parts at k = 0 and N/2 do not reach the output, so their gradient is 0."""
+    the imaginary parts at k = 0 and N/2 do not reach the output, so their gradient is 0.
+    With fp32=True the spectrum and the (power-of-two) weights are applied in FP32."""
     g = np.asarray(g, dtype=np.float64)
     N = g.shape[-1]
-    Y = rdft(g, threads)
+    Y = rdft(g, threads, fp32=fp32)
     w = np.full(N // 2 + 1, 2.0 / N)
     w[0] = w[-1] = 1.0 / N
     Y = Y * w

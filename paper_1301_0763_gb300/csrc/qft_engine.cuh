@@ -1,0 +1,499 @@
+// qft_engine.cuh -- the improved-QFT row engine (Pasquini, "Improved QFT
+// algorithm for power-of-two FFT", Sec. 3-5), written once for the sm_103a
+// kernels and, with QFT_HOST_EMULATION, for a host build used only by the
+// test-suite to check the engine's index logic without a GPU.
+//
+// Data layout of one row (N = 2^r, r >= 2) in shared memory
+// ----------------------------------------------------------
+// The CDFT is split (Sec. 4.1/4.2; complex data pushed through the
+// real-coefficient network, re and im lanes together) into
+//   c(n) = z(n) + z(N-n)  (s_dc_tt, n in [0, N/2]) and
+//   d(n) = z(n) - z(N-n)  (s_ds_tt, n in [1, N/2-1]).
+// dct and dst first separate even from odd time indices (Sec. 3.1) and halve
+// the even ones (Sec. 3.4), recursively; unrolled, this partitions the time
+// indices by their 2-adic valuation: class j holds n = 2^j * (2c+1),
+// c in [0, P_j), P_j = N / 2^(j+2), and is one dct_ot / dst_ot of
+// periodization N / 2^j.  DCT classes are j = 0..r-2, DST classes j = 0..r-3.
+// Each side (DCT, DST) is one array of N/2+1 complex cells:
+//   class j occupies [N/2 - 2^(r-1-j), N/2 - 2^(r-2-j)),
+//   DCT: c(0) at N/2-1, c(N/2) at N/2;  DST: d(N/4) (the dst(4) base) at N/2-2.
+// Shared-memory addresses are padded by one cell every 16 (qft_pidx) so that
+// strided task accesses do not collide on banks.
+//
+// Forward phase of a class (Sec. 3.2 + 3.3, eqs qft_1, qft_2, qft_9, qft_10,
+// and the secant conversion of dct_oo / dst_oo, eq qft_38A): a node of
+// 2^b cells (own time index n = 2c+1, periodization M = 2^(b+2)) splits by
+// the mirror butterfly s(n) +- s(M/2-n) into its even-harmonic child (a
+// dct_ot / dst_ot of periodization M/2) and its odd-harmonic child, which is
+// scaled by 1/(2cos(2 pi n/M)) and is then also a dct_ot / dst_ot of
+// periodization M/2.  Cells are stored in Gray order: slot g holds own cell
+// invgray(g).  In that order the mirror partner of a cell differs only in the
+// node's top slot bit, the even-harmonic child keeps the lower half, the
+// odd-harmonic child the upper half, and both children are again in their own
+// Gray order -- so the whole forward phase is an in-place radix-2 network.
+//
+// Backward phase (eqs qft_4B, qft_38B (read as X(M/4-1) = Y(M/8-1)),
+// qft_38C): outputs are kept in natural frequency order per node; a node's
+// output interleaves E (even harmonics) with Y(j) + Y(j+1) (odd harmonics,
+// DCT) or Z(j-1) + Z(j) (DST, stored at k-1).
+//
+// Final phase (eqs qft_5C, qft_5D, qft_6 and their DST forms; Sec. 4.1):
+// C_M(k) = C_{M/2}(k) + O(k), C_M(M/2-k) = C_{M/2}(k) - O(k), C_M(M/4) =
+// C_{M/2}(M/4); S_M(k) = S_{M/2}(k) + O(k), S_M(M/2-k) = O(k) - S_{M/2}(k),
+// S_M(M/4) = O(M/4); X(k) = C(k) - i S(k), X(N-k) = C(k) + i S(k).
+//
+// Every arithmetic operation is a single round-to-nearest fp32 operation on
+// each lane (never contracted into an FMA), and the operands of every
+// operation are exactly the ones the recursion of Sec. 5 prescribes, so the
+// engine's result does not depend on the order in which tasks run.
+#pragma once
+
+#include <stdint.h>
+#include "qft_plan.h"
+
+#if defined(__CUDACC__) && !defined(QFT_HOST_EMULATION)
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#define QFT_HD __host__ __device__ __forceinline__
+typedef float2 qc;
+#else
+#include <string.h>
+#define QFT_HD inline
+struct qc { float x, y; };
+#endif
+
+namespace qft {
+
+// ------------------------------------------------------------ arithmetic
+QFT_HD qc mkc(float x, float y) { qc r; r.x = x; r.y = y; return r; }
+
+#if defined(__CUDA_ARCH__)
+QFT_HD qc cadd(qc a, qc b) {
+  qc r;
+  asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\t"
+      "add.rn.f32x2 rc, ra, rb;\n\tmov.b64 {%0,%1}, rc;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+QFT_HD qc csub(qc a, qc b) {
+  qc r;
+  asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\t"
+      "sub.rn.f32x2 rc, ra, rb;\n\tmov.b64 {%0,%1}, rc;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+QFT_HD qc cmul(qc a, float s) {
+  qc r;
+  asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%4};\n\t"
+      "mul.rn.f32x2 rc, ra, rb;\n\tmov.b64 {%0,%1}, rc;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(s));
+  return r;
+}
+QFT_HD float fmul(float a, float b) { return __fmul_rn(a, b); }
+QFT_HD float fadd(float a, float b) { return __fadd_rn(a, b); }
+QFT_HD float fsub(float a, float b) { return __fsub_rn(a, b); }
+#else
+// host emulation: plain IEEE single precision (built with -ffp-contract=off)
+QFT_HD qc cadd(qc a, qc b) { return mkc(a.x + b.x, a.y + b.y); }
+QFT_HD qc csub(qc a, qc b) { return mkc(a.x - b.x, a.y - b.y); }
+QFT_HD qc cmul(qc a, float s) { return mkc(a.x * s, a.y * s); }
+QFT_HD float fmul(float a, float b) { return a * b; }
+QFT_HD float fadd(float a, float b) { return a + b; }
+QFT_HD float fsub(float a, float b) { return a - b; }
+#endif
+
+// ------------------------------------------------------------ geometry
+QFT_HD int qft_pidx(int i) { return i + (i >> 4); }
+QFT_HD int qft_side_len(int N) { return qft_pidx(N / 2) + 1; }   // padded cells per side
+QFT_HD int cls_off(int r, int j) { return (1 << (r - 1)) - (1 << (r - 1 - j)); }
+QFT_HD int cls_bits(int r, int j) { return r - 2 - j; }
+QFT_HD unsigned invgray(unsigned g) {
+  g ^= g >> 1; g ^= g >> 2; g ^= g >> 4; g ^= g >> 8; g ^= g >> 16;
+  return g;
+}
+#if defined(__CUDACC__) && !defined(QFT_HOST_EMULATION)
+__host__ __device__ constexpr int ig_c(int x) { return x ^ (x >> 1) ^ (x >> 2) ^ (x >> 3) ^ (x >> 4) ^ (x >> 5); }
+#else
+static constexpr int ig_c(int x) { return x ^ (x >> 1) ^ (x >> 2) ^ (x >> 3) ^ (x >> 4) ^ (x >> 5); }
+#endif
+
+// Everything a phase needs about the row being transformed.
+struct Eng {
+  qc* side0;          // DCT side (padded), N/2+1 cells
+  qc* side1;          // DST side (padded)
+  const float* sec;   // sec[m] = 1/(2 cos(2 pi m / N)), m in [1, N/4)
+  int r;              // log2 N
+  int N;
+};
+
+QFT_HD qc* side_ptr(const Eng& e, int s) { return s ? e.side1 : e.side0; }
+
+// ------------------------------------------------- forward mirror levels
+// L levels of the forward phase on registers v[t], t in [0, 2^L).  Register t
+// holds node slot t*H + lo (H = 2^(nb-L)) of a node of 2^nb cells; ilo is
+// invgray(lo).  Level l pairs t and t + 2^(L-l); the lower element is own
+// cell c of the current node (2^bp cells, bp = nb-l+1), whose periodization
+// is 2^(bp+2), so its secant is sec[(2c+1) << (r-bp-2)].
+// DCT (eqs qft_1, qft_2): e = a + b, o = (a - b) sec.
+// DST (roles swapped, Sec. 3.2): e = a - b, o = (a + b) sec.
+template <int L, int SIDE>
+QFT_HD void dif_regs(qc (&v)[1 << L], int nb, int ilo, const float* sec, int r) {
+  const int h = nb - L;
+  const int H = 1 << h;
+#pragma unroll
+  for (int l = 1; l <= L; ++l) {
+    const int half = 1 << (L - l);
+    const int bp = nb - l + 1;
+    const int sh = r - bp - 2;
+#pragma unroll
+    for (int t = 0; t < (1 << L); ++t) {
+      if (t & half) continue;
+      const int hi = t & (half - 1);
+      const int ig = ig_c(hi);
+      const int cl = (ig << h) | ((ig & 1) ? (H - 1 - ilo) : ilo);
+      const float s = sec[(2 * cl + 1) << sh];
+      const qc a = v[t], b = v[t | half];
+      if (SIDE == 0) { v[t] = cadd(a, b); v[t | half] = cmul(csub(a, b), s); }
+      else           { v[t] = csub(a, b); v[t | half] = cmul(cadd(a, b), s); }
+    }
+  }
+}
+
+// ------------------------------------------------------ backward levels
+// Backward phase of L tree levels on w[t] (t = path of a depth-L descendant,
+// MSB first, 0 = even-harmonic child, 1 = odd-harmonic child).  On entry w[t]
+// holds one frequency value of descendant t (the chunk of this task); on exit
+// w holds 2^L consecutive outputs of the top node.  h[t] (t >= 1) is the
+// neighbouring value of descendant t (next chunk for DCT, previous chunk for
+// DST) used at a chunk edge when hv is true; at a node edge hv is false.
+// DCT (dct_ot, eqs qft_4B, qft_38B, qft_38C): X(2i) = E(i),
+//   X(2i+1) = Y(i) + Y(i+1), last X(B-1) = Y(B/2-1).
+// DST (dst_ot, outputs k = 1..B stored at k-1): X(2i+1) = E(i), X(0) = Z(0),
+//   X(2i) = Z(i-1) + Z(i).
+template <int L, int SIDE>
+QFT_HD void bwd_chunk(qc (&w)[1 << L], const qc* h, bool hv) {
+#pragma unroll
+  for (int s = 2; s <= (1 << L); s <<= 1) {
+    const int hs = s >> 1;
+#pragma unroll
+    for (int base = 0; base < (1 << L); base += s) {
+      qc tmp[1 << L];
+#pragma unroll
+      for (int i = 0; i < hs; ++i) {
+        const qc E = w[base + i];
+        const qc Y = w[base + hs + i];
+        if (SIDE == 0) {
+          tmp[2 * i] = E;
+          if (i + 1 < hs) tmp[2 * i + 1] = cadd(Y, w[base + hs + i + 1]);
+          else tmp[2 * i + 1] = hv ? cadd(Y, h[base + hs]) : Y;
+        } else {
+          tmp[2 * i + 1] = E;
+          if (i >= 1) tmp[2 * i] = cadd(w[base + hs + i - 1], Y);
+          else tmp[2 * i] = hv ? cadd(h[base + hs], Y) : Y;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < s; ++i) w[base + i] = tmp[i];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ F1
+// Large class j: one task = the 2^L1 Gray slots t*H + lo (H = 2^(b-L1),
+// lo = gray(ilo)) of both sides.  The cells are loaded straight from the row:
+// own cell c -> time index n = 2^j (2c+1); the IO object returns the folded
+// pair (c(n), d(n)).
+template <int L1, class IO>
+QFT_HD void task_f1_big(const Eng& e, const IO& io, int j, int ilo) {
+  const int b = cls_bits(e.r, j);
+  const int h = b - L1;
+  const int H = 1 << h;
+  const int lo = ilo ^ (ilo >> 1);
+  qc vc[1 << L1], vs[1 << L1];
+#pragma unroll
+  for (int t = 0; t < (1 << L1); ++t) {
+    const int ig = ig_c(t);
+    const int c = (ig << h) | ((ig & 1) ? (H - 1 - ilo) : ilo);
+    io.get_cd((2 * c + 1) << j, vc[t], vs[t]);
+  }
+  dif_regs<L1, 0>(vc, b, ilo, e.sec, e.r);
+  dif_regs<L1, 1>(vs, b, ilo, e.sec, e.r);
+  const int off = cls_off(e.r, j);
+#pragma unroll
+  for (int t = 0; t < (1 << L1); ++t) {
+    e.side0[qft_pidx(off + t * H + lo)] = vc[t];
+    e.side1[qft_pidx(off + t * H + lo)] = vs[t];
+  }
+}
+
+// Small class j (2^L cells, L = r-2-j): forward and backward in one task.
+// Class r-2 (one cell, n = N/4) has no DST class; its DST value d(N/4) is the
+// dst(4) base case and goes to the DST base cell.
+template <int L, class IO>
+QFT_HD void task_f1_small(const Eng& e, const IO& io, int j) {
+  qc vc[1 << L], vs[1 << L];
+#pragma unroll
+  for (int g = 0; g < (1 << L); ++g) io.get_cd((2 * ig_c(g) + 1) << j, vc[g], vs[g]);
+  const int off = cls_off(e.r, j);
+  dif_regs<L, 0>(vc, L, 0, e.sec, e.r);
+  bwd_chunk<L, 0>(vc, vc, false);
+#pragma unroll
+  for (int k = 0; k < (1 << L); ++k) e.side0[qft_pidx(off + k)] = vc[k];
+  if (j <= e.r - 3) {
+    dif_regs<L, 1>(vs, L, 0, e.sec, e.r);
+    bwd_chunk<L, 1>(vs, vs, false);
+#pragma unroll
+    for (int k = 0; k < (1 << L); ++k) e.side1[qft_pidx(off + k)] = vs[k];
+  } else {
+    e.side1[qft_pidx(e.N / 2 - 2)] = vs[0];
+  }
+}
+
+template <class IO>
+QFT_HD void task_f1_base(const Eng& e, const IO& io) {
+  e.side0[qft_pidx(e.N / 2 - 1)] = io.get_c(0);
+  e.side0[qft_pidx(e.N / 2)] = io.get_c(e.N / 2);
+}
+
+// ------------------------------------------------------------ DIF, LEAF
+template <int L, int SIDE>
+QFT_HD void task_dif(const Eng& e, int j, int D, int tau) {
+  const int nb = cls_bits(e.r, j) - D;
+  const int h = nb - L;
+  const int q = tau >> h;
+  const int lo = tau & ((1 << h) - 1);
+  qc* A = side_ptr(e, SIDE);
+  const int base = cls_off(e.r, j) + (q << nb) + lo;
+  qc v[1 << L];
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) v[t] = A[qft_pidx(base + (t << h))];
+  dif_regs<L, SIDE>(v, nb, (int)invgray((unsigned)lo), e.sec, e.r);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) A[qft_pidx(base + (t << h))] = v[t];
+}
+
+template <int L, int SIDE>
+QFT_HD void task_leaf(const Eng& e, int j, int q) {
+  qc* A = side_ptr(e, SIDE);
+  const int base = cls_off(e.r, j) + (q << L);
+  qc v[1 << L];
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) v[t] = A[qft_pidx(base + t)];
+  dif_regs<L, SIDE>(v, L, 0, e.sec, e.r);
+  bwd_chunk<L, SIDE>(v, v, false);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) A[qft_pidx(base + t)] = v[t];
+}
+
+// --------------------------------------------------------------- SLICE
+// Node at depth D-L (2^nb cells) whose depth-D descendants (2^(b-D) cells
+// each, natural frequency order, descendant t at offset t*S) are known.  Task
+// (q, r_) produces node outputs [r_ 2^L, (r_+1) 2^L).  The neighbour value
+// needed at a chunk edge for the odd-harmonic child of every sub-node is, by
+// the even-harmonic copies of the recursion, a raw value of descendant t at
+// slice r_+1 (DCT) or r_-1 (DST), for every t >= 1.
+struct SliceRegs {
+  qc w[16];
+  qc h[16];
+  int base;   // node base + r_ * 2^L  (write position)
+  bool hv;
+};
+
+template <int L, int SIDE>
+QFT_HD void task_slice_read(const Eng& e, int j, int D, int tau, SliceRegs& s) {
+  const int b = cls_bits(e.r, j);
+  const int sb = b - D;                   // log2 S
+  const int S = 1 << sb;
+  const int nb = b - (D - L);
+  const int q = tau >> sb;
+  const int rr = tau & (S - 1);
+  const qc* A = side_ptr(e, SIDE);
+  const int nbase = cls_off(e.r, j) + (q << nb);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) s.w[t] = A[qft_pidx(nbase + t * S + rr)];
+  const bool hv = SIDE == 0 ? (rr + 1 < S) : (rr >= 1);
+  const int hoff = SIDE == 0 ? rr + 1 : rr - 1;
+  if (hv) {
+#pragma unroll
+    for (int t = 1; t < (1 << L); ++t) s.h[t] = A[qft_pidx(nbase + t * S + hoff)];
+  }
+  s.hv = hv;
+  s.base = nbase + (rr << L);
+}
+
+template <int L, int SIDE>
+QFT_HD void task_slice_write(const Eng& e, SliceRegs& s) {
+  qc w[1 << L];
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) w[t] = s.w[t];
+  bwd_chunk<L, SIDE>(w, s.h, s.hv);
+  qc* A = side_ptr(e, SIDE);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) A[qft_pidx(s.base + t)] = w[t];
+}
+
+// --------------------------------------------------------------- FINAL
+// Class output O_j(k) of side s: DCT k in [0, P_j) at off+k; DST k in [1, P_j]
+// at off+k-1.
+QFT_HD qc cls_out(const Eng& e, int s, int j, int k) {
+  return side_ptr(e, s)[qft_pidx(cls_off(e.r, j) + k - s)];
+}
+
+// C_M(k) for M = 2^m, k in [0, M/2]: walk down the dct recursion (recording
+// which of eqs qft_5C / qft_5D / qft_6 applies at each level), then add the
+// class outputs bottom-up in the recursion's order.
+QFT_HD qc chain_c(const Eng& e, int m, int k) {
+  uint64_t ops = 0;
+  int nl = 0;
+  while (m > 1) {
+    const int M = 1 << m;
+    const int qq = M >> 2;
+    uint64_t op;
+    if (k < qq) op = 0;
+    else if (k > qq) { op = 1; k = (M >> 1) - k; }
+    else op = 2;
+    ops |= op << (2 * nl);
+    ++nl;
+    --m;
+  }
+  const qc c0 = e.side0[qft_pidx(e.N / 2 - 1)];
+  const qc c1 = e.side0[qft_pidx(e.N / 2)];
+  qc v = (k == 0) ? cadd(c0, c1) : csub(c0, c1);    // dct(2)
+  for (int i = nl - 1; i >= 0; --i) {
+    const int op = (int)((ops >> (2 * i)) & 3);
+    const int mm = m + nl - i;                        // log2 of this level's periodization
+    const int j = e.r - mm;
+    if (op == 0) v = cadd(v, cls_out(e, 0, j, k));
+    else if (op == 1) { v = csub(v, cls_out(e, 0, j, k)); k = (1 << (mm - 1)) - k; }
+  }
+  return v;
+}
+
+// S_M(k), k in [1, M/2-1]: same walk for the dst recursion; it stops at
+// k = M/4 (S_M(M/4) = O(M/4)) or at the dst(4) base.
+QFT_HD qc chain_s(const Eng& e, int m, int k) {
+  uint64_t ops = 0;
+  int nl = 0;
+  qc v;
+  for (;;) {
+    if (m == 2) { v = e.side1[qft_pidx(e.N / 2 - 2)]; break; }
+    const int M = 1 << m;
+    const int qq = M >> 2;
+    if (k == qq) { v = cls_out(e, 1, e.r - m, qq); break; }
+    uint64_t op;
+    if (k < qq) op = 0;
+    else { op = 1; k = (M >> 1) - k; }
+    ops |= op << nl;
+    ++nl;
+    --m;
+  }
+  for (int i = nl - 1; i >= 0; --i) {
+    const int op = (int)((ops >> i) & 1);
+    const int mm = m + nl - i;
+    const int j = e.r - mm;
+    const qc o = cls_out(e, 1, j, k);
+    if (op == 0) v = cadd(v, o);
+    else { v = csub(o, v); k = (1 << (mm - 1)) - k; }
+  }
+  return v;
+}
+
+// Regular frequency orbit: k0 in [1, N/2^(LF+1)).  The task builds C and S
+// on the orbit {+-k0 + m N/2^LF} level by level and emits X at 2^(LF+1) bins.
+template <int LF, class IO>
+QFT_HD void task_fin_reg(const Eng& e, const IO& io, int k0) {
+  qc C[1 << LF], S[1 << LF];
+  int K[1 << LF];
+  C[0] = chain_c(e, e.r - LF, k0);
+  S[0] = chain_s(e, e.r - LF, k0);
+  K[0] = k0;
+#pragma unroll
+  for (int l = LF; l >= 1; --l) {
+    const int n = 1 << (LF - l);
+    const int j = l - 1;
+    const int Mh = e.N >> l;    // M/2 with M = N/2^(l-1)
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const qc oc = cls_out(e, 0, j, K[i]);
+      const qc os = cls_out(e, 1, j, K[i]);
+      C[n + i] = csub(C[i], oc);
+      C[i] = cadd(C[i], oc);
+      S[n + i] = csub(os, S[i]);
+      S[i] = cadd(S[i], os);
+      K[n + i] = Mh - K[i];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < (1 << LF); ++i) io.emit(K[i], C[i], S[i]);
+}
+
+// Multiples of N/2^(LF+1): one bin pair per task, full chain from periodization N.
+template <class IO>
+QFT_HD void task_fin_spec(const Eng& e, const IO& io, int LF, int mi) {
+  const int k = mi * (e.N >> (LF + 1));
+  const qc C = chain_c(e, e.r, k);
+  const qc S = (k > 0 && k < e.N / 2) ? chain_s(e, e.r, k) : mkc(0.f, 0.f);
+  io.emit(k, C, S);
+}
+
+// ------------------------------------------------------------ dispatch
+QFT_HD const QftSeg& find_seg(const QftRowPlan& P, int p, int tau) {
+  int s = P.phase_seg0[p];
+  const int e = P.phase_seg0[p + 1];
+  while (s + 1 < e && P.segs[s + 1].begin <= tau) ++s;
+  return P.segs[s];
+}
+
+template <int L1, class IO>
+QFT_HD void run_plain_task(const QftRowPlan& P, const QftSeg& sg, const Eng& e, const IO& io, int loc) {
+  switch (sg.type) {
+  case QFT_SEG_F1_BIG: task_f1_big<L1>(e, io, sg.cls, loc); break;
+  case QFT_SEG_F1_SMALL:
+    switch (sg.L) {
+    case 0: task_f1_small<0>(e, io, sg.cls); break;
+    case 1: task_f1_small<1>(e, io, sg.cls); break;
+    case 2: task_f1_small<2>(e, io, sg.cls); break;
+    case 3: task_f1_small<3>(e, io, sg.cls); break;
+    case 4: task_f1_small<4>(e, io, sg.cls); break;
+    default: break;
+    }
+    break;
+  case QFT_SEG_F1_BASE: task_f1_base(e, io); break;
+  case QFT_SEG_DIF:
+#define QFT_DIF_CASE(LL) case LL: if (sg.side) task_dif<LL, 1>(e, sg.cls, sg.D, loc); else task_dif<LL, 0>(e, sg.cls, sg.D, loc); break;
+    switch (sg.L) { QFT_DIF_CASE(1) QFT_DIF_CASE(2) QFT_DIF_CASE(3) QFT_DIF_CASE(4) default: break; }
+#undef QFT_DIF_CASE
+    break;
+  case QFT_SEG_LEAF:
+#define QFT_LEAF_CASE(LL) case LL: if (sg.side) task_leaf<LL, 1>(e, sg.cls, loc); else task_leaf<LL, 0>(e, sg.cls, loc); break;
+    switch (sg.L) { QFT_LEAF_CASE(1) QFT_LEAF_CASE(2) QFT_LEAF_CASE(3) QFT_LEAF_CASE(4) default: break; }
+#undef QFT_LEAF_CASE
+    break;
+  case QFT_SEG_FIN_REG:
+    switch (P.LF) {
+    case 0: task_fin_reg<0>(e, io, loc + 1); break;
+    case 1: task_fin_reg<1>(e, io, loc + 1); break;
+    case 2: task_fin_reg<2>(e, io, loc + 1); break;
+    case 3: task_fin_reg<3>(e, io, loc + 1); break;
+    default: break;
+    }
+    break;
+  case QFT_SEG_FIN_SPEC: task_fin_spec(e, io, P.LF, loc); break;
+  default: break;
+  }
+}
+
+QFT_HD void run_slice_read(const QftSeg& sg, const Eng& e, int loc, SliceRegs& s) {
+#define QFT_SR_CASE(LL) case LL: if (sg.side) task_slice_read<LL, 1>(e, sg.cls, sg.D, loc, s); else task_slice_read<LL, 0>(e, sg.cls, sg.D, loc, s); break;
+  switch (sg.L) { QFT_SR_CASE(1) QFT_SR_CASE(2) QFT_SR_CASE(3) QFT_SR_CASE(4) default: break; }
+#undef QFT_SR_CASE
+}
+
+QFT_HD void run_slice_write(const QftSeg& sg, const Eng& e, SliceRegs& s) {
+#define QFT_SW_CASE(LL) case LL: if (sg.side) task_slice_write<LL, 1>(e, s); else task_slice_write<LL, 0>(e, s); break;
+  switch (sg.L) { QFT_SW_CASE(1) QFT_SW_CASE(2) QFT_SW_CASE(3) QFT_SW_CASE(4) default: break; }
+#undef QFT_SW_CASE
+}
+
+}  // namespace qft

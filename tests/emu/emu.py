@@ -1,0 +1,90 @@
+"""Builds and loads the host emulation of the row engine (tests only)."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+SRC = os.path.join(HERE, "qft_emu.cpp")
+DEPS = [os.path.join(ROOT, "paper_1301_0763_gb300", "csrc", f)
+        for f in ("qft_engine.cuh", "qft_io.cuh", "qft_planner.h", "qft_plan.h", "qft_consts.h")]
+LIB = os.path.join(HERE, "_qft_emu.so")
+_lib = None
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    newest = max(os.path.getmtime(p) for p in [SRC] + DEPS)
+    if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
+        subprocess.run(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", SRC, "-o", LIB],
+                       check=True)
+    lib = ctypes.CDLL(LIB)
+    fp = ctypes.POINTER(ctypes.c_float)
+    ip = ctypes.POINTER(ctypes.c_int)
+    up = ctypes.POINTER(ctypes.c_uint16)
+    lib.emu_c2c.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ip, ctypes.c_int]
+    lib.emu_c2c_half.argtypes = [ctypes.c_int, ctypes.c_int64, up, up, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.emu_r2c.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int]
+    lib.emu_plan_info.argtypes = [ctypes.c_int, ip, ip, ip, ip]
+    _lib = lib
+    return lib
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def c2c(z, op=0, tune=None, nthr=256):
+    z = np.ascontiguousarray(z, dtype=np.complex64)
+    N = z.shape[-1]
+    out = np.empty_like(z)
+    t = None
+    if tune is not None:
+        t = (ctypes.c_int * 5)(*tune)
+    rc = load().emu_c2c(N, z.size // N, _fp(z.view(np.float32)), _fp(out.view(np.float32)), op,
+                        ctypes.cast(t, ctypes.POINTER(ctypes.c_int)) if t is not None else None, nthr)
+    if rc != 0:
+        raise ValueError(f"emulation rejected N={N} tune={tune} (rc={rc})")
+    return out
+
+
+def c2c_half(z16, dtype, op=0, nthr=256):
+    """z16: uint16 array [..., N, 2] holding fp16 (dtype=1) or bf16 (dtype=2) pairs."""
+    z16 = np.ascontiguousarray(z16, dtype=np.uint16)
+    N = z16.shape[-2]
+    out = np.empty_like(z16)
+    up = ctypes.POINTER(ctypes.c_uint16)
+    rc = load().emu_c2c_half(N, z16.size // (2 * N), z16.ctypes.data_as(up), out.ctypes.data_as(up), dtype, op, nthr)
+    if rc != 0:
+        raise ValueError("emulation rejected")
+    return out
+
+
+def r2c(x, op, N, nthr=256):
+    """op 0: real [B,N] -> complex [B,N/2+1]; 1: complex -> real (1/N); 2: complex -> real (adjoint);
+    3: real -> complex (adjoint of the real inverse)."""
+    if op in (0, 3):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        out = np.empty(x.shape[:-1] + (N // 2 + 1,), dtype=np.complex64)
+        rows = x.size // N
+        rc = load().emu_r2c(N, rows, _fp(x), _fp(out.view(np.float32)), op, nthr)
+    else:
+        x = np.ascontiguousarray(x, dtype=np.complex64)
+        out = np.empty(x.shape[:-1] + (N,), dtype=np.float32)
+        rows = x.size // (N // 2 + 1)
+        rc = load().emu_r2c(N, rows, _fp(x.view(np.float32)), _fp(out), op, nthr)
+    if rc != 0:
+        raise ValueError("emulation rejected")
+    return out
+
+
+def plan_info(N, tune=None):
+    t = (ctypes.c_int * 5)(*tune) if tune is not None else None
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc = load().emu_plan_info(N, ctypes.cast(t, ctypes.POINTER(ctypes.c_int)) if t is not None else None,
+                              ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return rc, a.value, b.value, c.value

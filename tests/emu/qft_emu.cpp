@@ -1,0 +1,144 @@
+// Host emulation of the row engine (test infrastructure only).
+//
+// Compiles the library's engine header (qft_engine.cuh / qft_io.cuh) and its
+// planner for the host with QFT_HOST_EMULATION, and runs the phases of one CTA
+// the way the kernel does: every phase loops over its tasks, SLICE phases run
+// in rounds (all reads of a round, then all writes).  The test-suite compares
+// its output bit for bit with the improved-QFT oracle built in FP32, which
+// checks the engine's index logic without a GPU.  The product never loads this.
+#define QFT_HOST_EMULATION 1
+#include "../../paper_1301_0763_gb300/csrc/qft_io.cuh"
+#include "../../paper_1301_0763_gb300/csrc/qft_planner.h"
+#include "../../paper_1301_0763_gb300/csrc/qft_consts.h"
+#include <vector>
+#include <stdint.h>
+
+using namespace qft;
+
+template <class IO>
+static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr) {
+  for (int p = 0; p < P.nphase; ++p) {
+    const int nt = P.phase_ntasks[p];
+    if (!P.phase_is_slice[p]) {
+      for (int tid = 0; tid < nthr; ++tid)
+        for (int tau = tid; tau < nt; tau += nthr) {
+          const QftSeg& sg = find_seg(P, p, tau);
+          switch (P.L1) {
+          case 0: run_plain_task<0>(P, sg, e, io, tau - sg.begin); break;
+          case 1: run_plain_task<1>(P, sg, e, io, tau - sg.begin); break;
+          case 2: run_plain_task<2>(P, sg, e, io, tau - sg.begin); break;
+          case 3: run_plain_task<3>(P, sg, e, io, tau - sg.begin); break;
+          default: run_plain_task<4>(P, sg, e, io, tau - sg.begin); break;
+          }
+        }
+    } else {
+      std::vector<SliceRegs> regs(nthr);
+      std::vector<int> segi(nthr);
+      for (int rb = 0; rb < nt; rb += nthr) {
+        for (int tid = 0; tid < nthr; ++tid) {
+          const int tau = rb + tid;
+          segi[tid] = -1;
+          if (tau < nt) {
+            const QftSeg& sg = find_seg(P, p, tau);
+            segi[tid] = (int)(&sg - P.segs);
+            run_slice_read(sg, e, tau - sg.begin, regs[tid]);
+          }
+        }
+        for (int tid = 0; tid < nthr; ++tid)
+          if (segi[tid] >= 0) run_slice_write(P.segs[segi[tid]], e, regs[tid]);
+      }
+    }
+  }
+}
+
+struct Row {
+  std::vector<qc> s0, s1;
+  std::vector<float> sec;
+  QftRowPlan P;
+  Eng e;
+  int ok;
+  Row(int N, const int* tune, int nthr) {
+    int r = 0; while ((1 << r) < N) ++r;
+    QftTune t = qft_default_tune(r);
+    if (tune) { t.L1 = tune[0]; t.LS = tune[1]; t.LL = tune[2]; t.LB = tune[3]; t.LF = tune[4]; }
+    ok = qft_build_row_plan(r, t, &P) == 0 && P.max_slice_nodes <= nthr;
+    s0.assign(qft_side_len(N), mkc(NAN, NAN));
+    s1.assign(qft_side_len(N), mkc(NAN, NAN));
+    sec.assign(N / 4 + 1, 0.f);
+    qft_fill_secants(N, sec.data());
+    e.side0 = s0.data(); e.side1 = s1.data(); e.sec = sec.data(); e.r = r; e.N = N;
+  }
+};
+
+extern "C" int emu_plan_info(int N, const int* tune, int* nphase, int* nseg, int* max_slice) {
+  Row R(N, tune, 1 << 20);
+  *nphase = R.P.nphase; *nseg = R.P.nseg; *max_slice = R.P.max_slice_nodes;
+  return R.ok ? 0 : -1;
+}
+
+// op: 0 forward, 1 inverse, 2 forward adjoint, 3 inverse adjoint; data complex64 interleaved
+extern "C" int emu_c2c(int N, int64_t batch, const float* in, float* out, int op, const int* tune, int nthr) {
+  if (N < 4) return -1;
+  Row R(N, tune, nthr);
+  if (!R.ok) return -2;
+  for (int64_t b = 0; b < batch; ++b) {
+    IoC2C<StC64> io;
+    io.in = reinterpret_cast<const qc*>(in) + b * N;
+    io.out = reinterpret_cast<qc*>(out) + b * N;
+    io.N = N; io.scale = 1.f; io.scaled = false;
+    io.in_op = io.out_op = QFT_LANE_ID;
+    if (op == 1) { io.in_op = io.out_op = QFT_LANE_SWAP; io.scale = 1.f / N; io.scaled = true; }
+    if (op == 2) { io.in_op = io.out_op = QFT_LANE_CONJ; }
+    if (op == 3) { io.scale = 1.f / N; io.scaled = true; }
+    run_row(R.P, R.e, io, nthr);
+  }
+  return 0;
+}
+
+// dtype 1: fp16 pairs, 2: bf16 pairs (uint16 pairs in memory)
+extern "C" int emu_c2c_half(int N, int64_t batch, const uint16_t* in, uint16_t* out, int dtype, int op, int nthr) {
+  Row R(N, nullptr, nthr);
+  if (!R.ok) return -2;
+  for (int64_t b = 0; b < batch; ++b) {
+    if (dtype == 1) {
+      IoC2C<StC16> io;
+      io.in = reinterpret_cast<const h2pair*>(in) + b * N; io.out = reinterpret_cast<h2pair*>(out) + b * N;
+      io.N = N; io.scale = 1.f; io.scaled = false; io.in_op = io.out_op = QFT_LANE_ID;
+      if (op == 1) { io.in_op = io.out_op = QFT_LANE_SWAP; io.scale = 1.f / N; io.scaled = true; }
+      run_row(R.P, R.e, io, nthr);
+    } else {
+      IoC2C<StBF16> io;
+      io.in = reinterpret_cast<const h2pair*>(in) + b * N; io.out = reinterpret_cast<h2pair*>(out) + b * N;
+      io.N = N; io.scale = 1.f; io.scaled = false; io.in_op = io.out_op = QFT_LANE_ID;
+      if (op == 1) { io.in_op = io.out_op = QFT_LANE_SWAP; io.scale = 1.f / N; io.scaled = true; }
+      run_row(R.P, R.e, io, nthr);
+    }
+  }
+  return 0;
+}
+
+// R2C family: op 0 forward (real->half spectrum), 1 inverse (half->real),
+// 2 forward adjoint (half->real, w=1), 3 inverse adjoint (real->half, weights w/N)
+extern "C" int emu_r2c(int N, int64_t batch, const float* in, float* out, int op, int nthr) {
+  Row R(N, nullptr, nthr);
+  if (!R.ok) return -2;
+  const int64_t H = N / 2 + 1;
+  for (int64_t it = 0; it < (batch + 1) / 2; ++it) {
+    const int64_t a = 2 * it, b = 2 * it + 1;
+    if (op == 0 || op == 3) {
+      IoR2C<StC64> io;
+      io.ina = in + a * N; io.inb = b < batch ? in + b * N : nullptr;
+      io.outa = reinterpret_cast<qc*>(out) + a * H; io.outb = b < batch ? reinterpret_cast<qc*>(out) + b * H : nullptr;
+      io.N = N; io.wscale = op == 0 ? 0.f : 1.f / N;
+      run_row(R.P, R.e, io, nthr);
+    } else {
+      IoC2R<StC64> io;
+      io.ina = reinterpret_cast<const qc*>(in) + a * H; io.inb = b < batch ? reinterpret_cast<const qc*>(in) + b * H : nullptr;
+      io.outa = out + a * N; io.outb = b < batch ? out + b * N : nullptr;
+      io.N = N;
+      if (op == 1) { io.wmid = 2.f; io.scale = 1.f / N; } else { io.wmid = 1.f; io.scale = 1.f; }
+      run_row(R.P, R.e, io, nthr);
+    }
+  }
+  return 0;
+}

@@ -1,0 +1,125 @@
+"""The kernel's engine source, compiled for the host, against the oracle (no GPU).
+
+The row engine (qft_engine.cuh / qft_io.cuh) is the code the sm_103a kernels
+run.  Built for the host with QFT_HOST_EMULATION and driven phase by phase like
+one CTA, it must reproduce the improved-QFT recursion evaluated in FP32 by the
+oracle bit for bit: every task performs exactly the additions and multiplies
+of Sec. 5 on exactly the same operands, so any index mistake shows up as a
+mismatch.  It is also checked against the FP64 oracle within the FP32 error
+level of the method.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1301_0763_gb300 import inputs
+from tests.emu import emu
+
+LOGS = list(range(2, 15))
+
+
+def bits_equal(a, b):
+    a = np.ascontiguousarray(a)
+    b = np.ascontiguousarray(b)
+    return a.shape == b.shape and np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def rel_l2_rows(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+@pytest.mark.parametrize("lg", LOGS)
+def test_c2c_forward_bit_exact(lg):
+    N = 1 << lg
+    z = inputs.normal_complex(3, N, seed=1)
+    X = emu.c2c(z)
+    ref32 = orc.cdft(z, fp32=True).astype(np.complex64)
+    assert bits_equal(X, ref32)
+    ref64 = orc.cdft(z)
+    assert rel_l2_rows(X.astype(np.complex128), ref64).max() < 4e-8 * np.sqrt(N) + 1e-7
+
+
+@pytest.mark.parametrize("lg", [2, 3, 6, 10, 13])
+@pytest.mark.parametrize("op", [1, 2, 3])
+def test_c2c_other_ops_bit_exact(lg, op):
+    N = 1 << lg
+    z = inputs.uniform_complex(2, N, seed=3)
+    out = emu.c2c(z, op=op)
+    if op == 1:
+        ref = orc.icdft(z, fp32=True)
+    elif op == 2:
+        ref = orc.cdft_adjoint(z, fp32=True)
+    else:
+        ref = orc.cdft(z, fp32=True) / N
+    assert bits_equal(out, ref.astype(np.complex64))
+
+
+@pytest.mark.parametrize("tune", [(3, 4, 3, 4, 3), (4, 2, 2, 2, 2), (2, 3, 4, 3, 1), (4, 4, 1, 1, 0),
+                                  (0, 1, 1, 4, 3), (3, 3, 3, 3, 3)])
+@pytest.mark.parametrize("lg", [5, 9, 12])
+def test_schedules_do_not_change_the_result(tune, lg):
+    """Any tile/stage schedule of the planner yields the same bits."""
+    N = 1 << lg
+    rc, _, _, max_slice = emu.plan_info(N, tune)
+    if rc != 0 or max_slice > 256:
+        pytest.skip("schedule not valid for this N with 256 threads")
+    z = inputs.normal_complex(1, N, seed=5)
+    assert bits_equal(emu.c2c(z, tune=tune), emu.c2c(z))
+
+
+@pytest.mark.parametrize("lg", [2, 3, 5, 8, 12])
+@pytest.mark.parametrize("rows", [1, 2, 5])
+def test_real_forward_and_inverse_bit_exact(lg, rows):
+    N = 1 << lg
+    x = inputs.normal_real(rows, N, seed=7)
+    X = emu.r2c(x, 0, N)
+    assert bits_equal(X, orc.rdft(x, fp32=True).astype(np.complex64))
+    Y = X.copy()
+    Y[:, 0] += 0.25j          # imaginary parts at 0 and N/2 are ignored by the inverse
+    Y[:, -1] -= 0.5j
+    xr = emu.r2c(Y, 1, N)
+    assert bits_equal(xr, orc.irdft(Y, N, fp32=True).astype(np.float32))
+    assert np.abs(xr - x).max() < 1e-5 * np.sqrt(N)
+
+
+@pytest.mark.parametrize("lg", [2, 4, 9, 12])
+def test_real_adjoints_bit_exact(lg):
+    N = 1 << lg
+    g = inputs.normal_complex(3, N // 2 + 1, seed=8)
+    gx = emu.r2c(g, 2, N)
+    assert bits_equal(gx, orc.rdft_adjoint(g, N, fp32=True).astype(np.float32))
+    u = inputs.normal_real(3, N, seed=9)
+    gy = emu.r2c(u, 3, N)
+    ref = orc.irdft_adjoint(u, fp32=True).astype(np.complex64)
+    assert bits_equal(gy, ref)
+
+
+def _bf16_round(x32):
+    """Round float32 -> bfloat16 (nearest even), returned as uint16 bits."""
+    u = np.ascontiguousarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return u.astype(np.uint16)
+
+
+def _bf16_to_f32(b):
+    return (b.astype(np.uint32) << 16).view(np.float32)
+
+
+@pytest.mark.parametrize("lg", [4, 10, 13])
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_half_storage_bit_exact(lg, dtype):
+    N = 1 << lg
+    z = inputs.uniform_complex(2, N, seed=10).view(np.float32).reshape(2, N, 2)
+    if dtype == 1:
+        zin = z.astype(np.float16)
+        bits = zin.view(np.uint16)
+        zf = zin.astype(np.float32)
+    else:
+        bits = _bf16_round(z)
+        zf = _bf16_to_f32(bits)
+    out = emu.c2c_half(bits, dtype)
+    zc = zf[..., 0].astype(np.float64) + 1j * zf[..., 1]
+    ref = orc.cdft(zc, fp32=True).astype(np.complex64)
+    ref2 = ref.view(np.float32).reshape(2, N, 2)
+    ref_bits = ref2.astype(np.float16).view(np.uint16) if dtype == 1 else _bf16_round(ref2)
+    assert np.array_equal(out, ref_bits)
