@@ -1,0 +1,49 @@
+// qft_internal.h -- definitions shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "qft_plan.h"
+#include "qft_planner.h"
+#include "../../include/qft_gb300.h"
+
+namespace qft_lib {
+constexpr int kThreads = 256;     // threads per CTA of the row engine
+constexpr int kMaxRowLog2 = 14;   // largest row one CTA transforms in shared memory
+
+// Shared-memory layout of the row engine: plan | secant table | DCT side | DST side.
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t side_bytes(int N) { return align16(8 * (size_t)((N / 2) + ((N / 2) >> 4) + 1)); }
+__host__ __device__ inline size_t off_sec() { return align16(sizeof(QftRowPlan)); }
+__host__ __device__ inline size_t off_side0(int N) { return off_sec() + align16(sizeof(float) * (size_t)(N / 4 + 1)); }
+__host__ __device__ inline size_t row_smem_bytes(int N) { return off_side0(N) + 2 * side_bytes(N); }
+}
+
+struct qft_plan_s {
+  uint32_t magic;
+  int kind, dtype;
+  int64_t n, batch;
+  int r;
+  QftTune tune;
+  QftRowPlan host_plan;
+  QftRowPlan* d_plan;
+  float* d_sec;
+  int grid;
+  size_t smem;
+  int device;
+  int sms;
+  cudaError_t last_cuda;
+  cudaStream_t last_stream;
+};
+
+
+static inline int qft_set_cuda(qft_plan p, cudaError_t e) {
+  if (e == cudaSuccess) return QFT_OK;
+  if (p) p->last_cuda = e;
+  return QFT_ERR_CUDA;
+}
+
+// Launchers, one translation unit each (compiled in parallel).
+int qft_launch_c2c_f32(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
+int qft_launch_c2c_f16(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
+int qft_launch_c2c_bf16(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
+int qft_launch_real(qft_plan p, int op, const void* in, void* out, cudaStream_t st);

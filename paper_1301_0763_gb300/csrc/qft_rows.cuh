@@ -1,0 +1,209 @@
+// qft_rows.cuh -- the row-engine kernel (one CTA per row or pair of real rows,
+// persistent over the batch) and its launch helpers.
+#pragma once
+#include "qft_internal.h"
+#include "qft_io.cuh"
+
+using namespace qft;
+using qft_lib::kThreads;
+
+namespace {
+
+// ------------------------------------------------------------ factories
+template <class ST>
+struct FacC2C {
+  const typename ST::elem* in;
+  typename ST::elem* out;
+  int N;
+  int in_op, out_op;
+  float scale;
+  int scaled;
+  __device__ __forceinline__ IoC2C<ST> make(int64_t row) const {
+    IoC2C<ST> io;
+    io.in = in + row * (int64_t)N;
+    io.out = out + row * (int64_t)N;
+    io.N = N; io.in_op = in_op; io.out_op = out_op; io.scale = scale; io.scaled = scaled != 0;
+    return io;
+  }
+};
+
+template <class ST>
+struct FacR2C {
+  const float* in;
+  typename ST::elem* out;
+  int64_t rows;
+  int N;
+  float wscale;
+  __device__ __forceinline__ IoR2C<ST> make(int64_t item) const {
+    IoR2C<ST> io;
+    const int64_t a = 2 * item, b = 2 * item + 1;
+    const int64_t H = N / 2 + 1;
+    io.ina = in + a * (int64_t)N;
+    io.inb = b < rows ? in + b * (int64_t)N : nullptr;
+    io.outa = out + a * H;
+    io.outb = b < rows ? out + b * H : nullptr;
+    io.N = N; io.wscale = wscale;
+    return io;
+  }
+};
+
+template <class ST>
+struct FacC2R {
+  const typename ST::elem* in;
+  float* out;
+  int64_t rows;
+  int N;
+  float wmid, scale;
+  __device__ __forceinline__ IoC2R<ST> make(int64_t item) const {
+    IoC2R<ST> io;
+    const int64_t a = 2 * item, b = 2 * item + 1;
+    const int64_t H = N / 2 + 1;
+    io.ina = in + a * H;
+    io.inb = b < rows ? in + b * H : nullptr;
+    io.outa = out + a * (int64_t)N;
+    io.outb = b < rows ? out + b * (int64_t)N : nullptr;
+    io.N = N; io.wmid = wmid; io.scale = scale;
+    return io;
+  }
+};
+
+// ------------------------------------------------------------ row kernel
+using qft_lib::off_sec;
+using qft_lib::off_side0;
+using qft_lib::side_bytes;
+
+template <class FAC, int L1>
+__global__ void __launch_bounds__(kThreads)
+k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int sec_stride,
+       int64_t nitems, FAC fac) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  QftRowPlan& P = *reinterpret_cast<QftRowPlan*>(smem);
+  {
+    const int* src = reinterpret_cast<const int*>(gplan);
+    int* dst = reinterpret_cast<int*>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(QftRowPlan) / 4); i += kThreads) dst[i] = src[i];
+  }
+  __syncthreads();
+  const int r = P.r;
+  const int N = 1 << r;
+  float* sec = reinterpret_cast<float*>(smem + off_sec());
+  qc* side0 = reinterpret_cast<qc*>(smem + off_side0(N));
+  qc* side1 = reinterpret_cast<qc*>(smem + off_side0(N) + side_bytes(N));
+  for (int m = threadIdx.x; m <= N / 4; m += kThreads) sec[m] = gsec[(int64_t)m * sec_stride];
+  __syncthreads();
+  Eng e;
+  e.side0 = side0; e.side1 = side1; e.sec = sec; e.r = r; e.N = N;
+  const int tid = threadIdx.x;
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const auto io = fac.make(item);
+    for (int p = 0; p < P.nphase; ++p) {
+      const int nt = P.phase_ntasks[p];
+      if (!P.phase_is_slice[p]) {
+        for (int tau = tid; tau < nt; tau += kThreads) {
+          const QftSeg& sg = find_seg(P, p, tau);
+          run_plain_task<L1>(P, sg, e, io, tau - sg.begin);
+        }
+        __syncthreads();
+      } else {
+        for (int rb = 0; rb < nt; rb += kThreads) {
+          const int tau = rb + tid;
+          SliceRegs s;
+          int segi = -1;
+          if (tau < nt) {
+            const QftSeg& sg = find_seg(P, p, tau);
+            segi = (int)(&sg - P.segs);
+            run_slice_read(sg, e, tau - sg.begin, s);
+          }
+          __syncthreads();
+          if (segi >= 0) run_slice_write(P.segs[segi], e, s);
+          __syncthreads();
+        }
+      }
+    }
+  }
+}
+
+// N = 2: the CDFT definition (Sec. 4.1), one thread per row.
+template <class ST>
+__global__ void k_c2c_n2(FacC2C<ST> fac, int64_t rows) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= rows) return;
+  const auto io = fac.make(row);
+  const qc a = io.ld(0), b = io.ld(1);
+  io.st(0, cadd(a, b));
+  io.st(1, csub(a, b));
+}
+
+}  // namespace
+
+
+template <class K>
+static int occupancy_grid(qft_plan p, K kernel, int64_t items) {
+  int per_sm = 0;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+  if (e != cudaSuccess) return qft_set_cuda(p, e);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, p->smem);
+  if (e != cudaSuccess) return qft_set_cuda(p, e);
+  if (per_sm < 1) per_sm = 1;
+  int64_t g = (int64_t)per_sm * p->sms;
+  if (g > items) g = items;
+  if (g < 1) g = 1;
+  p->grid = (int)g;
+  return QFT_OK;
+}
+
+// ------------------------------------------------------------ launchers
+template <class FAC, int L1>
+static inline int launch_rows(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
+  auto kern = k_rows<FAC, L1>;
+  int rc = occupancy_grid(p, kern, items);
+  if (rc != QFT_OK) return rc;
+  kern<<<p->grid, kThreads, p->smem, st>>>(p->d_plan, p->d_sec, 1, items, fac);
+  return qft_set_cuda(p, cudaGetLastError());
+}
+
+template <class ST>
+static inline int exec_c2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
+  FacC2C<ST> f;
+  f.in = static_cast<const typename ST::elem*>(in);
+  f.out = static_cast<typename ST::elem*>(out);
+  f.N = (int)p->n;
+  f.scale = 1.f; f.scaled = 0;
+  switch (op) {
+  case QFT_OP_FORWARD: f.in_op = QFT_LANE_ID; f.out_op = QFT_LANE_ID; break;
+  case QFT_OP_INVERSE: f.in_op = QFT_LANE_SWAP; f.out_op = QFT_LANE_SWAP; f.scale = 1.f / (float)p->n; f.scaled = 1; break;
+  case QFT_OP_FORWARD_ADJOINT: f.in_op = QFT_LANE_CONJ; f.out_op = QFT_LANE_CONJ; break;
+  case QFT_OP_INVERSE_ADJOINT: f.in_op = QFT_LANE_ID; f.out_op = QFT_LANE_ID; f.scale = 1.f / (float)p->n; f.scaled = 1; break;
+  default: return QFT_ERR_INVALID_ARG;
+  }
+  if (p->r == 1) {
+    const int64_t blocks = (p->batch + 127) / 128;
+    k_c2c_n2<ST><<<(unsigned)blocks, 128, 0, st>>>(f, p->batch);
+    return qft_set_cuda(p, cudaGetLastError());
+  }
+  return launch_rows<FacC2C<ST>, 4>(p, f, p->batch, st);
+}
+
+static inline int exec_r2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
+  const int64_t items = (p->batch + 1) / 2;
+  const int N = (int)p->n;
+  if (op == QFT_OP_FORWARD || op == QFT_OP_INVERSE_ADJOINT) {
+    FacR2C<StC64> f;
+    f.in = static_cast<const float*>(in);
+    f.out = static_cast<qc*>(out);
+    f.rows = p->batch; f.N = N;
+    f.wscale = op == QFT_OP_FORWARD ? 0.f : 1.f / (float)N;
+    return launch_rows<FacR2C<StC64>, 4>(p, f, items, st);
+  }
+  if (op == QFT_OP_INVERSE || op == QFT_OP_FORWARD_ADJOINT) {
+    FacC2R<StC64> f;
+    f.in = static_cast<const qc*>(in);
+    f.out = static_cast<float*>(out);
+    f.rows = p->batch; f.N = N;
+    if (op == QFT_OP_INVERSE) { f.wmid = 2.f; f.scale = 1.f / (float)N; }
+    else { f.wmid = 1.f; f.scale = 1.f; }
+    return launch_rows<FacC2R<StC64>, 4>(p, f, items, st);
+  }
+  return QFT_ERR_INVALID_ARG;
+}
+

@@ -1,0 +1,252 @@
+"""Python binding of the GB300 improved-QFT library (C ABI in include/qft_gb300.h).
+
+Argument marshalling only: every step of every transform runs in the CUDA
+kernels of ``_qft_gb300.so``.  PyTorch provides device memory and streams.
+If the library is missing this module raises -- there is no CPU fallback.
+
+Transforms (the improved QFT of Pasquini, arXiv 1301.0763, Sec. 5):
+  fft(x)        X(k) = sum_n x(n) e^{-2 pi i n k/N}       (eq qft_0A), complex
+  ifft(X)       x = swap(DFT(swap X))/N                    (1/N scaled inverse)
+  rfft(x)       real [.., N] -> complex [.., N/2+1]        (rdft of Sec. 4.2)
+  irfft(Y, n)   complex [.., N/2+1] -> real [.., N]        (1/N scaled)
+All four are differentiable (torch.autograd.Function); their backward passes
+call the library's adjoint kernels and store nothing but the plan.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_qft_gb300.so")
+
+KIND_C2C, KIND_R2C = 0, 1
+DTYPE_F32, DTYPE_F16, DTYPE_BF16 = 0, 1, 2
+OP_FORWARD, OP_INVERSE, OP_FORWARD_ADJOINT, OP_INVERSE_ADJOINT = 0, 1, 2, 3
+
+_lib = None
+_lock = threading.Lock()
+
+
+class QFTError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})" if what else status_string(status))
+
+
+def load_library(path: str | None = None):
+    """Load the CUDA library (once).  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build it with `python -m paper_1301_0763_gb300.build` "
+                "(nvcc, sm_103a). There is no CPU fallback.")
+        lib = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        ci = ctypes.c_int
+        lib.qft_plan_create.argtypes = [ctypes.POINTER(vp), i64, i64, ci, ci, ctypes.c_uint]
+        lib.qft_plan_create_ragged.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                                               i64, ci, ci, ctypes.c_uint]
+        lib.qft_execute.argtypes = [vp, ci, vp, vp, vp]
+        for f in (lib.qft_execute_forward, lib.qft_execute_inverse, lib.qft_execute_backward):
+            f.argtypes = [vp, vp, vp, vp]
+        lib.qft_plan_destroy.argtypes = [vp]
+        lib.qft_plan_sync_status.argtypes = [vp]
+        lib.qft_plan_last_cuda_error.argtypes = [vp]
+        lib.qft_plan_info.argtypes = [vp] + [ctypes.POINTER(ci)] * 4
+        lib.qft_status_string.argtypes = [ci]
+        lib.qft_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    return load_library().qft_status_string(int(status)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise QFTError(rc, what)
+
+
+def _stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Plan:
+    """A plan of `batch` transforms of length `n` (see qft_plan_create)."""
+
+    def __init__(self, n: int, batch: int, kind: int = KIND_C2C, dtype: int = DTYPE_F32, device=None):
+        self.lib = load_library()
+        self.n, self.batch, self.kind, self.dtype = int(n), int(batch), int(kind), int(dtype)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.qft_plan_create(ctypes.byref(self.handle), self.n, self.batch, self.kind,
+                                            self.dtype, 0), "qft_plan_create")
+
+    def execute(self, op: int, inp: torch.Tensor, out: torch.Tensor, stream=None):
+        with torch.cuda.device(self.device):
+            _check(self.lib.qft_execute(self.handle, int(op), ctypes.c_void_p(inp.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_handle(stream))),
+                   "qft_execute")
+        return out
+
+    def info(self):
+        t, c, s, l = (ctypes.c_int() for _ in range(4))
+        _check(self.lib.qft_plan_info(self.handle, ctypes.byref(t), ctypes.byref(c), ctypes.byref(s),
+                                      ctypes.byref(l)), "qft_plan_info")
+        return {"threads": t.value, "ctas": c.value, "smem": s.value, "launches": l.value}
+
+    def sync_status(self) -> int:
+        return int(self.lib.qft_plan_sync_status(self.handle))
+
+    def destroy(self):
+        if self.handle and self.handle.value:
+            self.lib.qft_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+_plans: dict = {}
+
+
+def get_plan(n: int, batch: int, kind: int, dtype: int, device: torch.device) -> Plan:
+    key = (n, batch, kind, dtype, device.index)
+    p = _plans.get(key)
+    if p is None:
+        p = Plan(n, batch, kind, dtype, device)
+        _plans[key] = p
+    return p
+
+
+def _rows(x: torch.Tensor, last: int):
+    return x.numel() // last if last else 0
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype in (torch.complex64, torch.float32):
+        return DTYPE_F32
+    if t.dtype == torch.complex32:
+        return DTYPE_F16
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _need_cuda(x: torch.Tensor):
+    if not x.is_cuda:
+        raise ValueError("the improved-QFT library runs on CUDA tensors only (no CPU fallback)")
+
+
+def _c2c(x: torch.Tensor, op: int) -> torch.Tensor:
+    _need_cuda(x)
+    x = x.contiguous()
+    n = x.shape[-1]
+    out = torch.empty_like(x)
+    get_plan(n, _rows(x, n), KIND_C2C, _dtype_code(x), x.device).execute(op, x, out)
+    return out
+
+
+def fft_bf16(x: torch.Tensor, op: int = OP_FORWARD) -> torch.Tensor:
+    """C2C on bf16 storage: x is a real tensor [..., N, 2] of dtype bfloat16 (re, im)."""
+    _need_cuda(x)
+    assert x.dtype == torch.bfloat16 and x.shape[-1] == 2
+    x = x.contiguous()
+    n = x.shape[-2]
+    out = torch.empty_like(x)
+    get_plan(n, x.numel() // (2 * n), KIND_C2C, DTYPE_BF16, x.device).execute(op, x, out)
+    return out
+
+
+def _real_fwd(x: torch.Tensor, op: int) -> torch.Tensor:
+    _need_cuda(x)
+    x = x.contiguous()
+    assert x.dtype == torch.float32
+    n = x.shape[-1]
+    out = torch.empty(x.shape[:-1] + (n // 2 + 1,), dtype=torch.complex64, device=x.device)
+    get_plan(n, _rows(x, n), KIND_R2C, DTYPE_F32, x.device).execute(op, x, out)
+    return out
+
+
+def _real_inv(Y: torch.Tensor, n: int, op: int) -> torch.Tensor:
+    _need_cuda(Y)
+    Y = Y.contiguous()
+    assert Y.dtype == torch.complex64 and Y.shape[-1] == n // 2 + 1
+    out = torch.empty(Y.shape[:-1] + (n,), dtype=torch.float32, device=Y.device)
+    get_plan(n, _rows(Y, n // 2 + 1), KIND_R2C, DTYPE_F32, Y.device).execute(op, Y, out)
+    return out
+
+
+class _FFT(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x):
+        return _c2c(x, OP_FORWARD)
+
+    @staticmethod
+    def backward(ctx, g):
+        return _c2c(g, OP_FORWARD_ADJOINT)
+
+
+class _IFFT(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X):
+        return _c2c(X, OP_INVERSE)
+
+    @staticmethod
+    def backward(ctx, g):
+        return _c2c(g, OP_INVERSE_ADJOINT)
+
+
+class _RFFT(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x):
+        ctx.n = x.shape[-1]
+        return _real_fwd(x, OP_FORWARD)
+
+    @staticmethod
+    def backward(ctx, g):
+        return _real_inv(g, ctx.n, OP_FORWARD_ADJOINT)
+
+
+class _IRFFT(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, Y, n):
+        return _real_inv(Y, n, OP_INVERSE)
+
+    @staticmethod
+    def backward(ctx, g):
+        return _real_fwd(g, OP_INVERSE_ADJOINT), None
+
+
+def fft(x: torch.Tensor) -> torch.Tensor:
+    """Forward DFT along the last dim (complex64 or complex32 storage)."""
+    return _FFT.apply(x)
+
+
+def ifft(X: torch.Tensor) -> torch.Tensor:
+    """Inverse DFT along the last dim, 1/N scaled."""
+    return _IFFT.apply(X)
+
+
+def rfft(x: torch.Tensor) -> torch.Tensor:
+    """Real-input DFT along the last dim: [..., N] float32 -> [..., N/2+1] complex64."""
+    return _RFFT.apply(x)
+
+
+def irfft(Y: torch.Tensor, n: int) -> torch.Tensor:
+    """Inverse of rfft: [..., N/2+1] complex64 -> [..., n] float32 (1/n scaled)."""
+    return _IRFFT.apply(Y, n)
