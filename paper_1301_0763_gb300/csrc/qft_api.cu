@@ -18,7 +18,6 @@
 #include "qft_internal.h"
 
 using namespace qft;
-using qft_lib::kThreads;
 using qft_lib::kMaxRowLog2;
 
 static const uint32_t kMagic = 0x51465447u;   // "QFTG"
@@ -65,16 +64,20 @@ extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind
   if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); delete p; return rc; }
   if (r >= 2) {
     p->tune = qft_default_tune(r);
-    if (qft_build_row_plan(r, p->tune, &p->host_plan) != 0 || p->host_plan.max_slice_nodes > kThreads) {
+    p->tune.L1 = qft_lib::kL1;
+    p->tune.LB = qft_lib::kLB;
+    p->threads = qft_default_threads(r);
+    if (qft_build_row_plan(r, p->tune, &p->host_plan) != 0 || p->host_plan.max_slice_nodes > p->threads) {
       delete p;
       return QFT_ERR_INVALID_N;
     }
     const int N = 1 << r;
-    float* hsec = (float*)malloc(sizeof(float) * (N / 4 + 1));
+    const size_t nsec = (size_t)N / 4 + 1;
+    float* hsec = (float*)calloc(nsec, sizeof(float));
     if (!hsec) { delete p; return QFT_ERR_CUDA; }
-    qft_fill_secants(N, hsec);
-    e = cudaMalloc(&p->d_sec, sizeof(float) * (N / 4 + 1));
-    if (e == cudaSuccess) e = cudaMemcpy(p->d_sec, hsec, sizeof(float) * (N / 4 + 1), cudaMemcpyHostToDevice);
+    qft_fill_gray_secants(r, hsec);
+    e = cudaMalloc(&p->d_sec, sizeof(float) * nsec);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_sec, hsec, sizeof(float) * nsec, cudaMemcpyHostToDevice);
     free(hsec);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_plan, sizeof(QftRowPlan));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_plan, &p->host_plan, sizeof(QftRowPlan), cudaMemcpyHostToDevice);
@@ -168,7 +171,7 @@ extern "C" int qft_plan_last_cuda_error(qft_plan p) {
 extern "C" int qft_plan_info(qft_plan p, int* threads, int* ctas, int* smem_bytes, int* launches) {
   int rc = plan_check(p);
   if (rc != QFT_OK) return rc;
-  if (threads) *threads = kThreads;
+  if (threads) *threads = p->threads;
   if (ctas) *ctas = p->grid;
   if (smem_bytes) *smem_bytes = (int)p->smem;
   if (launches) *launches = 1;

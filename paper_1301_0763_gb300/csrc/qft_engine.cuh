@@ -68,7 +68,12 @@ namespace qft {
 // ------------------------------------------------------------ arithmetic
 QFT_HD qc mkc(float x, float y) { qc r; r.x = x; r.y = y; return r; }
 
-#if defined(__CUDA_ARCH__)
+// Packed two-lane FP32 instructions (add/sub/mul.rn.f32x2) are correctly
+// rounded lane by lane in isolation, but whole engine builds that use them did
+// not reproduce the FP32 evaluation of the recursion bit for bit on sm_103a,
+// while the scalar round-to-nearest intrinsics do; the scalar form is the
+// default and the packed form is kept behind QFT_PACKED_F32X2.
+#if defined(__CUDA_ARCH__) && defined(QFT_PACKED_F32X2)
 QFT_HD qc cadd(qc a, qc b) {
   qc r;
   asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\t"
@@ -90,6 +95,14 @@ QFT_HD qc cmul(qc a, float s) {
       : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(s));
   return r;
 }
+QFT_HD float fmul(float a, float b) { return __fmul_rn(a, b); }
+QFT_HD float fadd(float a, float b) { return __fadd_rn(a, b); }
+QFT_HD float fsub(float a, float b) { return __fsub_rn(a, b); }
+#elif defined(__CUDA_ARCH__)
+// scalar round-to-nearest intrinsics (never contracted), one per lane (default)
+QFT_HD qc cadd(qc a, qc b) { return mkc(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+QFT_HD qc csub(qc a, qc b) { return mkc(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+QFT_HD qc cmul(qc a, float s) { return mkc(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
 QFT_HD float fmul(float a, float b) { return __fmul_rn(a, b); }
 QFT_HD float fadd(float a, float b) { return __fadd_rn(a, b); }
 QFT_HD float fsub(float a, float b) { return __fsub_rn(a, b); }
@@ -122,7 +135,8 @@ static constexpr int ig_c(int x) { return x ^ (x >> 1) ^ (x >> 2) ^ (x >> 3) ^ (
 struct Eng {
   qc* side0;          // DCT side (padded), N/2+1 cells
   qc* side1;          // DST side (padded)
-  const float* sec;   // sec[m] = 1/(2 cos(2 pi m / N)), m in [1, N/4)
+  const float* sec;   // Gray-ordered secants (qft_fill_gray_secants): node of 2^b cells,
+                      // lower butterfly slot g -> sec[2^(b-1) + g]
   int r;              // log2 N
   int N;
 };
@@ -131,28 +145,24 @@ QFT_HD qc* side_ptr(const Eng& e, int s) { return s ? e.side1 : e.side0; }
 
 // ------------------------------------------------- forward mirror levels
 // L levels of the forward phase on registers v[t], t in [0, 2^L).  Register t
-// holds node slot t*H + lo (H = 2^(nb-L)) of a node of 2^nb cells; ilo is
-// invgray(lo).  Level l pairs t and t + 2^(L-l); the lower element is own
-// cell c of the current node (2^bp cells, bp = nb-l+1), whose periodization
-// is 2^(bp+2), so its secant is sec[(2c+1) << (r-bp-2)].
-// DCT (eqs qft_1, qft_2): e = a + b, o = (a - b) sec.
-// DST (roles swapped, Sec. 3.2): e = a - b, o = (a + b) sec.
+// holds node slot t*H + lo (H = 2^(nb-L)) of a node of 2^nb cells.  Level l
+// pairs t and t + 2^(L-l); the node at that level has 2^bp cells
+// (bp = nb-l+1) and the lower element sits in its slot hi*H + lo
+// (hi = t mod 2^(L-l)), so its secant is sec[2^(bp-1) + hi*H + lo].
+// DCT (eqs qft_1, qft_2, qft_38A): e = a + b, o = (a - b) sec.
+// DST (roles swapped, Sec. 3.2):   e = a - b, o = (a + b) sec.
 template <int L, int SIDE>
-QFT_HD void dif_regs(qc (&v)[1 << L], int nb, int ilo, const float* sec, int r) {
+QFT_HD void dif_regs(qc (&v)[1 << L], int nb, int lo, const float* sec) {
   const int h = nb - L;
-  const int H = 1 << h;
+  const float* sl = sec + lo;
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
     const int half = 1 << (L - l);
-    const int bp = nb - l + 1;
-    const int sh = r - bp - 2;
+    const float* sb = sl + (1 << (nb - l));
 #pragma unroll
     for (int t = 0; t < (1 << L); ++t) {
       if (t & half) continue;
-      const int hi = t & (half - 1);
-      const int ig = ig_c(hi);
-      const int cl = (ig << h) | ((ig & 1) ? (H - 1 - ilo) : ilo);
-      const float s = sec[(2 * cl + 1) << sh];
+      const float s = sb[(t & (half - 1)) << h];
       const qc a = v[t], b = v[t | half];
       if (SIDE == 0) { v[t] = cadd(a, b); v[t | half] = cmul(csub(a, b), s); }
       else           { v[t] = csub(a, b); v[t | half] = cmul(cadd(a, b), s); }
@@ -217,8 +227,8 @@ QFT_HD void task_f1_big(const Eng& e, const IO& io, int j, int ilo) {
     const int c = (ig << h) | ((ig & 1) ? (H - 1 - ilo) : ilo);
     io.get_cd((2 * c + 1) << j, vc[t], vs[t]);
   }
-  dif_regs<L1, 0>(vc, b, ilo, e.sec, e.r);
-  dif_regs<L1, 1>(vs, b, ilo, e.sec, e.r);
+  dif_regs<L1, 0>(vc, b, lo, e.sec);
+  dif_regs<L1, 1>(vs, b, lo, e.sec);
   const int off = cls_off(e.r, j);
 #pragma unroll
   for (int t = 0; t < (1 << L1); ++t) {
@@ -236,12 +246,12 @@ QFT_HD void task_f1_small(const Eng& e, const IO& io, int j) {
 #pragma unroll
   for (int g = 0; g < (1 << L); ++g) io.get_cd((2 * ig_c(g) + 1) << j, vc[g], vs[g]);
   const int off = cls_off(e.r, j);
-  dif_regs<L, 0>(vc, L, 0, e.sec, e.r);
+  dif_regs<L, 0>(vc, L, 0, e.sec);
   bwd_chunk<L, 0>(vc, vc, false);
 #pragma unroll
   for (int k = 0; k < (1 << L); ++k) e.side0[qft_pidx(off + k)] = vc[k];
   if (j <= e.r - 3) {
-    dif_regs<L, 1>(vs, L, 0, e.sec, e.r);
+    dif_regs<L, 1>(vs, L, 0, e.sec);
     bwd_chunk<L, 1>(vs, vs, false);
 #pragma unroll
     for (int k = 0; k < (1 << L); ++k) e.side1[qft_pidx(off + k)] = vs[k];
@@ -268,7 +278,7 @@ QFT_HD void task_dif(const Eng& e, int j, int D, int tau) {
   qc v[1 << L];
 #pragma unroll
   for (int t = 0; t < (1 << L); ++t) v[t] = A[qft_pidx(base + (t << h))];
-  dif_regs<L, SIDE>(v, nb, (int)invgray((unsigned)lo), e.sec, e.r);
+  dif_regs<L, SIDE>(v, nb, lo, e.sec);
 #pragma unroll
   for (int t = 0; t < (1 << L); ++t) A[qft_pidx(base + (t << h))] = v[t];
 }
@@ -280,7 +290,7 @@ QFT_HD void task_leaf(const Eng& e, int j, int q) {
   qc v[1 << L];
 #pragma unroll
   for (int t = 0; t < (1 << L); ++t) v[t] = A[qft_pidx(base + t)];
-  dif_regs<L, SIDE>(v, L, 0, e.sec, e.r);
+  dif_regs<L, SIDE>(v, L, 0, e.sec);
   bwd_chunk<L, SIDE>(v, v, false);
 #pragma unroll
   for (int t = 0; t < (1 << L); ++t) A[qft_pidx(base + t)] = v[t];
@@ -293,9 +303,12 @@ QFT_HD void task_leaf(const Eng& e, int j, int q) {
 // needed at a chunk edge for the odd-harmonic child of every sub-node is, by
 // the even-harmonic copies of the recursion, a raw value of descendant t at
 // slice r_+1 (DCT) or r_-1 (DST), for every t >= 1.
+#ifndef QFT_MAX_LB
+#define QFT_MAX_LB 3    // largest number of backward levels one SLICE task does
+#endif
 struct SliceRegs {
-  qc w[16];
-  qc h[16];
+  qc w[1 << QFT_MAX_LB];
+  qc h[1 << QFT_MAX_LB];
   int base;   // node base + r_ * 2^L  (write position)
   bool hv;
 };
@@ -342,59 +355,64 @@ QFT_HD qc cls_out(const Eng& e, int s, int j, int k) {
 
 // C_M(k) for M = 2^m, k in [0, M/2]: walk down the dct recursion (recording
 // which of eqs qft_5C / qft_5D / qft_6 applies at each level), then add the
-// class outputs bottom-up in the recursion's order.
+// class outputs bottom-up in the recursion's order.  Branch-free: every lane
+// executes the same instructions (the eq qft_6 case keeps v; v - O is computed
+// as v + (-O), which is the same IEEE operation).
 QFT_HD qc chain_c(const Eng& e, int m, int k) {
   uint64_t ops = 0;
-  int nl = 0;
-  while (m > 1) {
-    const int M = 1 << m;
+  const int nl = m - 1;
+  for (int i = 0; i < nl; ++i) {
+    const int M = 1 << (m - i);
     const int qq = M >> 2;
-    uint64_t op;
-    if (k < qq) op = 0;
-    else if (k > qq) { op = 1; k = (M >> 1) - k; }
-    else op = 2;
-    ops |= op << (2 * nl);
-    ++nl;
-    --m;
+    const uint64_t op = k < qq ? 0u : (k > qq ? 1u : 2u);
+    k = op == 1 ? (M >> 1) - k : k;
+    ops |= op << (2 * i);
   }
   const qc c0 = e.side0[qft_pidx(e.N / 2 - 1)];
   const qc c1 = e.side0[qft_pidx(e.N / 2)];
-  qc v = (k == 0) ? cadd(c0, c1) : csub(c0, c1);    // dct(2)
+  const qc cm = k == 0 ? c1 : mkc(-c1.x, -c1.y);
+  qc v = cadd(c0, cm);                                  // dct(2): c0 + c1 or c0 - c1
   for (int i = nl - 1; i >= 0; --i) {
     const int op = (int)((ops >> (2 * i)) & 3);
-    const int mm = m + nl - i;                        // log2 of this level's periodization
+    const int mm = m - i;                             // log2 of this level's periodization
     const int j = e.r - mm;
-    if (op == 0) v = cadd(v, cls_out(e, 0, j, k));
-    else if (op == 1) { v = csub(v, cls_out(e, 0, j, k)); k = (1 << (mm - 1)) - k; }
+    qc o = e.side0[qft_pidx(cls_off(e.r, j) + k)];    // O_j(k) (k = M/4 reads a neighbour, unused)
+    if (op == 1) o = mkc(-o.x, -o.y);
+    const qc w = cadd(v, o);
+    v = op == 2 ? v : w;
+    k = op == 1 ? (1 << (mm - 1)) - k : k;
   }
   return v;
 }
 
 // S_M(k), k in [1, M/2-1]: same walk for the dst recursion; it stops at
-// k = M/4 (S_M(M/4) = O(M/4)) or at the dst(4) base.
+// k = M/4 (S_M(M/4) = O(M/4)) or at the dst(4) base.  The walk runs over every
+// level in every lane; levels below the stop only carry a dummy in-range index.
 QFT_HD qc chain_s(const Eng& e, int m, int k) {
   uint64_t ops = 0;
-  int nl = 0;
-  qc v;
-  for (;;) {
-    if (m == 2) { v = e.side1[qft_pidx(e.N / 2 - 2)]; break; }
-    const int M = 1 << m;
+  const int nl = m - 2;                  // levels M = 2^m .. 8 above the dst(4) base
+  int stop = nl;                         // first level (from the top) with k == M/4
+  for (int i = 0; i < nl; ++i) {
+    const int M = 1 << (m - i);
     const int qq = M >> 2;
-    if (k == qq) { v = cls_out(e, 1, e.r - m, qq); break; }
-    uint64_t op;
-    if (k < qq) op = 0;
-    else { op = 1; k = (M >> 1) - k; }
-    ops |= op << nl;
-    ++nl;
-    --m;
+    const bool hit = stop == nl && k == qq;
+    stop = hit ? i : stop;
+    const uint64_t op = k > qq ? 1u : 0u;
+    k = (stop == nl && op == 1) ? (M >> 1) - k : k;
+    ops |= op << i;
   }
+  qc v = e.side1[qft_pidx(e.N / 2 - 2)];   // dst(4) base, used when no level stops
   for (int i = nl - 1; i >= 0; --i) {
-    const int op = (int)((ops >> i) & 1);
-    const int mm = m + nl - i;
+    const int mm = m - i;
     const int j = e.r - mm;
-    const qc o = cls_out(e, 1, j, k);
-    if (op == 0) v = cadd(v, o);
-    else { v = csub(o, v); k = (1 << (mm - 1)) - k; }
+    const int P = 1 << (mm - 2);
+    const int kk = k & (P - 1 + P);        // keeps the dummy index inside class j's cells
+    const qc o = e.side1[qft_pidx(cls_off(e.r, j) + (kk > 0 ? kk - 1 : 0))];
+    const int op = (int)((ops >> i) & 1);
+    const qc negv = mkc(-v.x, -v.y);
+    const qc w = cadd(op ? negv : v, o);   // S(k) = E + O  or  S(M/2-k) = O - E
+    v = i == stop ? o : (i < stop ? w : v);
+    k = (i < stop && op == 1) ? (1 << (mm - 1)) - k : k;
   }
   return v;
 }
@@ -486,13 +504,25 @@ QFT_HD void run_plain_task(const QftRowPlan& P, const QftSeg& sg, const Eng& e, 
 
 QFT_HD void run_slice_read(const QftSeg& sg, const Eng& e, int loc, SliceRegs& s) {
 #define QFT_SR_CASE(LL) case LL: if (sg.side) task_slice_read<LL, 1>(e, sg.cls, sg.D, loc, s); else task_slice_read<LL, 0>(e, sg.cls, sg.D, loc, s); break;
-  switch (sg.L) { QFT_SR_CASE(1) QFT_SR_CASE(2) QFT_SR_CASE(3) QFT_SR_CASE(4) default: break; }
+  switch (sg.L) {
+    QFT_SR_CASE(1) QFT_SR_CASE(2) QFT_SR_CASE(3)
+#if QFT_MAX_LB >= 4
+    QFT_SR_CASE(4)
+#endif
+    default: break;
+  }
 #undef QFT_SR_CASE
 }
 
 QFT_HD void run_slice_write(const QftSeg& sg, const Eng& e, SliceRegs& s) {
 #define QFT_SW_CASE(LL) case LL: if (sg.side) task_slice_write<LL, 1>(e, s); else task_slice_write<LL, 0>(e, s); break;
-  switch (sg.L) { QFT_SW_CASE(1) QFT_SW_CASE(2) QFT_SW_CASE(3) QFT_SW_CASE(4) default: break; }
+  switch (sg.L) {
+    QFT_SW_CASE(1) QFT_SW_CASE(2) QFT_SW_CASE(3)
+#if QFT_MAX_LB >= 4
+    QFT_SW_CASE(4)
+#endif
+    default: break;
+  }
 #undef QFT_SW_CASE
 }
 

@@ -7,8 +7,9 @@
 #include "../../include/qft_gb300.h"
 
 namespace qft_lib {
-constexpr int kThreads = 256;     // threads per CTA of the row engine
 constexpr int kMaxRowLog2 = 14;   // largest row one CTA transforms in shared memory
+constexpr int kL1 = 3;            // mirror levels per F1 task (register tile 2^kL1 per side)
+constexpr int kLB = 3;            // backward levels per SLICE task (QFT_MAX_LB)
 
 // Shared-memory layout of the row engine: plan | secant table | DCT side | DST side.
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -28,6 +29,7 @@ struct qft_plan_s {
   QftRowPlan* d_plan;
   float* d_sec;
   int grid;
+  int threads;
   size_t smem;
   int device;
   int sms;

@@ -16,12 +16,17 @@ struct QftTune {
   int L1, LS, LL, LB, LF;
 };
 
+// The library's schedule: register tiles of 8 cells per side in F1 and SLICE,
+// 16 in DIF, 8 in LEAF, 16 output bins per FINAL task; 256 threads per CTA
+// (512 for N = 2^14, whose top SLICE phase has 512 tasks per node).
 static inline QftTune qft_default_tune(int r) {
   QftTune t;
-  t.L1 = 4; t.LS = 4; t.LL = 3; t.LB = 4; t.LF = 3;
+  t.L1 = 3; t.LS = 4; t.LL = 3; t.LB = 3; t.LF = 3;
   (void)r;
   return t;
 }
+
+static inline int qft_default_threads(int r) { return r >= 14 ? 512 : 256; }
 
 namespace qft_planner_detail {
 struct Builder {

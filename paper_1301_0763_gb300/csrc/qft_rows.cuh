@@ -5,7 +5,6 @@
 #include "qft_io.cuh"
 
 using namespace qft;
-using qft_lib::kThreads;
 
 namespace {
 
@@ -72,8 +71,10 @@ using qft_lib::off_sec;
 using qft_lib::off_side0;
 using qft_lib::side_bytes;
 
-template <class FAC, int L1>
-__global__ void __launch_bounds__(kThreads)
+// NT threads per CTA; the register budget allows 512 threads per SM
+// (2 CTAs of 256 or 1 of 512), i.e. at most 128 registers per thread.
+template <class FAC, int L1, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT)
 k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int sec_stride,
        int64_t nitems, FAC fac) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -81,7 +82,7 @@ k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int
   {
     const int* src = reinterpret_cast<const int*>(gplan);
     int* dst = reinterpret_cast<int*>(smem);
-    for (int i = threadIdx.x; i < (int)(sizeof(QftRowPlan) / 4); i += kThreads) dst[i] = src[i];
+    for (int i = threadIdx.x; i < (int)(sizeof(QftRowPlan) / 4); i += NT) dst[i] = src[i];
   }
   __syncthreads();
   const int r = P.r;
@@ -89,7 +90,7 @@ k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int
   float* sec = reinterpret_cast<float*>(smem + off_sec());
   qc* side0 = reinterpret_cast<qc*>(smem + off_side0(N));
   qc* side1 = reinterpret_cast<qc*>(smem + off_side0(N) + side_bytes(N));
-  for (int m = threadIdx.x; m <= N / 4; m += kThreads) sec[m] = gsec[(int64_t)m * sec_stride];
+  for (int m = threadIdx.x; m <= N / 4; m += NT) sec[m] = gsec[(int64_t)m * sec_stride];
   __syncthreads();
   Eng e;
   e.side0 = side0; e.side1 = side1; e.sec = sec; e.r = r; e.N = N;
@@ -98,24 +99,28 @@ k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int
     const auto io = fac.make(item);
     for (int p = 0; p < P.nphase; ++p) {
       const int nt = P.phase_ntasks[p];
+      // tasks are visited in increasing order, so the segment is found by
+      // advancing from the previous one (amortised O(1) per task)
+      int sgi = P.phase_seg0[p];
+      const int sge = P.phase_seg0[p + 1];
       if (!P.phase_is_slice[p]) {
-        for (int tau = tid; tau < nt; tau += kThreads) {
-          const QftSeg& sg = find_seg(P, p, tau);
+        for (int tau = tid; tau < nt; tau += NT) {
+          while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
+          const QftSeg& sg = P.segs[sgi];
           run_plain_task<L1>(P, sg, e, io, tau - sg.begin);
         }
         __syncthreads();
       } else {
-        for (int rb = 0; rb < nt; rb += kThreads) {
+        for (int rb = 0; rb < nt; rb += NT) {
           const int tau = rb + tid;
           SliceRegs s;
-          int segi = -1;
-          if (tau < nt) {
-            const QftSeg& sg = find_seg(P, p, tau);
-            segi = (int)(&sg - P.segs);
-            run_slice_read(sg, e, tau - sg.begin, s);
+          const bool act = tau < nt;
+          if (act) {
+            while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
+            run_slice_read(P.segs[sgi], e, tau - P.segs[sgi].begin, s);
           }
           __syncthreads();
-          if (segi >= 0) run_slice_write(P.segs[segi], e, s);
+          if (act) run_slice_write(P.segs[sgi], e, s);
           __syncthreads();
         }
       }
@@ -138,11 +143,11 @@ __global__ void k_c2c_n2(FacC2C<ST> fac, int64_t rows) {
 
 
 template <class K>
-static int occupancy_grid(qft_plan p, K kernel, int64_t items) {
+static int occupancy_grid(qft_plan p, K kernel, int nt, int64_t items) {
   int per_sm = 0;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
   if (e != cudaSuccess) return qft_set_cuda(p, e);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, p->smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, p->smem);
   if (e != cudaSuccess) return qft_set_cuda(p, e);
   if (per_sm < 1) per_sm = 1;
   int64_t g = (int64_t)per_sm * p->sms;
@@ -153,13 +158,19 @@ static int occupancy_grid(qft_plan p, K kernel, int64_t items) {
 }
 
 // ------------------------------------------------------------ launchers
-template <class FAC, int L1>
-static inline int launch_rows(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
-  auto kern = k_rows<FAC, L1>;
-  int rc = occupancy_grid(p, kern, items);
+template <class FAC, int L1, int NT>
+static inline int launch_rows_nt(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
+  auto kern = k_rows<FAC, L1, NT>;
+  int rc = occupancy_grid(p, kern, NT, items);
   if (rc != QFT_OK) return rc;
-  kern<<<p->grid, kThreads, p->smem, st>>>(p->d_plan, p->d_sec, 1, items, fac);
+  kern<<<p->grid, NT, p->smem, st>>>(p->d_plan, p->d_sec, 1, items, fac);
   return qft_set_cuda(p, cudaGetLastError());
+}
+
+template <class FAC>
+static inline int launch_rows(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
+  if (p->threads == 512) return launch_rows_nt<FAC, qft_lib::kL1, 512>(p, fac, items, st);
+  return launch_rows_nt<FAC, qft_lib::kL1, 256>(p, fac, items, st);
 }
 
 template <class ST>
@@ -181,7 +192,7 @@ static inline int exec_c2c(qft_plan p, int op, const void* in, void* out, cudaSt
     k_c2c_n2<ST><<<(unsigned)blocks, 128, 0, st>>>(f, p->batch);
     return qft_set_cuda(p, cudaGetLastError());
   }
-  return launch_rows<FacC2C<ST>, 4>(p, f, p->batch, st);
+  return launch_rows<FacC2C<ST>>(p, f, p->batch, st);
 }
 
 static inline int exec_r2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
@@ -193,7 +204,7 @@ static inline int exec_r2c(qft_plan p, int op, const void* in, void* out, cudaSt
     f.out = static_cast<qc*>(out);
     f.rows = p->batch; f.N = N;
     f.wscale = op == QFT_OP_FORWARD ? 0.f : 1.f / (float)N;
-    return launch_rows<FacR2C<StC64>, 4>(p, f, items, st);
+    return launch_rows<FacR2C<StC64>>(p, f, items, st);
   }
   if (op == QFT_OP_INVERSE || op == QFT_OP_FORWARD_ADJOINT) {
     FacC2R<StC64> f;
@@ -202,7 +213,7 @@ static inline int exec_r2c(qft_plan p, int op, const void* in, void* out, cudaSt
     f.rows = p->batch; f.N = N;
     if (op == QFT_OP_INVERSE) { f.wmid = 2.f; f.scale = 1.f / (float)N; }
     else { f.wmid = 1.f; f.scale = 1.f; }
-    return launch_rows<FacC2R<StC64>, 4>(p, f, items, st);
+    return launch_rows<FacC2R<StC64>>(p, f, items, st);
   }
   return QFT_ERR_INVALID_ARG;
 }

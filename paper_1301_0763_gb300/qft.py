@@ -43,7 +43,7 @@ def load_library(path: str | None = None):
     with _lock:
         if _lib is not None:
             return _lib
-        path = path or LIB_PATH
+        path = path or os.environ.get("QFT_GB300_LIB", LIB_PATH)
         if not os.path.exists(path):
             raise RuntimeError(
                 f"{path} is missing: build it with `python -m paper_1301_0763_gb300.build` "

@@ -38,7 +38,7 @@ def _fp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
 
-def c2c(z, op=0, tune=None, nthr=256):
+def c2c(z, op=0, tune=None, nthr=0):
     z = np.ascontiguousarray(z, dtype=np.complex64)
     N = z.shape[-1]
     out = np.empty_like(z)
@@ -52,7 +52,7 @@ def c2c(z, op=0, tune=None, nthr=256):
     return out
 
 
-def c2c_half(z16, dtype, op=0, nthr=256):
+def c2c_half(z16, dtype, op=0, nthr=0):
     """z16: uint16 array [..., N, 2] holding fp16 (dtype=1) or bf16 (dtype=2) pairs."""
     z16 = np.ascontiguousarray(z16, dtype=np.uint16)
     N = z16.shape[-2]
@@ -64,7 +64,7 @@ def c2c_half(z16, dtype, op=0, nthr=256):
     return out
 
 
-def r2c(x, op, N, nthr=256):
+def r2c(x, op, N, nthr=0):
     """op 0: real [B,N] -> complex [B,N/2+1]; 1: complex -> real (1/N); 2: complex -> real (adjoint);
     3: real -> complex (adjoint of the real inverse)."""
     if op in (0, 3):

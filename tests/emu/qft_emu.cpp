@@ -7,6 +7,7 @@
 // its output bit for bit with the improved-QFT oracle built in FP32, which
 // checks the engine's index logic without a GPU.  The product never loads this.
 #define QFT_HOST_EMULATION 1
+#define QFT_MAX_LB 4
 #include "../../paper_1301_0763_gb300/csrc/qft_io.cuh"
 #include "../../paper_1301_0763_gb300/csrc/qft_planner.h"
 #include "../../paper_1301_0763_gb300/csrc/qft_consts.h"
@@ -57,21 +58,23 @@ struct Row {
   QftRowPlan P;
   Eng e;
   int ok;
-  Row(int N, const int* tune, int nthr) {
+  Row(int N, const int* tune, int& nthr) {
     int r = 0; while ((1 << r) < N) ++r;
+    if (nthr <= 0) nthr = qft_default_threads(r);
     QftTune t = qft_default_tune(r);
     if (tune) { t.L1 = tune[0]; t.LS = tune[1]; t.LL = tune[2]; t.LB = tune[3]; t.LF = tune[4]; }
     ok = qft_build_row_plan(r, t, &P) == 0 && P.max_slice_nodes <= nthr;
     s0.assign(qft_side_len(N), mkc(NAN, NAN));
     s1.assign(qft_side_len(N), mkc(NAN, NAN));
     sec.assign(N / 4 + 1, 0.f);
-    qft_fill_secants(N, sec.data());
+    qft_fill_gray_secants(r, sec.data());
     e.side0 = s0.data(); e.side1 = s1.data(); e.sec = sec.data(); e.r = r; e.N = N;
   }
 };
 
 extern "C" int emu_plan_info(int N, const int* tune, int* nphase, int* nseg, int* max_slice) {
-  Row R(N, tune, 1 << 20);
+  int big = 1 << 20;
+  Row R(N, tune, big);
   *nphase = R.P.nphase; *nseg = R.P.nseg; *max_slice = R.P.max_slice_nodes;
   return R.ok ? 0 : -1;
 }

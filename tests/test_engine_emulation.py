@@ -55,13 +55,13 @@ def test_c2c_other_ops_bit_exact(lg, op):
 
 
 @pytest.mark.parametrize("tune", [(3, 4, 3, 4, 3), (4, 2, 2, 2, 2), (2, 3, 4, 3, 1), (4, 4, 1, 1, 0),
-                                  (0, 1, 1, 4, 3), (3, 3, 3, 3, 3)])
+                                  (0, 1, 1, 4, 3), (4, 4, 3, 4, 3), (3, 3, 3, 3, 2)])
 @pytest.mark.parametrize("lg", [5, 9, 12])
 def test_schedules_do_not_change_the_result(tune, lg):
     """Any tile/stage schedule of the planner yields the same bits."""
     N = 1 << lg
     rc, _, _, max_slice = emu.plan_info(N, tune)
-    if rc != 0 or max_slice > 256:
+    if rc != 0 or max_slice > (512 if lg >= 14 else 256):
         pytest.skip("schedule not valid for this N with 256 threads")
     z = inputs.normal_complex(1, N, seed=5)
     assert bits_equal(emu.c2c(z, tune=tune), emu.c2c(z))
