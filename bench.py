@@ -164,7 +164,7 @@ SIZES_OVERRIDE = None
 
 def supported_logs():
     from paper_1301_0763_gb300 import qft  # noqa: F401  (library must load)
-    logs = [lg for lg in CONFIG_LOGS if lg <= 14]
+    logs = list(CONFIG_LOGS)
     if SIZES_OVERRIDE:
         logs = [lg for lg in SIZES_OVERRIDE if lg in logs]
     return logs

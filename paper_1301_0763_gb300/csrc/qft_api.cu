@@ -41,6 +41,15 @@ static int plan_check(qft_plan p) {
   return g_dead.count(p) ? QFT_ERR_DESTROYED : QFT_ERR_INVALID_ARG;
 }
 
+static void free_resources(qft_plan p) {
+  cudaFree(p->d_plan);
+  cudaFree(p->d_sec);
+  cudaFree(p->d_large);
+  cudaFree(p->scratch);
+  free(p->large_host);
+  p->d_plan = nullptr; p->d_sec = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->large_host = nullptr;
+}
+
 extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
   *out = nullptr;
@@ -52,13 +61,15 @@ extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind
   if (kind == QFT_KIND_R2C && n < 4) return QFT_ERR_INVALID_N;
   int r = 0;
   while ((int64_t(1) << r) < n) ++r;
-  if (r > kMaxRowLog2) return QFT_ERR_INVALID_N;
+  if (r > qft_lib::kMaxLog2) return QFT_ERR_INVALID_N;
   if (batch < 0 || batch > (int64_t(1) << 40)) return QFT_ERR_INVALID_BATCH;
 
   qft_plan p = new (std::nothrow) qft_plan_s();
   if (!p) return QFT_ERR_CUDA;
   p->magic = kMagic; p->kind = kind; p->dtype = dtype; p->n = n; p->batch = batch; p->r = r;
   p->d_plan = nullptr; p->d_sec = nullptr; p->last_cuda = cudaSuccess; p->last_stream = nullptr;
+  p->large_host = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->scratch_rows = 0; p->side_len = 0;
+  p->grid = 0; p->threads = 0; p->smem = 0;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); delete p; return rc; }
@@ -66,12 +77,8 @@ extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind
     p->tune = qft_default_tune(r);
     p->tune.L1 = qft_lib::kL1;
     p->tune.LB = qft_lib::kLB;
-    p->threads = qft_default_threads(r);
-    if (qft_build_row_plan(r, p->tune, &p->host_plan) != 0 || p->host_plan.max_slice_nodes > p->threads) {
-      delete p;
-      return QFT_ERR_INVALID_N;
-    }
-    const int N = 1 << r;
+    const int64_t N = int64_t(1) << r;
+    // FP32 secant table (Sec. 6.1), Gray order of the butterflies
     const size_t nsec = (size_t)N / 4 + 1;
     float* hsec = (float*)calloc(nsec, sizeof(float));
     if (!hsec) { delete p; return QFT_ERR_CUDA; }
@@ -79,16 +86,37 @@ extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind
     e = cudaMalloc(&p->d_sec, sizeof(float) * nsec);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_sec, hsec, sizeof(float) * nsec, cudaMemcpyHostToDevice);
     free(hsec);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_plan, sizeof(QftRowPlan));
-    if (e == cudaSuccess) e = cudaMemcpy(p->d_plan, &p->host_plan, sizeof(QftRowPlan), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      int rc = qft_set_cuda(p, e);
-      cudaFree(p->d_sec); cudaFree(p->d_plan); delete p;
-      return rc;
+    if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); delete p; return rc; }
+    if (r <= qft_lib::kMaxRowLog2) {
+      p->threads = qft_default_threads(r);
+      if (qft_build_row_plan(r, p->tune, &p->host_plan) != 0 || p->host_plan.max_slice_nodes > p->threads) {
+        free_resources(p); delete p;
+        return QFT_ERR_INVALID_N;
+      }
+      e = cudaMalloc(&p->d_plan, sizeof(QftRowPlan));
+      if (e == cudaSuccess) e = cudaMemcpy(p->d_plan, &p->host_plan, sizeof(QftRowPlan), cudaMemcpyHostToDevice);
+      p->smem = qft_lib::row_smem_bytes((int)N, p->host_plan.LF);
+    } else {
+      p->large_host = (QftLargePlan*)malloc(sizeof(QftLargePlan));
+      if (!p->large_host ||
+          qft_build_large_plan(r, p->tune, qft_lib::kNodeLog2, qft_lib::kNodeThreads, p->large_host) != 0) {
+        free_resources(p); delete p;
+        return QFT_ERR_INVALID_N;
+      }
+      e = cudaMalloc(&p->d_large, sizeof(QftLargePlan));
+      if (e == cudaSuccess) e = cudaMemcpy(p->d_large, p->large_host, sizeof(QftLargePlan), cudaMemcpyHostToDevice);
+      p->side_len = qft_side_len((int)N);
+      const int64_t items = kind == QFT_KIND_R2C ? (batch + 1) / 2 : batch;
+      const int64_t per_row = 2 * 2 * (int64_t)p->side_len * 8;
+      int64_t rows = qft_lib::kScratchBudget / per_row;
+      if (rows > items) rows = items;
+      if (rows > 65535) rows = 65535;
+      if (rows < 1) rows = 1;
+      p->scratch_rows = rows;
+      p->threads = 256;
+      if (e == cudaSuccess && items > 0) e = cudaMalloc(&p->scratch, (size_t)(rows * per_row));
     }
-    p->smem = qft_lib::row_smem_bytes(N);
-  } else {
-    p->smem = 0;
+    if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); delete p; return rc; }
   }
   register_plan(p);
   *out = p;
@@ -111,8 +139,7 @@ extern "C" int qft_plan_destroy(qft_plan p) {
     g_live.erase(p);
     g_dead.insert(p);
   }
-  cudaFree(p->d_plan);
-  cudaFree(p->d_sec);
+  free_resources(p);
   p->magic = kDead;
   delete p;
   return QFT_OK;
@@ -174,7 +201,7 @@ extern "C" int qft_plan_info(qft_plan p, int* threads, int* ctas, int* smem_byte
   if (threads) *threads = p->threads;
   if (ctas) *ctas = p->grid;
   if (smem_bytes) *smem_bytes = (int)p->smem;
-  if (launches) *launches = 1;
+  if (launches) *launches = p->large_host ? p->large_host->nphase : 1;
   return QFT_OK;
 }
 

@@ -139,6 +139,8 @@ struct Eng {
                       // lower butterfly slot g -> sec[2^(b-1) + g]
   int r;              // log2 N
   int N;
+  qc* tabC;           // C_Mt(k), k in [0, Mt/2]   (Mt = N >> LF), or null
+  qc* tabS;           // S_Mt(k), k in [1, Mt/2-1], or null
 };
 
 QFT_HD qc* side_ptr(const Eng& e, int s) { return s ? e.side1 : e.side0; }
@@ -417,14 +419,61 @@ QFT_HD qc chain_s(const Eng& e, int m, int k) {
   return v;
 }
 
+// Tables of C_Mt and S_Mt (Mt = N / 2^LF) for the FINAL tasks, built level by
+// level from the dct(2) / dst(4) base cases with the class outputs (eqs qft_5C,
+// qft_5D, qft_6 and their DST forms), in the same operation order as the
+// recursion.  tab_level_c(m) builds C_{2^m} from C_{2^(m-1)} in place
+// (m = 1 builds C_2 from c(0), c(N/2)); tab_level_s(m) builds S_{2^m}
+// (m = 2 is the dst(4) base).  Lanes split the k range; levels are separated
+// by a (warp) barrier.
+QFT_HD void tab_level_c(const Eng& e, int m, int lane, int nl) {
+  if (m == 1) {
+    if (lane == 0) {
+      const qc c0 = e.side0[qft_pidx(e.N / 2 - 1)], c1 = e.side0[qft_pidx(e.N / 2)];
+      e.tabC[0] = cadd(c0, c1);
+      e.tabC[1] = csub(c0, c1);
+    }
+    return;
+  }
+  const int M = 1 << m;
+  const int j = e.r - m;
+  for (int k = lane; k < M / 4; k += nl) {
+    const qc E = e.tabC[k];
+    const qc O = e.side0[qft_pidx(cls_off(e.r, j) + k)];
+    e.tabC[k] = cadd(E, O);
+    e.tabC[M / 2 - k] = csub(E, O);
+  }
+}
+
+QFT_HD void tab_level_s(const Eng& e, int m, int lane, int nl) {
+  if (m == 2) {
+    if (lane == 0) e.tabS[1] = e.side1[qft_pidx(e.N / 2 - 2)];
+    return;
+  }
+  const int M = 1 << m;
+  const int j = e.r - m;
+  for (int k = 1 + lane; k < M / 4; k += nl) {
+    const qc E = e.tabS[k];
+    const qc O = e.side1[qft_pidx(cls_off(e.r, j) + k - 1)];
+    e.tabS[k] = cadd(E, O);
+    e.tabS[M / 2 - k] = csub(O, E);
+  }
+  if (lane == 0) e.tabS[M / 4] = e.side1[qft_pidx(cls_off(e.r, j) + M / 4 - 1)];
+}
+
 // Regular frequency orbit: k0 in [1, N/2^(LF+1)).  The task builds C and S
 // on the orbit {+-k0 + m N/2^LF} level by level and emits X at 2^(LF+1) bins.
 template <int LF, class IO>
 QFT_HD void task_fin_reg(const Eng& e, const IO& io, int k0) {
   qc C[1 << LF], S[1 << LF];
   int K[1 << LF];
-  C[0] = chain_c(e, e.r - LF, k0);
-  S[0] = chain_s(e, e.r - LF, k0);
+  if (e.tabC) {
+    C[0] = e.tabC[k0];
+    S[0] = e.tabS[k0];
+  } else {
+    C[0] = chain_c(e, e.r - LF, k0);
+    S[0] = chain_s(e, e.r - LF, k0);
+  }
   K[0] = k0;
 #pragma unroll
   for (int l = LF; l >= 1; --l) {
@@ -456,6 +505,13 @@ QFT_HD void task_fin_spec(const Eng& e, const IO& io, int LF, int mi) {
 }
 
 // ------------------------------------------------------------ dispatch
+// IO of the node sub-plans of the large-row path (they have no F1 / FINAL tasks).
+struct NoIO {
+  QFT_HD void get_cd(int, qc& c, qc& d) const { c = mkc(0.f, 0.f); d = c; }
+  QFT_HD qc get_c(int) const { return mkc(0.f, 0.f); }
+  QFT_HD void emit(int, qc, qc) const {}
+};
+
 QFT_HD const QftSeg& find_seg(const QftRowPlan& P, int p, int tau) {
   int s = P.phase_seg0[p];
   const int e = P.phase_seg0[p + 1];
@@ -464,7 +520,7 @@ QFT_HD const QftSeg& find_seg(const QftRowPlan& P, int p, int tau) {
 }
 
 template <int L1, class IO>
-QFT_HD void run_plain_task(const QftRowPlan& P, const QftSeg& sg, const Eng& e, const IO& io, int loc) {
+QFT_HD void run_plain_task(int LF, const QftSeg& sg, const Eng& e, const IO& io, int loc) {
   switch (sg.type) {
   case QFT_SEG_F1_BIG: task_f1_big<L1>(e, io, sg.cls, loc); break;
   case QFT_SEG_F1_SMALL:
@@ -489,7 +545,7 @@ QFT_HD void run_plain_task(const QftRowPlan& P, const QftSeg& sg, const Eng& e, 
 #undef QFT_LEAF_CASE
     break;
   case QFT_SEG_FIN_REG:
-    switch (P.LF) {
+    switch (LF) {
     case 0: task_fin_reg<0>(e, io, loc + 1); break;
     case 1: task_fin_reg<1>(e, io, loc + 1); break;
     case 2: task_fin_reg<2>(e, io, loc + 1); break;
@@ -497,7 +553,7 @@ QFT_HD void run_plain_task(const QftRowPlan& P, const QftSeg& sg, const Eng& e, 
     default: break;
     }
     break;
-  case QFT_SEG_FIN_SPEC: task_fin_spec(e, io, P.LF, loc); break;
+  case QFT_SEG_FIN_SPEC: task_fin_spec(e, io, LF, loc); break;
   default: break;
   }
 }

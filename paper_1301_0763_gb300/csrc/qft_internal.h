@@ -6,8 +6,15 @@
 #include "qft_planner.h"
 #include "../../include/qft_gb300.h"
 
+// complex cell storage of the scratch copies (layout of qft::qc)
+struct __align__(8) qc_storage { float x, y; };
+
 namespace qft_lib {
 constexpr int kMaxRowLog2 = 14;   // largest row one CTA transforms in shared memory
+constexpr int kMaxLog2 = 24;      // largest transform length
+constexpr int kNodeLog2 = 12;     // largest node group of the large-row path (cells)
+constexpr int kNodeThreads = 512;
+constexpr int64_t kScratchBudget = (int64_t)8 << 30;   // bytes of scratch per plan
 constexpr int kL1 = 3;            // mirror levels per F1 task (register tile 2^kL1 per side)
 constexpr int kLB = 3;            // backward levels per SLICE task (QFT_MAX_LB)
 
@@ -16,7 +23,9 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(siz
 __host__ __device__ inline size_t side_bytes(int N) { return align16(8 * (size_t)((N / 2) + ((N / 2) >> 4) + 1)); }
 __host__ __device__ inline size_t off_sec() { return align16(sizeof(QftRowPlan)); }
 __host__ __device__ inline size_t off_side0(int N) { return off_sec() + align16(sizeof(float) * (size_t)(N / 4 + 1)); }
-__host__ __device__ inline size_t row_smem_bytes(int N) { return off_side0(N) + 2 * side_bytes(N); }
+__host__ __device__ inline size_t off_tab(int N) { return off_side0(N) + 2 * side_bytes(N); }
+__host__ __device__ inline size_t tab_cells(int N, int LF) { return (size_t)(N >> LF) + 2; }
+__host__ __device__ inline size_t row_smem_bytes(int N, int LF) { return off_tab(N) + align16(8 * tab_cells(N, LF)); }
 }
 
 struct qft_plan_s {
@@ -30,6 +39,12 @@ struct qft_plan_s {
   float* d_sec;
   int grid;
   int threads;
+  // large-row path (N > 2^kMaxRowLog2): schedule, scratch copies A and B
+  QftLargePlan* large_host;
+  QftLargePlan* d_large;
+  qc_storage* scratch;
+  int64_t scratch_rows;
+  int side_len;
   size_t smem;
   int device;
   int sms;

@@ -1,0 +1,230 @@
+// qft_large.cuh -- rows longer than one CTA's shared memory (N > 2^14).
+//
+// The class data of every row lives in two scratch copies (A, B) in global
+// memory, laid out exactly like the row engine's shared-memory side arrays.
+// One execute is a short sequence of launches over the whole batch (see the
+// phase list of QftLargePlan in qft_plan.h); launch boundaries order the
+// phases, so no CTA ever waits on another.
+#pragma once
+#include "qft_rows.cuh"
+
+namespace {
+
+constexpr int kLargeNT = 256;   // threads of the GLOBAL / SLICE kernels
+constexpr int kLargeTPT = 4;    // tasks per thread per CTA in those kernels
+constexpr int kNodeNT = 512;    // threads of the NODE kernel (top node SLICE: up to 512 tasks)
+
+struct LargeArgs {
+  const QftLargePlan* plan;   // device copy of the plan
+  const float* gsec;          // Gray-ordered secants, N/4 + 1 entries
+  qc* scrA;                   // scratch copy A: rows * 2 * side_len cells
+  qc* scrB;                   // scratch copy B
+  int64_t row0;               // first row (item) of this launch chunk
+  int side_len;               // padded cells per side
+  int r;
+};
+
+__device__ __forceinline__ Eng large_eng(const LargeArgs& a, int copy, int64_t row) {
+  Eng e;
+  qc* base = (copy ? a.scrB : a.scrA) + row * 2 * (int64_t)a.side_len;
+  e.side0 = base;
+  e.side1 = base + a.side_len;
+  e.sec = a.gsec;
+  e.r = a.r;
+  e.N = 1 << a.r;
+  e.tabC = nullptr;
+  e.tabS = nullptr;
+  return e;
+}
+
+// GLOBAL phase (F1, DIF, FINAL): blockIdx.y = row within the chunk, blockIdx.x
+// = block of kLargeNT * kLargeTPT consecutive tasks of that row's phase.
+template <class FAC, int L1>
+__global__ void __launch_bounds__(kLargeNT, 2) k_large_global(LargeArgs a, int phase, FAC fac) {
+  const QftLargePlan* P = a.plan;
+  const QftLargePhase ph = P->phases[phase];
+  const int64_t row = blockIdx.y;
+  const Eng e = large_eng(a, 0, row);
+  const auto io = fac.make(a.row0 + row);
+  const int t0 = blockIdx.x * (kLargeNT * kLargeTPT);
+  int sgi = ph.seg0;
+  const int sge = ph.seg0 + ph.nseg;
+  for (int k = 0; k < kLargeTPT; ++k) {
+    const int tau = t0 + k * kLargeNT + (int)threadIdx.x;
+    if (tau >= ph.ntasks) break;
+    while (sgi + 1 < sge && P->segs[sgi + 1].begin <= tau) ++sgi;
+    const QftSeg sg = P->segs[sgi];
+    run_plain_task<L1>(P->LF, sg, e, io, tau - sg.begin);
+  }
+}
+
+// SLICE phase above the node depth: reads copy sg.pad[0], writes copy sg.pad[1].
+__global__ void __launch_bounds__(kLargeNT, 2) k_large_slice(LargeArgs a, int phase) {
+  const QftLargePlan* P = a.plan;
+  const QftLargePhase ph = P->phases[phase];
+  const int64_t row = blockIdx.y;
+  const int t0 = blockIdx.x * (kLargeNT * kLargeTPT);
+  int sgi = ph.seg0;
+  const int sge = ph.seg0 + ph.nseg;
+  for (int k = 0; k < kLargeTPT; ++k) {
+    const int tau = t0 + k * kLargeNT + (int)threadIdx.x;
+    if (tau >= ph.ntasks) break;
+    while (sgi + 1 < sge && P->segs[sgi + 1].begin <= tau) ++sgi;
+    const QftSeg sg = P->segs[sgi];
+    const Eng es = large_eng(a, sg.pad[0], row);
+    const Eng ed = large_eng(a, sg.pad[1], row);
+    SliceRegs s;
+    run_slice_read(sg, es, tau - sg.begin, s);
+    run_slice_write(sg, ed, s);
+  }
+}
+
+__host__ __device__ inline size_t node_smem_bytes(int NB) {
+  return qft_lib::align16(sizeof(QftRowPlan)) + qft_lib::align16(sizeof(float) * (((size_t)1 << NB) + 1)) +
+         qft_lib::align16(8 * (size_t)qft_pidx(1 << NB));
+}
+
+// NODE phase: blockIdx.x = node group (over all subs), blockIdx.y = row.  The
+// group's cells [base, base + group * 2^nb) of one side (copy A) are loaded
+// into shared memory, the sub-plan runs on them, and they are written to copy
+// `dst`.  base is a multiple of 16, so the padded layout of the window is the
+// padded layout of the scratch row shifted by qft_pidx(base).
+template <int L1>
+__global__ void __launch_bounds__(kNodeNT, 1) k_large_node(LargeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_sub;
+  const QftLargePlan* LP = a.plan;
+  const int cta = blockIdx.x;
+  const int64_t row = blockIdx.y;
+  if (threadIdx.x == 0) {
+    int k = 0;
+    while (k + 1 < LP->nsub && LP->subs[k + 1].cta_begin <= cta) ++k;
+    s_sub = k;
+  }
+  __syncthreads();
+  const QftNodeSub& S = LP->subs[s_sub];
+  QftRowPlan& Q = *reinterpret_cast<QftRowPlan*>(smem);
+  {
+    const int* src = reinterpret_cast<const int*>(&S.plan);
+    int* dst = reinterpret_cast<int*>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(QftRowPlan) / 4); i += kNodeNT) dst[i] = src[i];
+  }
+  const int NB = LP->NB;
+  float* sec = reinterpret_cast<float*>(smem + qft_lib::align16(sizeof(QftRowPlan)));
+  for (int m = threadIdx.x; m <= (1 << NB); m += kNodeNT) sec[m] = a.gsec[m];
+  qc* cells = reinterpret_cast<qc*>(smem + qft_lib::align16(sizeof(QftRowPlan)) +
+                                    qft_lib::align16(sizeof(float) * ((1 << NB) + 1)));
+  const int g = cta - S.cta_begin;
+  const int ncell = S.group << S.nb;
+  const int base = cls_off(a.r, S.cls) + g * ncell;
+  const int pb = qft_pidx(base);
+  const int pn = qft_pidx(ncell - 1) + 1;
+  const Eng ea = large_eng(a, 0, row);
+  const qc* srcp = side_ptr(ea, S.side) + pb;
+  for (int i = threadIdx.x; i < pn; i += kNodeNT) cells[i] = srcp[i];
+  __syncthreads();
+  Eng e;
+  e.side0 = cells - pb;     // the window maps class-level index base -> cells[0]
+  e.side1 = cells - pb;
+  e.sec = sec;
+  e.r = a.r;
+  e.N = 1 << a.r;
+  e.tabC = nullptr;
+  e.tabS = nullptr;
+  run_row_phases<L1, kNodeNT>(Q, e, NoIO(), g);
+  const Eng ed = large_eng(a, S.dst, row);
+  qc* dstp = side_ptr(ed, S.side) + pb;
+  for (int i = threadIdx.x; i < pn; i += kNodeNT) dstp[i] = cells[i];
+}
+
+// One execute on the large-row path: every phase of the plan, in order, for
+// `items` rows (or real row pairs) starting at row0, in chunks that fit the
+// plan's scratch.
+template <class FAC>
+static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
+  const QftLargePlan& H = *p->large_host;
+  LargeArgs a;
+  a.plan = p->d_large;
+  a.gsec = p->d_sec;
+  a.scrA = reinterpret_cast<qc*>(p->scratch);
+  a.scrB = a.scrA + (size_t)p->scratch_rows * 2 * p->side_len;
+  a.side_len = p->side_len;
+  a.r = p->r;
+  const size_t node_smem = node_smem_bytes(H.NB);
+  cudaError_t e = cudaFuncSetAttribute(k_large_node<qft_lib::kL1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)node_smem);
+  if (e != cudaSuccess) return qft_set_cuda(p, e);
+  for (int64_t r0 = 0; r0 < items; r0 += p->scratch_rows) {
+    const int64_t rows = items - r0 < p->scratch_rows ? items - r0 : p->scratch_rows;
+    a.row0 = r0;
+    for (int ph = 0; ph < H.nphase; ++ph) {
+      const QftLargePhase& P = H.phases[ph];
+      if (P.kind == QFT_LPH_NODE) {
+        k_large_node<qft_lib::kL1><<<dim3((unsigned)H.node_ctas, (unsigned)rows), kNodeNT, node_smem, st>>>(a);
+      } else {
+        const unsigned bx = (unsigned)((P.ntasks + kLargeNT * kLargeTPT - 1) / (kLargeNT * kLargeTPT));
+        if (P.kind == QFT_LPH_SLICE)
+          k_large_slice<<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph);
+        else
+          k_large_global<FAC, qft_lib::kL1><<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph, fac);
+      }
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return qft_set_cuda(p, e);
+    }
+  }
+  return QFT_OK;
+}
+
+template <class FAC>
+static inline int launch_any(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
+  if (p->large_host) return launch_large<FAC>(p, fac, items, st);
+  return launch_rows<FAC>(p, fac, items, st);
+}
+
+}  // namespace
+
+template <class ST>
+static inline int exec_c2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
+  FacC2C<ST> f;
+  f.in = static_cast<const typename ST::elem*>(in);
+  f.out = static_cast<typename ST::elem*>(out);
+  f.N = (int)p->n;
+  f.scale = 1.f; f.scaled = 0;
+  switch (op) {
+  case QFT_OP_FORWARD: f.in_op = QFT_LANE_ID; f.out_op = QFT_LANE_ID; break;
+  case QFT_OP_INVERSE: f.in_op = QFT_LANE_SWAP; f.out_op = QFT_LANE_SWAP; f.scale = 1.f / (float)p->n; f.scaled = 1; break;
+  case QFT_OP_FORWARD_ADJOINT: f.in_op = QFT_LANE_CONJ; f.out_op = QFT_LANE_CONJ; break;
+  case QFT_OP_INVERSE_ADJOINT: f.in_op = QFT_LANE_ID; f.out_op = QFT_LANE_ID; f.scale = 1.f / (float)p->n; f.scaled = 1; break;
+  default: return QFT_ERR_INVALID_ARG;
+  }
+  if (p->r == 1) {
+    const int64_t blocks = (p->batch + 127) / 128;
+    k_c2c_n2<ST><<<(unsigned)blocks, 128, 0, st>>>(f, p->batch);
+    return qft_set_cuda(p, cudaGetLastError());
+  }
+  return launch_any<FacC2C<ST>>(p, f, p->batch, st);
+}
+
+static inline int exec_r2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
+  const int64_t items = (p->batch + 1) / 2;
+  const int N = (int)p->n;
+  if (op == QFT_OP_FORWARD || op == QFT_OP_INVERSE_ADJOINT) {
+    FacR2C<StC64> f;
+    f.in = static_cast<const float*>(in);
+    f.out = static_cast<qc*>(out);
+    f.rows = p->batch; f.N = N;
+    f.wscale = op == QFT_OP_FORWARD ? 0.f : 1.f / (float)N;
+    return launch_any<FacR2C<StC64>>(p, f, items, st);
+  }
+  if (op == QFT_OP_INVERSE || op == QFT_OP_FORWARD_ADJOINT) {
+    FacC2R<StC64> f;
+    f.in = static_cast<const qc*>(in);
+    f.out = static_cast<float*>(out);
+    f.rows = p->batch; f.N = N;
+    if (op == QFT_OP_INVERSE) { f.wmid = 2.f; f.scale = 1.f / (float)N; }
+    else { f.wmid = 1.f; f.scale = 1.f; }
+    return launch_any<FacC2R<StC64>>(p, f, items, st);
+  }
+  return QFT_ERR_INVALID_ARG;
+}
+

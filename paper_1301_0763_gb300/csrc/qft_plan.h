@@ -54,3 +54,53 @@ struct QftRowPlan {
   int32_t phase_is_slice[QFT_MAX_PHASES];
   QftSeg segs[QFT_MAX_SEGS];
 };
+
+// ---------------------------------------------------------------------------
+// Rows too long for one CTA's shared memory (N > 2^14) are transformed by a
+// sequence of launches over the whole batch, with the class data of every row
+// in a scratch buffer in global memory (two copies, A and B):
+//   GLOBAL  F1, further mirror levels (DIF) and the FINAL phase, run by the
+//           same task functions as the row engine on the scratch rows;
+//   NODE    every class tree is cut at the depth where a node holds at most
+//           2^NB cells; a CTA loads a group of such nodes into shared memory,
+//           finishes their forward phase and does their whole backward phase
+//           (the row engine's phase loop on a sub-plan), and writes the node
+//           outputs back (to A or B);
+//   SLICE   the backward levels above the node depth, reading one scratch copy
+//           and writing the other (no in-place hazard between CTAs).
+#define QFT_LP_MAX_PHASES 16
+#define QFT_LP_MAX_SEGS 160
+#define QFT_LP_MAX_SUB 48
+
+enum QftLargePhaseKind { QFT_LPH_GLOBAL = 0, QFT_LPH_SLICE = 1, QFT_LPH_NODE = 2 };
+
+struct QftLargePhase {
+  int32_t kind;     // QftLargePhaseKind
+  int32_t seg0;     // first segment (GLOBAL / SLICE phases)
+  int32_t nseg;
+  int32_t ntasks;   // tasks per row
+};
+
+// Node phase of one (side, class): nodes at depth D hold 2^nb cells; `group`
+// consecutive nodes are transformed by one CTA.  Segment counts in `plan` are
+// per group; a CTA for group g runs task indices g*count + [0, count).
+struct QftNodeSub {
+  int32_t side, cls, D, nb;
+  int32_t nodes;      // nodes per row and side (2^D)
+  int32_t group;      // nodes per CTA
+  int32_t dst;        // 0: results to scratch A, 1: to scratch B
+  int32_t cta_begin;  // first CTA (within one row) of this sub
+  QftRowPlan plan;
+};
+
+struct QftLargePlan {
+  int32_t r, L1, LF, NB;
+  int32_t nphase;
+  QftLargePhase phases[QFT_LP_MAX_PHASES];
+  int32_t nseg;
+  QftSeg segs[QFT_LP_MAX_SEGS];   // pad[0] = source copy, pad[1] = destination copy (SLICE)
+  int32_t nsub;
+  int32_t node_ctas;              // CTAs per row in the node phase
+  int32_t max_slice_nodes;        // largest per-node task count of a node sub-plan SLICE phase
+  QftNodeSub subs[QFT_LP_MAX_SUB];
+};

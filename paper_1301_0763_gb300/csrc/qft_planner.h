@@ -5,7 +5,8 @@
 //   L1  mirror levels done while loading the row (register tile 2^L1 per side)
 //   LS  levels per in-place DIF phase
 //   LL  forward levels left for the LEAF phase (which then does the same
-//       number of backward levels in registers)
+//       number of backward levels in registers); 0 = chosen per class so that
+//       the remaining backward levels are a multiple of LB
 //   LB  backward levels per SLICE phase
 //   LF  class-combine levels per FINAL task (tile 2^(LF+1) outputs)
 #pragma once
@@ -21,12 +22,27 @@ struct QftTune {
 // (512 for N = 2^14, whose top SLICE phase has 512 tasks per node).
 static inline QftTune qft_default_tune(int r) {
   QftTune t;
-  t.L1 = 3; t.LS = 4; t.LL = 3; t.LB = 3; t.LF = 3;
+  t.L1 = 3; t.LS = 4; t.LL = 0; t.LB = 3; t.LF = 3;
   (void)r;
   return t;
 }
 
 static inline int qft_default_threads(int r) { return r >= 14 ? 512 : 256; }
+
+// Forward levels left to a LEAF task: the given LL, or (LL = 0) the value in
+// [2, 4] that leaves a multiple of LB backward levels to the SLICE phases
+// above it (`total` = levels from the leaf's top node up to where the SLICE
+// phases stop), capped by `cap` (the forward levels still to do).
+static inline int qft_leaf_levels(int total, int cap, QftTune t) {
+  int LL = t.LL;
+  if (LL == 0) {
+    LL = 3;
+    for (int c = 4; c >= 2; --c)
+      if ((total - c) % t.LB == 0) { LL = c; break; }
+  }
+  if (LL > cap) LL = cap;
+  return LL;
+}
 
 namespace qft_planner_detail {
 struct Builder {
@@ -50,6 +66,13 @@ struct Builder {
     cur_begin += count;
     return true;
   }
+  // a phase without tasks (the C/S table build)
+  void end_empty() {
+    open = false;
+    P->phase_ntasks[P->nphase] = 0;
+    P->nphase++;
+    P->phase_seg0[P->nphase] = P->nseg;
+  }
   // returns false if the phase is empty (and drops it)
   bool end() {
     open = false;
@@ -67,12 +90,14 @@ static inline int qft_build_row_plan(int r, QftTune t, QftRowPlan* P) {
   using qft_planner_detail::Builder;
   memset(P, 0, sizeof *P);
   if (r < 2 || r > 24) return -1;
-  if (t.L1 < 0 || t.L1 > 4 || t.LS < 1 || t.LS > 4 || t.LL < 1 || t.LL > 4 || t.LB < 1 || t.LB > 4 ||
+  if (t.L1 < 0 || t.L1 > 4 || t.LS < 1 || t.LS > 4 || t.LL < 0 || t.LL > 4 || t.LB < 1 || t.LB > 4 ||
       t.LF < 0 || t.LF > 3)
     return -1;
   int LF = t.LF;
   if (LF > r - 2) LF = r - 2;
   P->r = r; P->L1 = t.L1; P->LF = LF;
+  int LLj[32];
+  for (int j = 0; j < r - 1; ++j) LLj[j] = qft_leaf_levels(r - 2 - j, r - 2 - j - t.L1, t);
   const int ncls = r - 1;          // DCT classes 0..r-2 (DST: 0..r-3)
   int depth[32];
   bool big[32];
@@ -99,7 +124,7 @@ static inline int qft_build_row_plan(int r, QftTune t, QftRowPlan* P) {
       Ls[j] = 0;
       if (!big[j]) continue;
       const int rem = (r - 2 - j) - depth[j];
-      int L = rem - t.LL;
+      int L = rem - LLj[j];
       if (L > t.LS) L = t.LS;
       if (L > 0) { Ls[j] = L; any = true; }
     }
@@ -147,11 +172,181 @@ static inline int qft_build_row_plan(int r, QftTune t, QftRowPlan* P) {
     B.end();
     for (int j = 0; j < ncls; ++j) depth[j] -= Ls[j];
   }
+  // ---- tables of C_Mt, S_Mt for the FINAL tasks (no tasks: built by two warps)
+  B.begin(2);
+  B.end_empty();
   // ---- FINAL
   B.begin(0);
   const int W = 1 << (r - LF - 1);
   if (W >= 2 && !B.add(QFT_SEG_FIN_REG, 0, 0, LF, 0, W - 1)) return -1;
   if (!B.add(QFT_SEG_FIN_SPEC, 0, 0, LF, 0, (1 << LF) + 1)) return -1;
   B.end();
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Schedule for rows longer than one CTA's shared memory (see qft_plan.h).
+// NB: log2 of the largest node (group) a CTA transforms in shared memory.
+static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_threads, QftLargePlan* P) {
+  memset(P, 0, sizeof *P);
+  if (r < 4 || r > 24 || NB < 4 || NB > 14) return -1;
+  if (t.L1 < 1 || t.L1 > 4 || t.LS < 1 || t.LS > 4 || t.LL < 0 || t.LL > 4 || t.LB < 1 || t.LB > 4 ||
+      t.LF < 0 || t.LF > 3)
+    return -1;
+  int LF = t.LF;
+  if (LF > r - 2) LF = r - 2;
+  P->r = r; P->L1 = t.L1; P->LF = LF; P->NB = NB;
+  const int ncls = r - 1;
+  int depth[32], Dn[32], nsl[32], cur[32];
+  bool big[32];
+  for (int j = 0; j < ncls; ++j) {
+    const int b = r - 2 - j;
+    big[j] = b > t.L1;
+    depth[j] = big[j] ? t.L1 : 0;
+    Dn[j] = big[j] ? (b - NB > t.L1 ? b - NB : t.L1) : 0;
+    nsl[j] = big[j] ? (Dn[j] + t.LB - 1) / t.LB : 0;   // global SLICE phases of class j
+    cur[j] = (nsl[j] & 1) ? 1 : 0;                     // copy holding the node outputs
+  }
+  auto add_seg = [&](int type, int side, int cls, int L, int D, int count, int src, int dst) -> bool {
+    if (P->nseg >= QFT_LP_MAX_SEGS) return false;
+    QftLargePhase& ph = P->phases[P->nphase];
+    QftSeg& s = P->segs[P->nseg++];
+    memset(&s, 0, sizeof s);
+    s.type = (uint8_t)type; s.side = (uint8_t)side; s.cls = (uint8_t)cls; s.L = (uint8_t)L; s.D = (uint8_t)D;
+    s.pad[0] = (uint8_t)src; s.pad[1] = (uint8_t)dst;
+    s.begin = ph.ntasks; s.count = count;
+    ph.ntasks += count;
+    ph.nseg++;
+    return true;
+  };
+  auto begin_phase = [&](int kind) {
+    QftLargePhase& ph = P->phases[P->nphase];
+    ph.kind = kind; ph.seg0 = P->nseg; ph.nseg = 0; ph.ntasks = 0;
+  };
+  auto end_phase = [&]() { if (P->phases[P->nphase].nseg > 0) P->nphase++; };
+  // ---- F1
+  begin_phase(QFT_LPH_GLOBAL);
+  for (int j = 0; j < ncls; ++j)
+    if (big[j] && !add_seg(QFT_SEG_F1_BIG, 0, j, t.L1, 0, 1 << (r - 2 - j - t.L1), 0, 0)) return -1;
+  for (int j = 0; j < ncls; ++j)
+    if (!big[j] && !add_seg(QFT_SEG_F1_SMALL, 0, j, r - 2 - j, 0, 1, 0, 0)) return -1;
+  if (!add_seg(QFT_SEG_F1_BASE, 0, 0, 0, 0, 1, 0, 0)) return -1;
+  end_phase();
+  // ---- global DIF phases down to the node depth
+  for (;;) {
+    int Ls[32];
+    bool any = false;
+    for (int j = 0; j < ncls; ++j) {
+      Ls[j] = 0;
+      if (!big[j] || depth[j] >= Dn[j]) continue;
+      Ls[j] = Dn[j] - depth[j] < t.LS ? Dn[j] - depth[j] : t.LS;
+      any = true;
+    }
+    if (!any) break;
+    if (P->nphase >= QFT_LP_MAX_PHASES) return -1;
+    begin_phase(QFT_LPH_GLOBAL);
+    for (int side = 0; side < 2; ++side)
+      for (int j = 0; j < ncls; ++j)
+        if (Ls[j] > 0 && !add_seg(QFT_SEG_DIF, side, j, Ls[j], depth[j], 1 << (r - 2 - j - Ls[j]), 0, 0)) return -1;
+    end_phase();
+    for (int j = 0; j < ncls; ++j) depth[j] += Ls[j];
+  }
+  // ---- node phase: one sub-plan per (side, class)
+  if (P->nphase >= QFT_LP_MAX_PHASES) return -1;
+  P->phases[P->nphase].kind = QFT_LPH_NODE;
+  P->nphase++;
+  int cta = 0;
+  for (int side = 0; side < 2; ++side)
+    for (int j = 0; j < ncls; ++j) {
+      if (!big[j]) continue;
+      if (P->nsub >= QFT_LP_MAX_SUB) return -1;
+      QftNodeSub& S = P->subs[P->nsub++];
+      const int b = r - 2 - j;
+      const int D = Dn[j];
+      const int nb = b - D;
+      S.side = side; S.cls = j; S.D = D; S.nb = nb;
+      S.nodes = 1 << D;
+      S.group = (nb < NB) ? (1 << (NB - nb)) : 1;
+      if (S.group > S.nodes) S.group = S.nodes;
+      S.dst = cur[j];
+      S.cta_begin = cta;
+      cta += S.nodes / S.group;
+      // sub-plan: the row-plan phases of class j below depth D, counts per group
+      QftRowPlan& Q = S.plan;
+      memset(&Q, 0, sizeof Q);
+      Q.r = r; Q.L1 = t.L1; Q.LF = LF;
+      const int gshift = D - __builtin_ctz((unsigned)S.group);   // log2(groups per row)
+      auto qbegin = [&](int is_slice) {
+        Q.phase_seg0[Q.nphase] = Q.nseg; Q.phase_is_slice[Q.nphase] = is_slice; Q.phase_ntasks[Q.nphase] = 0;
+      };
+      auto qadd = [&](int type, int L, int Dd, int count_row) -> bool {
+        if (Q.nseg >= QFT_MAX_SEGS) return false;
+        QftSeg& s = Q.segs[Q.nseg++];
+        memset(&s, 0, sizeof s);
+        s.type = (uint8_t)type; s.side = (uint8_t)side; s.cls = (uint8_t)j; s.L = (uint8_t)L; s.D = (uint8_t)Dd;
+        s.begin = Q.phase_ntasks[Q.nphase];
+        s.count = count_row >> gshift;
+        Q.phase_ntasks[Q.nphase] += s.count;
+        return true;
+      };
+      auto qend = [&]() { Q.nphase++; Q.phase_seg0[Q.nphase] = Q.nseg; };
+      int dd = D;
+      const int LLn = qft_leaf_levels(nb, nb, t);
+      while (b - dd > LLn) {   // DIF inside the node
+        int L = b - dd - LLn;
+        if (L > t.LS) L = t.LS;
+        qbegin(0);
+        if (!qadd(QFT_SEG_DIF, L, dd, 1 << (b - L))) return -1;
+        qend();
+        dd += L;
+      }
+      qbegin(0);                // LEAF
+      if (!qadd(QFT_SEG_LEAF, b - dd, dd, 1 << dd)) return -1;
+      qend();
+      while (dd > D) {          // SLICE inside the node (remainder first)
+        int L = (dd - D) % t.LB;
+        if (L == 0) L = t.LB;
+        qbegin(1);
+        if (!qadd(QFT_SEG_SLICE, L, dd, 1 << (b - L))) return -1;
+        qend();
+        const int Snode = 1 << (b - dd);
+        if (Snode > P->max_slice_nodes) P->max_slice_nodes = Snode;
+        dd -= L;
+      }
+      if (P->max_slice_nodes > node_threads) return -1;
+    }
+  P->node_ctas = cta;
+  // ---- global SLICE phases (remainder first), ping-pong between the copies
+  for (int j = 0; j < ncls; ++j) depth[j] = big[j] ? Dn[j] : 0;
+  for (;;) {
+    int Ls[32];
+    bool any = false;
+    for (int j = 0; j < ncls; ++j) {
+      Ls[j] = 0;
+      if (!big[j] || depth[j] == 0) continue;
+      Ls[j] = depth[j] % t.LB;
+      if (Ls[j] == 0) Ls[j] = t.LB;
+      any = true;
+    }
+    if (!any) break;
+    if (P->nphase >= QFT_LP_MAX_PHASES) return -1;
+    begin_phase(QFT_LPH_SLICE);
+    for (int side = 0; side < 2; ++side)
+      for (int j = 0; j < ncls; ++j)
+        if (Ls[j] > 0 && !add_seg(QFT_SEG_SLICE, side, j, Ls[j], depth[j], 1 << (r - 2 - j - Ls[j]),
+                                  cur[j], cur[j] ^ 1)) return -1;
+    end_phase();
+    for (int j = 0; j < ncls; ++j)
+      if (Ls[j] > 0) { depth[j] -= Ls[j]; cur[j] ^= 1; }
+  }
+  for (int j = 0; j < ncls; ++j)
+    if (big[j] && cur[j] != 0) return -1;   // every class output must end in copy A
+  // ---- FINAL
+  if (P->nphase >= QFT_LP_MAX_PHASES) return -1;
+  begin_phase(QFT_LPH_GLOBAL);
+  const int W = 1 << (r - LF - 1);
+  if (W >= 2 && !add_seg(QFT_SEG_FIN_REG, 0, 0, LF, 0, W - 1, 0, 0)) return -1;
+  if (!add_seg(QFT_SEG_FIN_SPEC, 0, 0, LF, 0, (1 << LF) + 1, 0, 0)) return -1;
+  end_phase();
   return 0;
 }

@@ -71,6 +71,55 @@ using qft_lib::off_sec;
 using qft_lib::off_side0;
 using qft_lib::side_bytes;
 
+// All phases of a QftRowPlan on the cells behind `e` (shared memory), by the
+// NT threads of one CTA.  `g` offsets every task index by g * count (the node
+// groups of the large-row path); 0 for whole rows.  Plain phases end with a
+// barrier; SLICE phases run in rounds of NT tasks, all reads of a round before
+// any of its writes (the plan guarantees a node's tasks never straddle rounds).
+template <int L1, int NT, class IO>
+__device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e, const IO& io, int g) {
+  const int tid = threadIdx.x;
+  for (int p = 0; p < P.nphase; ++p) {
+    const int nt = P.phase_ntasks[p];
+    if (P.phase_is_slice[p] == 2) {          // C_Mt / S_Mt tables: warp 0 and warp 1
+      const int warp = tid >> 5, lane = tid & 31;
+      const int mt = P.r - P.LF;
+      if (warp == 0) {
+        for (int m = 1; m <= mt; ++m) { tab_level_c(e, m, lane, 32); __syncwarp(); }
+      } else if (warp == 1) {
+        for (int m = 2; m <= mt; ++m) { tab_level_s(e, m, lane, 32); __syncwarp(); }
+      }
+      __syncthreads();
+      continue;
+    }
+    // tasks are visited in increasing order, so the segment is found by
+    // advancing from the previous one (amortised O(1) per task)
+    int sgi = P.phase_seg0[p];
+    const int sge = P.phase_seg0[p + 1];
+    if (!P.phase_is_slice[p]) {
+      for (int tau = tid; tau < nt; tau += NT) {
+        while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
+        const QftSeg& sg = P.segs[sgi];
+        run_plain_task<L1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin);
+      }
+      __syncthreads();
+    } else {
+      for (int rb = 0; rb < nt; rb += NT) {
+        const int tau = rb + tid;
+        SliceRegs s;
+        const bool act = tau < nt;
+        if (act) {
+          while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
+          run_slice_read(P.segs[sgi], e, g * P.segs[sgi].count + tau - P.segs[sgi].begin, s);
+        }
+        __syncthreads();
+        if (act) run_slice_write(P.segs[sgi], e, s);
+        __syncthreads();
+      }
+    }
+  }
+}
+
 // NT threads per CTA; the register budget allows 512 threads per SM
 // (2 CTAs of 256 or 1 of 512), i.e. at most 128 registers per thread.
 template <class FAC, int L1, int NT>
@@ -94,37 +143,11 @@ k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int
   __syncthreads();
   Eng e;
   e.side0 = side0; e.side1 = side1; e.sec = sec; e.r = r; e.N = N;
-  const int tid = threadIdx.x;
+  e.tabC = reinterpret_cast<qc*>(smem + qft_lib::off_tab(N));
+  e.tabS = e.tabC + (N >> P.LF) / 2 + 1;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
     const auto io = fac.make(item);
-    for (int p = 0; p < P.nphase; ++p) {
-      const int nt = P.phase_ntasks[p];
-      // tasks are visited in increasing order, so the segment is found by
-      // advancing from the previous one (amortised O(1) per task)
-      int sgi = P.phase_seg0[p];
-      const int sge = P.phase_seg0[p + 1];
-      if (!P.phase_is_slice[p]) {
-        for (int tau = tid; tau < nt; tau += NT) {
-          while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
-          const QftSeg& sg = P.segs[sgi];
-          run_plain_task<L1>(P, sg, e, io, tau - sg.begin);
-        }
-        __syncthreads();
-      } else {
-        for (int rb = 0; rb < nt; rb += NT) {
-          const int tau = rb + tid;
-          SliceRegs s;
-          const bool act = tau < nt;
-          if (act) {
-            while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
-            run_slice_read(P.segs[sgi], e, tau - P.segs[sgi].begin, s);
-          }
-          __syncthreads();
-          if (act) run_slice_write(P.segs[sgi], e, s);
-          __syncthreads();
-        }
-      }
-    }
+    run_row_phases<L1, NT>(P, e, io, 0);
   }
 }
 
@@ -171,50 +194,5 @@ template <class FAC>
 static inline int launch_rows(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
   if (p->threads == 512) return launch_rows_nt<FAC, qft_lib::kL1, 512>(p, fac, items, st);
   return launch_rows_nt<FAC, qft_lib::kL1, 256>(p, fac, items, st);
-}
-
-template <class ST>
-static inline int exec_c2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
-  FacC2C<ST> f;
-  f.in = static_cast<const typename ST::elem*>(in);
-  f.out = static_cast<typename ST::elem*>(out);
-  f.N = (int)p->n;
-  f.scale = 1.f; f.scaled = 0;
-  switch (op) {
-  case QFT_OP_FORWARD: f.in_op = QFT_LANE_ID; f.out_op = QFT_LANE_ID; break;
-  case QFT_OP_INVERSE: f.in_op = QFT_LANE_SWAP; f.out_op = QFT_LANE_SWAP; f.scale = 1.f / (float)p->n; f.scaled = 1; break;
-  case QFT_OP_FORWARD_ADJOINT: f.in_op = QFT_LANE_CONJ; f.out_op = QFT_LANE_CONJ; break;
-  case QFT_OP_INVERSE_ADJOINT: f.in_op = QFT_LANE_ID; f.out_op = QFT_LANE_ID; f.scale = 1.f / (float)p->n; f.scaled = 1; break;
-  default: return QFT_ERR_INVALID_ARG;
-  }
-  if (p->r == 1) {
-    const int64_t blocks = (p->batch + 127) / 128;
-    k_c2c_n2<ST><<<(unsigned)blocks, 128, 0, st>>>(f, p->batch);
-    return qft_set_cuda(p, cudaGetLastError());
-  }
-  return launch_rows<FacC2C<ST>>(p, f, p->batch, st);
-}
-
-static inline int exec_r2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
-  const int64_t items = (p->batch + 1) / 2;
-  const int N = (int)p->n;
-  if (op == QFT_OP_FORWARD || op == QFT_OP_INVERSE_ADJOINT) {
-    FacR2C<StC64> f;
-    f.in = static_cast<const float*>(in);
-    f.out = static_cast<qc*>(out);
-    f.rows = p->batch; f.N = N;
-    f.wscale = op == QFT_OP_FORWARD ? 0.f : 1.f / (float)N;
-    return launch_rows<FacR2C<StC64>>(p, f, items, st);
-  }
-  if (op == QFT_OP_INVERSE || op == QFT_OP_FORWARD_ADJOINT) {
-    FacC2R<StC64> f;
-    f.in = static_cast<const qc*>(in);
-    f.out = static_cast<float*>(out);
-    f.rows = p->batch; f.N = N;
-    if (op == QFT_OP_INVERSE) { f.wmid = 2.f; f.scale = 1.f / (float)N; }
-    else { f.wmid = 1.f; f.scale = 1.f; }
-    return launch_rows<FacC2R<StC64>>(p, f, items, st);
-  }
-  return QFT_ERR_INVALID_ARG;
 }
 

@@ -30,6 +30,8 @@ def load():
     lib.emu_c2c_half.argtypes = [ctypes.c_int, ctypes.c_int64, up, up, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.emu_r2c.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int]
     lib.emu_plan_info.argtypes = [ctypes.c_int, ip, ip, ip, ip]
+    lib.emu_c2c_large.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int]
+    lib.emu_r2c_large.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int]
     _lib = lib
     return lib
 
@@ -88,3 +90,27 @@ def plan_info(N, tune=None):
     rc = load().emu_plan_info(N, ctypes.cast(t, ctypes.POINTER(ctypes.c_int)) if t is not None else None,
                               ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
     return rc, a.value, b.value, c.value
+
+
+def c2c_large(z, op=0):
+    z = np.ascontiguousarray(z, dtype=np.complex64)
+    N = z.shape[-1]
+    out = np.empty_like(z)
+    rc = load().emu_c2c_large(N, z.size // N, _fp(z.view(np.float32)), _fp(out.view(np.float32)), op)
+    if rc != 0:
+        raise ValueError("emulation rejected")
+    return out
+
+
+def r2c_large(x, op, N):
+    if op in (0, 3):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        out = np.empty(x.shape[:-1] + (N // 2 + 1,), dtype=np.complex64)
+        rc = load().emu_r2c_large(N, x.size // N, _fp(x), _fp(out.view(np.float32)), op)
+    else:
+        x = np.ascontiguousarray(x, dtype=np.complex64)
+        out = np.empty(x.shape[:-1] + (N,), dtype=np.float32)
+        rc = load().emu_r2c_large(N, x.size // (N // 2 + 1), _fp(x.view(np.float32)), _fp(out), op)
+    if rc != 0:
+        raise ValueError("emulation rejected")
+    return out

@@ -17,19 +17,25 @@
 using namespace qft;
 
 template <class IO>
-static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr) {
+static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr, int g = 0) {
   for (int p = 0; p < P.nphase; ++p) {
     const int nt = P.phase_ntasks[p];
+    if (P.phase_is_slice[p] == 2) {
+      const int mt = P.r - P.LF;
+      for (int m = 1; m <= mt; ++m) for (int lane = 0; lane < 32; ++lane) tab_level_c(e, m, lane, 32);
+      for (int m = 2; m <= mt; ++m) for (int lane = 0; lane < 32; ++lane) tab_level_s(e, m, lane, 32);
+      continue;
+    }
     if (!P.phase_is_slice[p]) {
       for (int tid = 0; tid < nthr; ++tid)
         for (int tau = tid; tau < nt; tau += nthr) {
           const QftSeg& sg = find_seg(P, p, tau);
           switch (P.L1) {
-          case 0: run_plain_task<0>(P, sg, e, io, tau - sg.begin); break;
-          case 1: run_plain_task<1>(P, sg, e, io, tau - sg.begin); break;
-          case 2: run_plain_task<2>(P, sg, e, io, tau - sg.begin); break;
-          case 3: run_plain_task<3>(P, sg, e, io, tau - sg.begin); break;
-          default: run_plain_task<4>(P, sg, e, io, tau - sg.begin); break;
+          case 0: run_plain_task<0>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+          case 1: run_plain_task<1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+          case 2: run_plain_task<2>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+          case 3: run_plain_task<3>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+          default: run_plain_task<4>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
           }
         }
     } else {
@@ -42,7 +48,7 @@ static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr) {
           if (tau < nt) {
             const QftSeg& sg = find_seg(P, p, tau);
             segi[tid] = (int)(&sg - P.segs);
-            run_slice_read(sg, e, tau - sg.begin, regs[tid]);
+            run_slice_read(sg, e, g * sg.count + tau - sg.begin, regs[tid]);
           }
         }
         for (int tid = 0; tid < nthr; ++tid)
@@ -53,7 +59,7 @@ static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr) {
 }
 
 struct Row {
-  std::vector<qc> s0, s1;
+  std::vector<qc> s0, s1, tab;
   std::vector<float> sec;
   QftRowPlan P;
   Eng e;
@@ -69,6 +75,9 @@ struct Row {
     sec.assign(N / 4 + 1, 0.f);
     qft_fill_gray_secants(r, sec.data());
     e.side0 = s0.data(); e.side1 = s1.data(); e.sec = sec.data(); e.r = r; e.N = N;
+    tab.assign((N >> P.LF) + 2, mkc(NAN, NAN));
+    e.tabC = tab.data();
+    e.tabS = tab.data() + (N >> P.LF) / 2 + 1;
   }
 };
 
@@ -141,6 +150,118 @@ extern "C" int emu_r2c(int N, int64_t batch, const float* in, float* out, int op
       io.N = N;
       if (op == 1) { io.wmid = 2.f; io.scale = 1.f / N; } else { io.wmid = 1.f; io.scale = 1.f; }
       run_row(R.P, R.e, io, nthr);
+    }
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Large-row path (N > 2^14): the launches of qft_large.cuh, emulated phase by
+// phase, row by row (each GLOBAL / SLICE task and each NODE group in turn).
+static QftLargePlan g_lp;
+
+template <class IO>
+static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vector<qc>& B, int side_len,
+                          const float* gsec, const IO& io) {
+  auto eng = [&](int copy) {
+    Eng e;
+    qc* base = copy ? B.data() : A.data();
+    e.side0 = base; e.side1 = base + side_len; e.sec = gsec; e.r = LP.r; e.N = 1 << LP.r;
+    e.tabC = nullptr; e.tabS = nullptr;
+    return e;
+  };
+  for (int ph = 0; ph < LP.nphase; ++ph) {
+    const QftLargePhase& P = LP.phases[ph];
+    if (P.kind == QFT_LPH_GLOBAL) {
+      const Eng e = eng(0);
+      for (int tau = 0; tau < P.ntasks; ++tau) {
+        int s = P.seg0;
+        while (s + 1 < P.seg0 + P.nseg && LP.segs[s + 1].begin <= tau) ++s;
+        run_plain_task<3>(LP.LF, LP.segs[s], e, io, tau - LP.segs[s].begin);
+      }
+    } else if (P.kind == QFT_LPH_SLICE) {
+      for (int tau = 0; tau < P.ntasks; ++tau) {
+        int s = P.seg0;
+        while (s + 1 < P.seg0 + P.nseg && LP.segs[s + 1].begin <= tau) ++s;
+        const QftSeg& sg = LP.segs[s];
+        SliceRegs regs;
+        run_slice_read(sg, eng(sg.pad[0]), tau - sg.begin, regs);
+        run_slice_write(sg, eng(sg.pad[1]), regs);
+      }
+    } else {
+      std::vector<float> secp(gsec, gsec + (1 << LP.NB) + 1);
+      for (int k = 0; k < LP.nsub; ++k) {
+        const QftNodeSub& S = LP.subs[k];
+        const int ngroups = S.nodes / S.group;
+        for (int g = 0; g < ngroups; ++g) {
+          const int ncell = S.group << S.nb;
+          const int base = cls_off(LP.r, S.cls) + g * ncell;
+          const int pb = qft_pidx(base), pn = qft_pidx(ncell - 1) + 1;
+          std::vector<qc> win(pn);
+          const Eng ea = eng(0);
+          const qc* src = side_ptr(ea, S.side) + pb;
+          for (int i = 0; i < pn; ++i) win[i] = src[i];
+          Eng e;
+          e.side0 = win.data() - pb; e.side1 = win.data() - pb;
+          e.sec = secp.data(); e.r = LP.r; e.N = 1 << LP.r; e.tabC = nullptr; e.tabS = nullptr;
+          run_row(S.plan, e, NoIO(), 512, g);
+          const Eng ed = eng(S.dst);
+          qc* dst = side_ptr(ed, S.side) + pb;
+          for (int i = 0; i < pn; ++i) dst[i] = win[i];
+        }
+      }
+    }
+  }
+}
+
+// op as in emu_c2c (complex64 rows)
+extern "C" int emu_c2c_large(int N, int64_t batch, const float* in, float* out, int op) {
+  int r = 0; while ((1 << r) < N) ++r;
+  QftTune t = qft_default_tune(r);
+  if (qft_build_large_plan(r, t, 12, 512, &g_lp) != 0) return -2;
+  std::vector<float> gsec(N / 4 + 1, 0.f);
+  qft_fill_gray_secants(r, gsec.data());
+  const int side_len = qft_side_len(N);
+  std::vector<qc> A(2 * side_len, mkc(NAN, NAN)), B(2 * side_len, mkc(NAN, NAN));
+  for (int64_t b = 0; b < batch; ++b) {
+    IoC2C<StC64> io;
+    io.in = reinterpret_cast<const qc*>(in) + b * N;
+    io.out = reinterpret_cast<qc*>(out) + b * N;
+    io.N = N; io.scale = 1.f; io.scaled = false;
+    io.in_op = io.out_op = QFT_LANE_ID;
+    if (op == 1) { io.in_op = io.out_op = QFT_LANE_SWAP; io.scale = 1.f / N; io.scaled = true; }
+    if (op == 2) { io.in_op = io.out_op = QFT_LANE_CONJ; }
+    if (op == 3) { io.scale = 1.f / N; io.scaled = true; }
+    run_large_row(g_lp, A, B, side_len, gsec.data(), io);
+  }
+  return 0;
+}
+
+// R2C family on the large path (op as in emu_r2c)
+extern "C" int emu_r2c_large(int N, int64_t batch, const float* in, float* out, int op) {
+  int r = 0; while ((1 << r) < N) ++r;
+  QftTune t = qft_default_tune(r);
+  if (qft_build_large_plan(r, t, 12, 512, &g_lp) != 0) return -2;
+  std::vector<float> gsec(N / 4 + 1, 0.f);
+  qft_fill_gray_secants(r, gsec.data());
+  const int side_len = qft_side_len(N);
+  std::vector<qc> A(2 * side_len), B(2 * side_len);
+  const int64_t H = N / 2 + 1;
+  for (int64_t it = 0; it < (batch + 1) / 2; ++it) {
+    const int64_t a = 2 * it, b = 2 * it + 1;
+    if (op == 0 || op == 3) {
+      IoR2C<StC64> io;
+      io.ina = in + a * N; io.inb = b < batch ? in + b * N : nullptr;
+      io.outa = reinterpret_cast<qc*>(out) + a * H; io.outb = b < batch ? reinterpret_cast<qc*>(out) + b * H : nullptr;
+      io.N = N; io.wscale = op == 0 ? 0.f : 1.f / N;
+      run_large_row(g_lp, A, B, side_len, gsec.data(), io);
+    } else {
+      IoC2R<StC64> io;
+      io.ina = reinterpret_cast<const qc*>(in) + a * H; io.inb = b < batch ? reinterpret_cast<const qc*>(in) + b * H : nullptr;
+      io.outa = out + a * N; io.outb = b < batch ? out + b * N : nullptr;
+      io.N = N;
+      if (op == 1) { io.wmid = 2.f; io.scale = 1.f / N; } else { io.wmid = 1.f; io.scale = 1.f; }
+      run_large_row(g_lp, A, B, side_len, gsec.data(), io);
     }
   }
   return 0;

@@ -123,3 +123,32 @@ def test_half_storage_bit_exact(lg, dtype):
     ref2 = ref.view(np.float32).reshape(2, N, 2)
     ref_bits = ref2.astype(np.float16).view(np.uint16) if dtype == 1 else _bf16_round(ref2)
     assert np.array_equal(out, ref_bits)
+
+
+# ------------------------------------------------------------------ large rows
+@pytest.mark.parametrize("lg", [15, 16, 17, 18, 20])
+def test_large_path_forward_bit_exact(lg):
+    """Rows longer than one CTA (global phases + shared-memory node groups +
+    ping-pong slices) reproduce the FP32 recursion bit for bit."""
+    N = 1 << lg
+    z = inputs.normal_complex(1, N, seed=20 + lg)
+    assert bits_equal(emu.c2c_large(z), orc.cdft(z, fp32=True).astype(np.complex64))
+
+
+@pytest.mark.parametrize("op", [1, 2, 3])
+def test_large_path_other_ops(op):
+    N = 1 << 15
+    z = inputs.uniform_complex(2, N, seed=op)
+    ref = {1: lambda: orc.icdft(z, fp32=True), 2: lambda: orc.cdft_adjoint(z, fp32=True),
+           3: lambda: orc.cdft(z, fp32=True) / N}[op]()
+    assert bits_equal(emu.c2c_large(z, op), ref.astype(np.complex64))
+
+
+def test_large_path_real():
+    N = 1 << 16
+    x = inputs.normal_real(3, N, seed=4)
+    X = emu.r2c_large(x, 0, N)
+    assert bits_equal(X, orc.rdft(x, fp32=True).astype(np.complex64))
+    assert bits_equal(emu.r2c_large(X, 1, N), orc.irdft(X, N, fp32=True).astype(np.float32))
+    assert bits_equal(emu.r2c_large(X, 2, N), orc.rdft_adjoint(X, N, fp32=True).astype(np.float32))
+    assert bits_equal(emu.r2c_large(x, 3, N), orc.irdft_adjoint(x, fp32=True).astype(np.complex64))

@@ -6,8 +6,10 @@ Two bars:
    Sec. 5 in FP32, so their output equals the oracle evaluated in FP32
    (same source, -DORACLE_REAL=float) bit for bit;
  * tolerance: against the FP64 oracle, max relative L2 error per row <= 1e-5
-   (the target), for every N the single-CTA engine covers (N <= 2^14; the
-   FP32 error of the method itself grows like ~3.5e-8 sqrt(N)).
+   (the target) for N <= 2^16.  Above that the FP32 error of the method itself
+   (measured on the CPU with the FP32 oracle, independent of any kernel) grows
+   like ~3.5e-8 sqrt(N), so the bound used is tol(N) = 6e-8 sqrt(N) (the
+   measured maxima: 1.9e-5 at 2^18, 3.6e-5 at 2^20, 8.1e-5 at 2^22).
 """
 import numpy as np
 import pytest
@@ -19,6 +21,10 @@ from paper_1301_0763_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
+
+
+def tol(N):
+    return max(TOL, 6e-8 * np.sqrt(N))
 
 
 @pytest.fixture(scope="module")
@@ -159,8 +165,54 @@ def test_half_storage(q, lg, half):
     assert np.array_equal(ob, ref_bits)
 
 
+# ------------------------------------------------------------- large rows
+@pytest.mark.parametrize("lg", [15, 16, 17, 18, 19, 20])
+def test_large_rows_forward(q, lg):
+    N = 1 << lg
+    rows = 3
+    z = inputs.normal_complex(rows, N, seed=lg)
+    X = run(q, N, rows, q.KIND_C2C, q.DTYPE_F32, q.OP_FORWARD, z, (rows, N), torch.complex64)
+    assert bits_equal(X, orc.cdft(z, fp32=True).astype(np.complex64))
+    assert rel_rows(X.astype(np.complex128), orc.cdft(z)).max() < tol(N)
+
+
+@pytest.mark.parametrize("op", [1, 2, 3])
+def test_large_rows_other_ops(q, op):
+    N = 1 << 17
+    rows = 2
+    z = inputs.uniform_complex(rows, N, seed=op)
+    out = run(q, N, rows, q.KIND_C2C, q.DTYPE_F32, op, z, (rows, N), torch.complex64)
+    ref32 = {1: lambda: orc.icdft(z, fp32=True), 2: lambda: orc.cdft_adjoint(z, fp32=True),
+             3: lambda: orc.cdft(z, fp32=True) / N}[op]()
+    assert bits_equal(out, ref32.astype(np.complex64))
+
+
+@pytest.mark.parametrize("lg", [15, 18])
+def test_large_rows_real(q, lg):
+    N = 1 << lg
+    H = N // 2 + 1
+    rows = 3
+    x = inputs.normal_real(rows, N, seed=lg)
+    X = run(q, N, rows, q.KIND_R2C, q.DTYPE_F32, q.OP_FORWARD, x, (rows, H), torch.complex64)
+    assert bits_equal(X, orc.rdft(x, fp32=True).astype(np.complex64))
+    xr = run(q, N, rows, q.KIND_R2C, q.DTYPE_F32, q.OP_INVERSE, X, (rows, N), torch.float32)
+    assert bits_equal(xr, orc.irdft(X, N, fp32=True).astype(np.float32))
+
+
+def test_single_n2_24_forward_and_backward(q):
+    """One N = 2^24 complex64 transform, forward and backward (adjoint)."""
+    N = 1 << 24
+    z = inputs.normal_complex(1, N, seed=24)
+    X = run(q, N, 1, q.KIND_C2C, q.DTYPE_F32, q.OP_FORWARD, z, (1, N), torch.complex64)
+    assert bits_equal(X, orc.cdft(z, fp32=True).astype(np.complex64))
+    ref64 = orc.cdft(z)
+    assert rel_rows(X.astype(np.complex128), ref64).max() < tol(N)
+    g = run(q, N, 1, q.KIND_C2C, q.DTYPE_F32, q.OP_FORWARD_ADJOINT, z, (1, N), torch.complex64)
+    assert bits_equal(g, orc.cdft_adjoint(z, fp32=True).astype(np.complex64))
+
+
 # ------------------------------------------------ full benchmark sizes (sampled)
-@pytest.mark.parametrize("lg", [12, 14])
+@pytest.mark.parametrize("lg", [12, 14, 16, 18, 20])
 def test_full_size_batched_sampled(q, lg):
     """The batched 2^28-element workload at the benchmark's own launch
     configuration; sampled rows are compared one by one with the oracle."""
@@ -173,11 +225,11 @@ def test_full_size_batched_sampled(q, lg):
     X = torch.empty_like(z)
     p.execute(q.OP_FORWARD, z, X)
     torch.cuda.synchronize()
-    idx = np.unique(np.concatenate([[0, 1, rows - 2, rows - 1], g.integers(0, rows, 60)]))
+    idx = np.unique(np.concatenate([[0, 1, rows - 2, rows - 1], g.integers(0, rows, max(4, min(60, (1 << 22) // N)))]))
     zs = z[idx].cpu().numpy()
     Xs = X[idx].cpu().numpy()
     assert bits_equal(Xs, orc.cdft(zs, fp32=True).astype(np.complex64))
-    assert rel_rows(Xs.astype(np.complex128), orc.cdft(zs)).max() < TOL
+    assert rel_rows(Xs.astype(np.complex128), orc.cdft(zs)).max() < tol(N)
     del z, X
     torch.cuda.empty_cache()
 
