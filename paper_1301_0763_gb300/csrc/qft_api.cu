@@ -1,10 +1,11 @@
 // qft_api.cu -- the C ABI declared in include/qft_gb300.h: plan creation
-// (schedule, constant table), validation and dispatch to the kernels.
+// (schedule, constant table, scratch), validation and dispatch to the kernels.
 //
-// One CTA transforms one row (C2C) or one pair of real rows (R2C / C2R) at a
-// time, entirely in shared memory, and loops over rows (persistent grid).
-// The phases of a row are listed in a QftRowPlan built on the host at plan
-// creation (qft_planner.h) and copied to shared memory by every CTA.
+// Rows up to 2^14: one CTA transforms one row (C2C) or one pair of real rows
+// (R2C / C2R) at a time, entirely in shared memory, and loops over rows
+// (persistent grid); its phases are the QftRowPlan built at plan creation.
+// Longer rows: the launch sequence of qft_large.cuh over scratch copies.
+// Ragged plans: one sub-plan per row length, all captured in one CUDA graph.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -14,7 +15,7 @@
 #include <unordered_set>
 
 #include "qft_consts.h"
-#include "qft_engine.cuh"
+#include "qft_io.cuh"
 #include "qft_internal.h"
 
 using namespace qft;
@@ -50,6 +51,66 @@ static void free_resources(qft_plan p) {
   p->d_plan = nullptr; p->d_sec = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->large_host = nullptr;
 }
 
+// Fills a freshly allocated plan for `batch` rows of length 2^r: schedule,
+// constant table and scratch.  On failure everything it allocated is freed.
+static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
+  p->magic = kMagic; p->kind = kind; p->dtype = dtype; p->n = int64_t(1) << r; p->batch = batch; p->r = r;
+  p->d_plan = nullptr; p->d_sec = nullptr; p->last_cuda = cudaSuccess; p->last_stream = nullptr;
+  p->large_host = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->scratch_rows = 0; p->side_len = 0;
+  p->grid = 0; p->threads = 0; p->smem = 0;
+  p->nclasses = 0; p->classes = nullptr; p->d_offsets = nullptr; p->d_args = nullptr; p->h_args = nullptr;
+  p->graph = nullptr; p->gexec = nullptr; p->graph_kernels = 0;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) { return qft_set_cuda(p, e); }
+  if (r >= 2) {
+    p->tune = qft_default_tune(r);
+    p->tune.L1 = qft_lib::kL1;
+    p->tune.LB = qft_lib::kLB;
+    const int64_t N = int64_t(1) << r;
+    // FP32 secant table (Sec. 6.1), Gray order of the butterflies
+    const size_t nsec = (size_t)N / 4 + 1;
+    float* hsec = (float*)calloc(nsec, sizeof(float));
+    if (!hsec) return QFT_ERR_CUDA;
+    qft_fill_gray_secants(r, hsec);
+    e = cudaMalloc(&p->d_sec, sizeof(float) * nsec);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_sec, hsec, sizeof(float) * nsec, cudaMemcpyHostToDevice);
+    free(hsec);
+    if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); return rc; }
+    if (r <= qft_lib::kMaxRowLog2) {
+      p->threads = qft_default_threads(r);
+      if (qft_build_row_plan(r, p->tune, &p->host_plan) != 0 || p->host_plan.max_slice_nodes > p->threads) {
+        free_resources(p);
+        return QFT_ERR_INVALID_N;
+      }
+      e = cudaMalloc(&p->d_plan, sizeof(QftRowPlan));
+      if (e == cudaSuccess) e = cudaMemcpy(p->d_plan, &p->host_plan, sizeof(QftRowPlan), cudaMemcpyHostToDevice);
+      p->smem = qft_lib::row_smem_bytes((int)N, p->host_plan.LF);
+    } else {
+      p->large_host = (QftLargePlan*)malloc(sizeof(QftLargePlan));
+      if (!p->large_host ||
+          qft_build_large_plan(r, p->tune, qft_lib::kNodeLog2, qft_lib::kNodeThreads, p->large_host) != 0) {
+        free_resources(p);
+        return QFT_ERR_INVALID_N;
+      }
+      e = cudaMalloc(&p->d_large, sizeof(QftLargePlan));
+      if (e == cudaSuccess) e = cudaMemcpy(p->d_large, p->large_host, sizeof(QftLargePlan), cudaMemcpyHostToDevice);
+      p->side_len = qft_side_len((int)N);
+      const int64_t items = kind == QFT_KIND_R2C ? (batch + 1) / 2 : batch;
+      const int64_t per_row = 2 * 2 * (int64_t)p->side_len * 8;
+      int64_t rows = qft_lib::kScratchBudget / per_row;
+      if (rows > items) rows = items;
+      if (rows > 65535) rows = 65535;
+      if (rows < 1) rows = 1;
+      p->scratch_rows = rows;
+      p->threads = 256;
+      if (e == cudaSuccess && items > 0) e = cudaMalloc(&p->scratch, (size_t)(rows * per_row));
+    }
+    if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); return rc; }
+  }
+  return QFT_OK;
+}
+
 extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
   *out = nullptr;
@@ -66,68 +127,139 @@ extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind
 
   qft_plan p = new (std::nothrow) qft_plan_s();
   if (!p) return QFT_ERR_CUDA;
-  p->magic = kMagic; p->kind = kind; p->dtype = dtype; p->n = n; p->batch = batch; p->r = r;
-  p->d_plan = nullptr; p->d_sec = nullptr; p->last_cuda = cudaSuccess; p->last_stream = nullptr;
-  p->large_host = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->scratch_rows = 0; p->side_len = 0;
-  p->grid = 0; p->threads = 0; p->smem = 0;
-  cudaError_t e = cudaGetDevice(&p->device);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
-  if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); delete p; return rc; }
-  if (r >= 2) {
-    p->tune = qft_default_tune(r);
-    p->tune.L1 = qft_lib::kL1;
-    p->tune.LB = qft_lib::kLB;
-    const int64_t N = int64_t(1) << r;
-    // FP32 secant table (Sec. 6.1), Gray order of the butterflies
-    const size_t nsec = (size_t)N / 4 + 1;
-    float* hsec = (float*)calloc(nsec, sizeof(float));
-    if (!hsec) { delete p; return QFT_ERR_CUDA; }
-    qft_fill_gray_secants(r, hsec);
-    e = cudaMalloc(&p->d_sec, sizeof(float) * nsec);
-    if (e == cudaSuccess) e = cudaMemcpy(p->d_sec, hsec, sizeof(float) * nsec, cudaMemcpyHostToDevice);
-    free(hsec);
-    if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); delete p; return rc; }
-    if (r <= qft_lib::kMaxRowLog2) {
-      p->threads = qft_default_threads(r);
-      if (qft_build_row_plan(r, p->tune, &p->host_plan) != 0 || p->host_plan.max_slice_nodes > p->threads) {
-        free_resources(p); delete p;
-        return QFT_ERR_INVALID_N;
-      }
-      e = cudaMalloc(&p->d_plan, sizeof(QftRowPlan));
-      if (e == cudaSuccess) e = cudaMemcpy(p->d_plan, &p->host_plan, sizeof(QftRowPlan), cudaMemcpyHostToDevice);
-      p->smem = qft_lib::row_smem_bytes((int)N, p->host_plan.LF);
-    } else {
-      p->large_host = (QftLargePlan*)malloc(sizeof(QftLargePlan));
-      if (!p->large_host ||
-          qft_build_large_plan(r, p->tune, qft_lib::kNodeLog2, qft_lib::kNodeThreads, p->large_host) != 0) {
-        free_resources(p); delete p;
-        return QFT_ERR_INVALID_N;
-      }
-      e = cudaMalloc(&p->d_large, sizeof(QftLargePlan));
-      if (e == cudaSuccess) e = cudaMemcpy(p->d_large, p->large_host, sizeof(QftLargePlan), cudaMemcpyHostToDevice);
-      p->side_len = qft_side_len((int)N);
-      const int64_t items = kind == QFT_KIND_R2C ? (batch + 1) / 2 : batch;
-      const int64_t per_row = 2 * 2 * (int64_t)p->side_len * 8;
-      int64_t rows = qft_lib::kScratchBudget / per_row;
-      if (rows > items) rows = items;
-      if (rows > 65535) rows = 65535;
-      if (rows < 1) rows = 1;
-      p->scratch_rows = rows;
-      p->threads = 256;
-      if (e == cudaSuccess && items > 0) e = cudaMalloc(&p->scratch, (size_t)(rows * per_row));
-    }
-    if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); delete p; return rc; }
-  }
+  const int rc = plan_init(p, r, batch, kind, dtype);
+  if (rc != QFT_OK) { delete p; return rc; }
   register_plan(p);
   *out = p;
   return QFT_OK;
 }
 
+// Ragged plans: rows grouped by length, one (unregistered) sub-plan per length
+// class, and the class launches captured once into a CUDA graph that reads the
+// execute-time pointers from d_args.
+static void free_ragged(qft_plan p) {
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  for (int c = 0; c < p->nclasses; ++c) {
+    if (p->classes[c].sub) { free_resources(p->classes[c].sub); delete p->classes[c].sub; }
+    cudaFree(p->classes[c].d_rows);
+  }
+  free(p->classes);
+  cudaFree(p->d_offsets);
+  cudaFree(p->d_args);
+  p->classes = nullptr; p->nclasses = 0; p->d_offsets = nullptr; p->d_args = nullptr;
+  p->graph = nullptr; p->gexec = nullptr;
+}
+
+__global__ void k_set_args(QftIoArgs* d, QftIoArgs v) { *d = v; }
+
+static int ragged_launch_all(qft_plan p, cudaStream_t st) {
+  for (int c = 0; c < p->nclasses; ++c) {
+    const int rc = qft_launch_ragged_class(p->classes[c].sub, p->d_args, p->d_offsets, p->classes[c].d_rows, st);
+    if (rc != QFT_OK) { p->last_cuda = p->classes[c].sub->last_cuda; return rc; }
+  }
+  return QFT_OK;
+}
+
 extern "C" int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host, const int32_t* log2n_host,
                                       int64_t count, int kind, int dtype, unsigned flags) {
-  (void)offsets_host; (void)log2n_host; (void)count; (void)kind; (void)dtype; (void)flags;
-  if (out) *out = nullptr;
-  return QFT_ERR_INVALID_ARG;
+  if (!out) return QFT_ERR_NULLPTR;
+  *out = nullptr;
+  if (flags != 0) return QFT_ERR_INVALID_ARG;
+  if (kind != QFT_KIND_C2C || dtype != QFT_DTYPE_F32) return QFT_ERR_DTYPE;
+  if (count < 0 || count > (int64_t(1) << 31)) return QFT_ERR_INVALID_BATCH;
+  if (count > 0 && (!offsets_host || !log2n_host)) return QFT_ERR_NULLPTR;
+  if (count > 0 && offsets_host[0] != 0) return QFT_ERR_INVALID_ARG;
+  int64_t per_r[32] = {0};
+  for (int64_t i = 0; i < count; ++i) {
+    const int r = log2n_host[i];
+    if (r < 1 || r > qft_lib::kMaxLog2) return QFT_ERR_INVALID_N;
+    if (offsets_host[i + 1] - offsets_host[i] != (int64_t(1) << r)) return QFT_ERR_INVALID_ARG;
+    per_r[r]++;
+  }
+  qft_plan p = new (std::nothrow) qft_plan_s();
+  if (!p) return QFT_ERR_CUDA;
+  int rc = plan_init(p, 1, 0, kind, dtype);   // the container itself holds no kernels' resources
+  if (rc != QFT_OK) { delete p; return rc; }
+  p->n = 0; p->batch = count; p->r = 0;
+  int ncls = 0;
+  for (int r = 1; r <= qft_lib::kMaxLog2; ++r) ncls += per_r[r] > 0;
+  p->classes = (QftRaggedClass*)calloc(ncls > 0 ? ncls : 1, sizeof(QftRaggedClass));
+  if (!p->classes) { delete p; return QFT_ERR_CUDA; }
+  cudaError_t e = cudaSuccess;
+  // largest rows first: their launches are the longest
+  for (int r = qft_lib::kMaxLog2; r >= 1 && rc == QFT_OK; --r) {
+    if (!per_r[r]) continue;
+    QftRaggedClass& C = p->classes[p->nclasses++];
+    C.r = r; C.count = per_r[r]; C.d_rows = nullptr;
+    C.sub = new (std::nothrow) qft_plan_s();
+    if (!C.sub) { rc = QFT_ERR_CUDA; break; }
+    rc = plan_init(C.sub, r, C.count, kind, dtype);
+    if (rc != QFT_OK) { delete C.sub; C.sub = nullptr; break; }
+    int32_t* rows = (int32_t*)malloc(sizeof(int32_t) * (size_t)C.count);
+    if (!rows) { rc = QFT_ERR_CUDA; break; }
+    int64_t k = 0;
+    for (int64_t i = 0; i < count; ++i) if (log2n_host[i] == r) rows[k++] = (int32_t)i;
+    e = cudaMalloc(&C.d_rows, sizeof(int32_t) * (size_t)C.count);
+    if (e == cudaSuccess) e = cudaMemcpy(C.d_rows, rows, sizeof(int32_t) * (size_t)C.count, cudaMemcpyHostToDevice);
+    free(rows);
+    if (e != cudaSuccess) rc = qft_set_cuda(p, e);
+  }
+  if (rc == QFT_OK) {
+    e = cudaMalloc(&p->d_offsets, sizeof(int64_t) * (size_t)(count + 1));
+    if (e == cudaSuccess && count > 0)
+      e = cudaMemcpy(p->d_offsets, offsets_host, sizeof(int64_t) * (size_t)(count + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_args, sizeof(QftIoArgs));
+    if (e != cudaSuccess) rc = qft_set_cuda(p, e);
+  }
+  if (rc == QFT_OK && p->nclasses > 0) {
+    // capture every class launch once; executes replay the graph
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const int lrc = ragged_launch_all(p, cs);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+      if (lrc == QFT_OK && e2 == cudaSuccess) {
+        p->graph = g;
+        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        size_t nn = 0;
+        if (e == cudaSuccess) e = cudaGraphGetNodes(g, nullptr, &nn);
+        p->graph_kernels = (int)nn;
+      } else {
+        if (g) cudaGraphDestroy(g);
+        e = e2 != cudaSuccess ? e2 : cudaErrorUnknown;
+      }
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {   // no graph: executes launch the classes directly
+      if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
+      p->gexec = nullptr;
+      cudaGetLastError();
+    }
+  }
+  if (rc != QFT_OK) { free_ragged(p); free_resources(p); delete p; return rc; }
+  register_plan(p);
+  *out = p;
+  return QFT_OK;
+}
+
+static int exec_ragged(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
+  QftIoArgs a;
+  a.in = in; a.out = out; a.scale = 1.f; a.scaled = 0;
+  switch (op) {
+  case QFT_OP_FORWARD: a.in_op = QFT_LANE_ID; a.out_op = QFT_LANE_ID; break;
+  case QFT_OP_INVERSE: a.in_op = QFT_LANE_SWAP; a.out_op = QFT_LANE_SWAP; a.scaled = 2; break;
+  case QFT_OP_FORWARD_ADJOINT: a.in_op = QFT_LANE_CONJ; a.out_op = QFT_LANE_CONJ; break;
+  case QFT_OP_INVERSE_ADJOINT: a.in_op = QFT_LANE_ID; a.out_op = QFT_LANE_ID; a.scaled = 2; break;
+  default: return QFT_ERR_INVALID_ARG;
+  }
+  k_set_args<<<1, 1, 0, st>>>(p->d_args, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return qft_set_cuda(p, e);
+  if (p->gexec) return qft_set_cuda(p, cudaGraphLaunch(p->gexec, st));
+  return ragged_launch_all(p, st);
 }
 
 extern "C" int qft_plan_destroy(qft_plan p) {
@@ -139,6 +271,7 @@ extern "C" int qft_plan_destroy(qft_plan p) {
     g_live.erase(p);
     g_dead.insert(p);
   }
+  free_ragged(p);
   free_resources(p);
   p->magic = kDead;
   delete p;
@@ -165,6 +298,7 @@ extern "C" int qft_execute(qft_plan p, int op, const void* in, void* out, void* 
   cudaError_t e = cudaGetDevice(&cur);
   if (e != cudaSuccess) return qft_set_cuda(p, e);
   if (cur != p->device) return QFT_ERR_INVALID_ARG;
+  if (p->classes) return exec_ragged(p, op, in, out, st);
   if (p->kind == QFT_KIND_R2C) return qft_launch_real(p, op, in, out, st);
   switch (p->dtype) {
   case QFT_DTYPE_F32: return qft_launch_c2c_f32(p, op, in, out, st);
@@ -201,7 +335,7 @@ extern "C" int qft_plan_info(qft_plan p, int* threads, int* ctas, int* smem_byte
   if (threads) *threads = p->threads;
   if (ctas) *ctas = p->grid;
   if (smem_bytes) *smem_bytes = (int)p->smem;
-  if (launches) *launches = p->large_host ? p->large_host->nphase : 1;
+  if (launches) *launches = p->classes ? 1 + p->graph_kernels : (p->large_host ? p->large_host->nphase : 1);
   return QFT_OK;
 }
 

@@ -68,12 +68,14 @@ namespace qft {
 // ------------------------------------------------------------ arithmetic
 QFT_HD qc mkc(float x, float y) { qc r; r.x = x; r.y = y; return r; }
 
-// Packed two-lane FP32 instructions (add/sub/mul.rn.f32x2) are correctly
-// rounded lane by lane in isolation, but whole engine builds that use them did
-// not reproduce the FP32 evaluation of the recursion bit for bit on sm_103a,
-// while the scalar round-to-nearest intrinsics do; the scalar form is the
-// default and the packed form is kept behind QFT_PACKED_F32X2.
-#if defined(__CUDA_ARCH__) && defined(QFT_PACKED_F32X2)
+// Complex adds and subtracts use the packed two-lane FP32 instructions
+// (add/sub.rn.f32x2, one instruction per complex value); multiplies by a
+// secant or a scale use the scalar round-to-nearest intrinsic per lane.  With
+// both packed multiplies and packed adds in one kernel, sm_103a builds did not
+// reproduce the FP32 evaluation of the recursion bit for bit (each of the
+// three packed forms alone does, in isolation and in the whole engine), so
+// the packed multiply is not used.  QFT_SCALAR_ARITH selects scalar adds too.
+#if defined(__CUDA_ARCH__) && !defined(QFT_SCALAR_ARITH)
 QFT_HD qc cadd(qc a, qc b) {
   qc r;
   asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\t"
@@ -88,18 +90,12 @@ QFT_HD qc csub(qc a, qc b) {
       : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
   return r;
 }
-QFT_HD qc cmul(qc a, float s) {
-  qc r;
-  asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%4};\n\t"
-      "mul.rn.f32x2 rc, ra, rb;\n\tmov.b64 {%0,%1}, rc;\n}"
-      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(s));
-  return r;
-}
+QFT_HD qc cmul(qc a, float s) { return mkc(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
 QFT_HD float fmul(float a, float b) { return __fmul_rn(a, b); }
 QFT_HD float fadd(float a, float b) { return __fadd_rn(a, b); }
 QFT_HD float fsub(float a, float b) { return __fsub_rn(a, b); }
 #elif defined(__CUDA_ARCH__)
-// scalar round-to-nearest intrinsics (never contracted), one per lane (default)
+// scalar round-to-nearest intrinsics (never contracted), one per lane
 QFT_HD qc cadd(qc a, qc b) { return mkc(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
 QFT_HD qc csub(qc a, qc b) { return mkc(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
 QFT_HD qc cmul(qc a, float s) { return mkc(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
@@ -556,6 +552,53 @@ QFT_HD void run_plain_task(int LF, const QftSeg& sg, const Eng& e, const IO& io,
   case QFT_SEG_FIN_SPEC: task_fin_spec(e, io, LF, loc); break;
   default: break;
   }
+}
+
+// All of one thread's tasks of one segment: local task indices
+// l = first, first + step, ... < end (task index g*count + l).  The switch on
+// the task kind is taken once per segment; the loop body is specialised, so
+// the class geometry is loop-invariant.
+template <int L1, class IO>
+QFT_HD void run_plain_segment(int LF, const QftSeg& sg, const Eng& e, const IO& io, int first, int end,
+                              int step, int g) {
+  const int off = g * sg.count;
+#define QFT_LOOP(CALL) for (int l = first; l < end; l += step) { const int loc = off + l; (void)loc; CALL; }
+  switch (sg.type) {
+  case QFT_SEG_F1_BIG: QFT_LOOP(task_f1_big<L1>(e, io, sg.cls, loc)) break;
+  case QFT_SEG_F1_SMALL:
+    switch (sg.L) {
+    case 0: QFT_LOOP(task_f1_small<0>(e, io, sg.cls)) break;
+    case 1: QFT_LOOP(task_f1_small<1>(e, io, sg.cls)) break;
+    case 2: QFT_LOOP(task_f1_small<2>(e, io, sg.cls)) break;
+    case 3: QFT_LOOP(task_f1_small<3>(e, io, sg.cls)) break;
+    case 4: QFT_LOOP(task_f1_small<4>(e, io, sg.cls)) break;
+    default: break;
+    }
+    break;
+  case QFT_SEG_F1_BASE: QFT_LOOP(task_f1_base(e, io)) break;
+  case QFT_SEG_DIF:
+#define QFT_DIF_CASE(LL) case LL: if (sg.side) { QFT_LOOP((task_dif<LL, 1>(e, sg.cls, sg.D, loc))) } else { QFT_LOOP((task_dif<LL, 0>(e, sg.cls, sg.D, loc))) } break;
+    switch (sg.L) { QFT_DIF_CASE(1) QFT_DIF_CASE(2) QFT_DIF_CASE(3) QFT_DIF_CASE(4) default: break; }
+#undef QFT_DIF_CASE
+    break;
+  case QFT_SEG_LEAF:
+#define QFT_LEAF_CASE(LL) case LL: if (sg.side) { QFT_LOOP((task_leaf<LL, 1>(e, sg.cls, loc))) } else { QFT_LOOP((task_leaf<LL, 0>(e, sg.cls, loc))) } break;
+    switch (sg.L) { QFT_LEAF_CASE(1) QFT_LEAF_CASE(2) QFT_LEAF_CASE(3) QFT_LEAF_CASE(4) default: break; }
+#undef QFT_LEAF_CASE
+    break;
+  case QFT_SEG_FIN_REG:
+    switch (LF) {
+    case 0: QFT_LOOP(task_fin_reg<0>(e, io, loc + 1)) break;
+    case 1: QFT_LOOP(task_fin_reg<1>(e, io, loc + 1)) break;
+    case 2: QFT_LOOP(task_fin_reg<2>(e, io, loc + 1)) break;
+    case 3: QFT_LOOP(task_fin_reg<3>(e, io, loc + 1)) break;
+    default: break;
+    }
+    break;
+  case QFT_SEG_FIN_SPEC: QFT_LOOP(task_fin_spec(e, io, LF, loc)) break;
+  default: break;
+  }
+#undef QFT_LOOP
 }
 
 QFT_HD void run_slice_read(const QftSeg& sg, const Eng& e, int loc, SliceRegs& s) {

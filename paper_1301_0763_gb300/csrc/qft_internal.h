@@ -6,6 +6,24 @@
 #include "qft_planner.h"
 #include "../../include/qft_gb300.h"
 
+// Execute-time arguments of a ragged plan, read by its kernels from device
+// memory so that the captured CUDA graph stays valid across executes.
+struct QftIoArgs {
+  const void* in;
+  void* out;
+  int in_op, out_op;
+  float scale;
+  int scaled;
+};
+
+struct qft_plan_s;
+struct QftRaggedClass {
+  int r;                 // log2 N of the rows of this class
+  int64_t count;         // rows
+  int32_t* d_rows;       // row indices (device)
+  qft_plan_s* sub;       // plan of `count` rows of length 2^r (not registered)
+};
+
 // complex cell storage of the scratch copies (layout of qft::qc)
 struct __align__(8) qc_storage { float x, y; };
 
@@ -45,6 +63,15 @@ struct qft_plan_s {
   qc_storage* scratch;
   int64_t scratch_rows;
   int side_len;
+  // ragged plans (qft_plan_create_ragged)
+  int nclasses;
+  QftRaggedClass* classes;
+  int64_t* d_offsets;
+  QftIoArgs* d_args;
+  QftIoArgs* h_args;          // pinned host staging of the arguments
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+  int graph_kernels;
   size_t smem;
   int device;
   int sms;
@@ -64,3 +91,5 @@ int qft_launch_c2c_f32(qft_plan p, int op, const void* in, void* out, cudaStream
 int qft_launch_c2c_f16(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
 int qft_launch_c2c_bf16(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
 int qft_launch_real(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
+int qft_launch_ragged_class(qft_plan sub, const QftIoArgs* d_args, const int64_t* d_offsets,
+                            const int32_t* d_rows, cudaStream_t st);

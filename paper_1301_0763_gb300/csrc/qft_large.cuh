@@ -46,15 +46,17 @@ __global__ void __launch_bounds__(kLargeNT, 2) k_large_global(LargeArgs a, int p
   const int64_t row = blockIdx.y;
   const Eng e = large_eng(a, 0, row);
   const auto io = fac.make(a.row0 + row);
-  const int t0 = blockIdx.x * (kLargeNT * kLargeTPT);
-  int sgi = ph.seg0;
-  const int sge = ph.seg0 + ph.nseg;
-  for (int k = 0; k < kLargeTPT; ++k) {
-    const int tau = t0 + k * kLargeNT + (int)threadIdx.x;
-    if (tau >= ph.ntasks) break;
-    while (sgi + 1 < sge && P->segs[sgi + 1].begin <= tau) ++sgi;
-    const QftSeg sg = P->segs[sgi];
-    run_plain_task<L1>(P->LF, sg, e, io, tau - sg.begin);
+  // this thread's tasks: T0 + k * kLargeNT, k < kLargeTPT, T0 = block start + tid
+  const int T0 = blockIdx.x * (kLargeNT * kLargeTPT) + (int)threadIdx.x;
+  const int T1 = blockIdx.x * (kLargeNT * kLargeTPT) + kLargeNT * kLargeTPT;
+  for (int s = ph.seg0; s < ph.seg0 + ph.nseg; ++s) {
+    const QftSeg sg = P->segs[s];
+    if (sg.begin >= T1 || sg.begin + sg.count <= T0 - (int)threadIdx.x) continue;
+    int first = T0 - sg.begin;
+    if (first < 0) first += ((-first + kLargeNT - 1) / kLargeNT) * kLargeNT;
+    int end = T1 - sg.begin;
+    if (end > sg.count) end = sg.count;
+    run_plain_segment<L1>(P->LF, sg, e, io, first, end, kLargeNT, 0);
   }
 }
 
@@ -182,6 +184,28 @@ static inline int launch_any(qft_plan p, FAC fac, int64_t items, cudaStream_t st
 }
 
 }  // namespace
+
+// N = 2 rows of a ragged plan
+__global__ void k_ragged_n2(FacRaggedC2C<StC64> fac, int64_t rows) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= rows) return;
+  const auto io = fac.make(row);
+  const qc a = io.ld(0), b = io.ld(1);
+  io.st(0, cadd(a, b));
+  io.st(1, csub(a, b));
+}
+
+static inline int exec_ragged_class(qft_plan sub, const QftIoArgs* d_args, const int64_t* d_offsets,
+                                    const int32_t* d_rows, cudaStream_t st) {
+  FacRaggedC2C<StC64> f;
+  f.args = d_args; f.offsets = d_offsets; f.rows = d_rows; f.N = (int)sub->n;
+  if (sub->r == 1) {
+    const int64_t blocks = (sub->batch + 127) / 128;
+    k_ragged_n2<<<(unsigned)blocks, 128, 0, st>>>(f, sub->batch);
+    return qft_set_cuda(sub, cudaGetLastError());
+  }
+  return launch_any<FacRaggedC2C<StC64>>(sub, f, sub->batch, st);
+}
 
 template <class ST>
 static inline int exec_c2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {

@@ -26,6 +26,27 @@ struct FacC2C {
   }
 };
 
+// Ragged C2C: item i is row rows[i] of a packed buffer, at complex offset
+// offsets[row]; pointers and lane operations come from device memory.
+template <class ST>
+struct FacRaggedC2C {
+  const QftIoArgs* args;
+  const int64_t* offsets;
+  const int32_t* rows;
+  int N;
+  __device__ __forceinline__ IoC2C<ST> make(int64_t item) const {
+    IoC2C<ST> io;
+    const int64_t off = offsets[rows[item]];
+    io.in = static_cast<const typename ST::elem*>(args->in) + off;
+    io.out = static_cast<typename ST::elem*>(args->out) + off;
+    // scaled == 2: scale by 1/N of this row's own length (inverse-type ops)
+    io.N = N; io.in_op = args->in_op; io.out_op = args->out_op;
+    io.scale = args->scaled == 2 ? 1.f / (float)N : args->scale;
+    io.scaled = args->scaled != 0;
+    return io;
+  }
+};
+
 template <class ST>
 struct FacR2C {
   const float* in;

@@ -123,6 +123,30 @@ class Plan:
             pass
 
 
+class RaggedPlan(Plan):
+    """Many C2C transforms of uneven power-of-two lengths in one packed buffer
+    (see qft_plan_create_ragged): row i occupies complex elements
+    [offsets[i], offsets[i+1]) and has length 2^log2n[i].  One execute is one
+    CUDA-graph launch of every length class."""
+
+    def __init__(self, offsets, log2n, device=None):
+        import numpy as np
+        self.lib = load_library()
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        lg = np.ascontiguousarray(np.asarray(log2n, dtype=np.int32))
+        self.count = int(lg.shape[0])
+        self.total = int(off[-1]) if off.size else 0
+        self.n, self.batch, self.kind, self.dtype = 0, self.count, KIND_C2C, DTYPE_F32
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.qft_plan_create_ragged(
+                ctypes.byref(self.handle), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                lg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.count, KIND_C2C, DTYPE_F32, 0),
+                "qft_plan_create_ragged")
+
+
 _plans: dict = {}
 
 

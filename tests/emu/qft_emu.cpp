@@ -28,14 +28,16 @@ static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr, i
     }
     if (!P.phase_is_slice[p]) {
       for (int tid = 0; tid < nthr; ++tid)
-        for (int tau = tid; tau < nt; tau += nthr) {
-          const QftSeg& sg = find_seg(P, p, tau);
+        for (int s = P.phase_seg0[p]; s < P.phase_seg0[p + 1]; ++s) {
+          const QftSeg& sg = P.segs[s];
+          int first = (tid - sg.begin) % nthr;
+          if (first < 0) first += nthr;
           switch (P.L1) {
-          case 0: run_plain_task<0>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
-          case 1: run_plain_task<1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
-          case 2: run_plain_task<2>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
-          case 3: run_plain_task<3>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
-          default: run_plain_task<4>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+          case 0: run_plain_segment<0>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
+          case 1: run_plain_segment<1>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
+          case 2: run_plain_segment<2>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
+          case 3: run_plain_segment<3>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
+          default: run_plain_segment<4>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
           }
         }
     } else {
@@ -174,11 +176,21 @@ static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vecto
     const QftLargePhase& P = LP.phases[ph];
     if (P.kind == QFT_LPH_GLOBAL) {
       const Eng e = eng(0);
-      for (int tau = 0; tau < P.ntasks; ++tau) {
-        int s = P.seg0;
-        while (s + 1 < P.seg0 + P.nseg && LP.segs[s + 1].begin <= tau) ++s;
-        run_plain_task<3>(LP.LF, LP.segs[s], e, io, tau - LP.segs[s].begin);
-      }
+      const int NT = 256, TPT = 4;
+      const int nblk = (P.ntasks + NT * TPT - 1) / (NT * TPT);
+      for (int bx = 0; bx < nblk; ++bx)
+        for (int tid = 0; tid < NT; ++tid) {
+          const int T0 = bx * NT * TPT + tid, T1 = bx * NT * TPT + NT * TPT;
+          for (int s = P.seg0; s < P.seg0 + P.nseg; ++s) {
+            const QftSeg& sg = LP.segs[s];
+            if (sg.begin >= T1 || sg.begin + sg.count <= T0 - tid) continue;
+            int first = T0 - sg.begin;
+            if (first < 0) first += ((-first + NT - 1) / NT) * NT;
+            int end = T1 - sg.begin;
+            if (end > sg.count) end = sg.count;
+            run_plain_segment<3>(LP.LF, sg, e, io, first, end, NT, 0);
+          }
+        }
     } else if (P.kind == QFT_LPH_SLICE) {
       for (int tau = 0; tau < P.ntasks; ++tau) {
         int s = P.seg0;

@@ -270,3 +270,46 @@ def test_errors_through_the_abi(q):
     p0.execute(q.OP_FORWARD, bad, bad)
     p0.destroy()
     del bad
+
+
+# ------------------------------------------------------------------ ragged
+def _ragged_check(q, log2n, seed, op=0, sample=None):
+    off = inputs.ragged_offsets(log2n)
+    total = int(off[-1])
+    z = inputs.ragged_values(total, seed=seed)
+    p = q.RaggedPlan(off, log2n)
+    zin = gpu(z)
+    out = torch.empty_like(zin)
+    p.execute(op, zin, out)
+    torch.cuda.synchronize()
+    rows = range(len(log2n)) if sample is None else sample
+    X = None
+    for i in rows:
+        a, b = int(off[i]), int(off[i + 1])
+        xi = out[a:b].cpu().numpy()
+        zi = z[a:b]
+        ref = {0: lambda: orc.cdft(zi, fp32=True), 1: lambda: orc.icdft(zi, fp32=True)}[op]()
+        assert bits_equal(xi, ref.astype(np.complex64)), (i, log2n[i])
+    p.destroy()
+
+
+def test_ragged_small_mix(q):
+    """Every length 2..2^17 (and repeats) packed in one buffer, one graph launch."""
+    g = inputs.rng(31)
+    log2n = np.concatenate([np.arange(1, 18), g.integers(1, 15, 40)]).astype(np.int32)
+    g.shuffle(log2n)
+    _ragged_check(q, log2n, seed=31)
+    _ragged_check(q, log2n, seed=32, op=1)
+
+
+def test_ragged_full_workload_sampled(q):
+    """4096 rows with log2 N uniform on 4..20 (the uneven-batch workload),
+    sampled rows checked one by one against the oracle."""
+    log2n = inputs.ragged_log2n(4096, seed=2)
+    g = inputs.rng(33)
+    big = np.nonzero(log2n >= 18)[0]
+    small = np.nonzero(log2n < 18)[0]
+    sample = sorted(set(g.choice(small, 40, replace=False).tolist()) | set(g.choice(big, 6, replace=False).tolist())
+                    | {0, 4095})
+    _ragged_check(q, log2n, seed=2, sample=sample)
+    torch.cuda.empty_cache()
