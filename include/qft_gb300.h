@@ -89,7 +89,10 @@ int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype
 
 /*
  * qft_plan_create_ragged -- plan many independent C2C transforms of uneven
- * power-of-two lengths, executed by one persistent launch.
+ * power-of-two lengths.  Rows are grouped by length at plan creation (one
+ * schedule per length); every execute replays one CUDA graph holding the
+ * launches of all length classes (it reads the data pointers from device
+ * memory, so the graph is captured once, here).
  *   offsets_host  count+1 int64 entries (host memory): row i occupies complex
  *                 elements [offsets[i], offsets[i+1]) of the packed buffer;
  *                 offsets[0] == 0 and offsets[i+1]-offsets[i] == 2^log2n[i].
@@ -120,6 +123,30 @@ int qft_execute(qft_plan plan, int op, const void* in, void* out, void* stream);
 int qft_execute_forward(qft_plan plan, const void* in, void* out, void* stream);
 int qft_execute_inverse(qft_plan plan, const void* in, void* out, void* stream);
 int qft_execute_backward(qft_plan plan, const void* grad_out, void* grad_in, void* stream);
+
+/*
+ * Spectral-filter layer y = irfft(W (.) rfft(x)) on real rows: rfft is the
+ * rdft of Sec. 4.2, irfft the real inverse x(n) = (A(n) - B(n))/N,
+ * x(N-n) = (A(n) + B(n))/N with A, B the DCT-0 / DST-0 (eqs qft_0B, qft_0C)
+ * of the weighted real and imaginary parts; W is applied bin by bin.
+ *   qft_filter_create: plan for x, y of shape [batch][channels][n] (float32,
+ *     device, contiguous) and weights W of shape [channels][n/2+1] (complex64).
+ *     4 <= n <= 2^13 power of two; batch, channels >= 1.  The plan owns a
+ *     scratch of channels * 4 * (n/2+1) complex partial gradients.
+ *   qft_filter_forward:  y = irfft(W[c] (.) rfft(x[b][c])) for every b, c.
+ *   qft_filter_backward: given x, W and gy = dL/dy, writes
+ *     gx = dL/dx = rfft^H(conj(W) (.) irfft^H(gy))  (shape of x) and
+ *     gW = dL/dW = sum_b irfft^H(gy[b]) (.) conj(rfft(x[b]))  ([channels][n/2+1]),
+ *     with the complex-gradient convention dL/dRe + i dL/dIm; the batch sum
+ *     is done in a fixed order (deterministic).  Nothing from the forward
+ *     pass is needed.
+ * Pointers: x, y, gy, gx 4-byte aligned; W, gW 8-byte aligned; y (gx) must not
+ * alias x or gy.  Same status codes as qft_execute.
+ */
+int qft_filter_create(qft_plan* out, int64_t n, int64_t batch, int64_t channels, unsigned flags);
+int qft_filter_forward(qft_plan plan, const float* x, const void* W, float* y, void* stream);
+int qft_filter_backward(qft_plan plan, const float* x, const void* W, const float* gy, float* gx, void* gW,
+                        void* stream);
 
 /* Releases every resource of the plan.  Safe on NULL.  A destroyed plan must
  * not be used again; the library detects most such uses (QFT_ERR_DESTROYED). */

@@ -241,3 +241,39 @@ def brute_dft(z) -> np.ndarray:
 
 if __name__ == "__main__":  # pragma: no cover - manual build helper
     print(build(force="--force" in sys.argv))
+
+
+# ------------------------------------------------------------ spectral filter
+def filter_forward(x, W, fp32: bool = False) -> np.ndarray:
+    """y = irfft(W (.) rfft(x)) for x [B, C, N] (real) and W [C, N/2+1] (complex),
+    by the oracle's rdft / real inverse.  With fp32=True the transforms run in
+    FP32 and the product is re = wr*xr - wi*xi, im = wr*xi + wi*xr with every
+    operation rounded to FP32 separately."""
+    x = np.asarray(x, dtype=np.float64)
+    N = x.shape[-1]
+    X = rdft(x.reshape(-1, N), fp32=fp32).reshape(x.shape[:-1] + (N // 2 + 1,))
+    if fp32:
+        f = np.float32
+        Xr, Xi = X.real.astype(f), X.imag.astype(f)
+        Wr, Wi = np.asarray(W).real.astype(f), np.asarray(W).imag.astype(f)
+        Yr = (Wr * Xr).astype(f) - (Wi * Xi).astype(f)
+        Yi = (Wr * Xi).astype(f) + (Wi * Xr).astype(f)
+        Y = Yr.astype(np.float64) + 1j * Yi.astype(np.float64)
+    else:
+        Y = np.asarray(W, dtype=np.complex128) * X
+    return irdft(Y.reshape(-1, N // 2 + 1), N, fp32=fp32).reshape(x.shape)
+
+
+def filter_backward(x, W, gy):
+    """(gx, gW) of the filter layer for the upstream gradient gy (FP64):
+    gx = rfft^H(conj(W) (.) irfft^H(gy)), gW = sum_b irfft^H(gy_b) (.) conj(rfft(x_b))."""
+    x = np.asarray(x, dtype=np.float64)
+    gy = np.asarray(gy, dtype=np.float64)
+    B, C, N = x.shape
+    H = N // 2 + 1
+    G = irdft_adjoint(gy.reshape(-1, N)).reshape(B, C, H)
+    X = rdft(x.reshape(-1, N)).reshape(B, C, H)
+    gW = (G * np.conj(X)).sum(axis=0)
+    gX = np.conj(np.asarray(W, dtype=np.complex128))[None] * G
+    gx = rdft_adjoint(gX.reshape(-1, H), N).reshape(B, C, N)
+    return gx, gW

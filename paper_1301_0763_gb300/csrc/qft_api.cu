@@ -43,6 +43,8 @@ static int plan_check(qft_plan p) {
 }
 
 static void free_resources(qft_plan p) {
+  cudaFree(p->d_status);
+  p->d_status = nullptr;
   cudaFree(p->d_plan);
   cudaFree(p->d_sec);
   cudaFree(p->d_large);
@@ -60,9 +62,13 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
   p->grid = 0; p->threads = 0; p->smem = 0;
   p->nclasses = 0; p->classes = nullptr; p->d_offsets = nullptr; p->d_args = nullptr; p->h_args = nullptr;
   p->graph = nullptr; p->gexec = nullptr; p->graph_kernels = 0;
+  p->d_status = nullptr;
+  p->channels = 0;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
-  if (e != cudaSuccess) { return qft_set_cuda(p, e); }
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); return rc; }
   if (r >= 2) {
     p->tune = qft_default_tune(r);
     p->tune.L1 = qft_lib::kL1;
@@ -262,6 +268,63 @@ static int exec_ragged(qft_plan p, int op, const void* in, void* out, cudaStream
   return ragged_launch_all(p, st);
 }
 
+// ---------------------------------------------------------- spectral filter
+static const int kKindFilter = 2;   // internal kind of filter plans
+
+extern "C" int qft_filter_create(qft_plan* out, int64_t n, int64_t batch, int64_t channels, unsigned flags) {
+  if (!out) return QFT_ERR_NULLPTR;
+  *out = nullptr;
+  if (flags != 0) return QFT_ERR_INVALID_ARG;
+  if (n < 4 || (n & (n - 1)) != 0 || n > (int64_t(1) << 13)) return QFT_ERR_INVALID_N;
+  if (batch < 1 || channels < 1 || batch > (int64_t(1) << 24) || channels > (int64_t(1) << 20))
+    return QFT_ERR_INVALID_BATCH;
+  int r = 0;
+  while ((int64_t(1) << r) < n) ++r;
+  qft_plan p = new (std::nothrow) qft_plan_s();
+  if (!p) return QFT_ERR_CUDA;
+  int rc = plan_init(p, r, batch, QFT_KIND_R2C, QFT_DTYPE_F32);
+  if (rc != QFT_OK) { delete p; return rc; }
+  p->kind = kKindFilter;
+  p->channels = channels;
+  // partial weight gradients [C][parts][n/2+1] (complex)
+  const size_t bytes = (size_t)channels * qft_filter_parts() * (size_t)(n / 2 + 1) * 8;
+  cudaError_t e = cudaMalloc(&p->scratch, bytes);
+  if (e != cudaSuccess) { rc = qft_set_cuda(p, e); free_resources(p); delete p; return rc; }
+  register_plan(p);
+  *out = p;
+  return QFT_OK;
+}
+
+static int filter_check(qft_plan p, const void* a, const void* b, const void* c) {
+  int rc = plan_check(p);
+  if (rc != QFT_OK) return rc;
+  if (p->kind != kKindFilter) return QFT_ERR_INVALID_ARG;
+  if (!a || !b || !c) return QFT_ERR_NULLPTR;
+  return QFT_OK;
+}
+
+extern "C" int qft_filter_forward(qft_plan p, const float* x, const void* W, float* y, void* stream) {
+  int rc = filter_check(p, x, W, y);
+  if (rc != QFT_OK) return rc;
+  if (((uintptr_t)x % 4) || ((uintptr_t)y % 4) || ((uintptr_t)W % 8)) return QFT_ERR_ALIGN;
+  if ((const void*)x == (const void*)y) return QFT_ERR_INPLACE;
+  p->last_stream = static_cast<cudaStream_t>(stream);
+  return qft_launch_filter(p, 0, x, W, nullptr, y, nullptr, p->last_stream);
+}
+
+extern "C" int qft_filter_backward(qft_plan p, const float* x, const void* W, const float* gy, float* gx, void* gW,
+                                   void* stream) {
+  int rc = filter_check(p, x, W, gy);
+  if (rc != QFT_OK) return rc;
+  if (!gx || !gW) return QFT_ERR_NULLPTR;
+  if (((uintptr_t)x % 4) || ((uintptr_t)gy % 4) || ((uintptr_t)gx % 4) || ((uintptr_t)W % 8) ||
+      ((uintptr_t)gW % 8))
+    return QFT_ERR_ALIGN;
+  if ((const void*)gx == (const void*)gy || (const void*)gx == (const void*)x) return QFT_ERR_INPLACE;
+  p->last_stream = static_cast<cudaStream_t>(stream);
+  return qft_launch_filter(p, 1, x, W, gy, gx, gW, p->last_stream);
+}
+
 extern "C" int qft_plan_destroy(qft_plan p) {
   if (!p) return QFT_OK;
   int rc = plan_check(p);
@@ -298,6 +361,7 @@ extern "C" int qft_execute(qft_plan p, int op, const void* in, void* out, void* 
   cudaError_t e = cudaGetDevice(&cur);
   if (e != cudaSuccess) return qft_set_cuda(p, e);
   if (cur != p->device) return QFT_ERR_INVALID_ARG;
+  if (p->kind == kKindFilter) return QFT_ERR_INVALID_ARG;
   if (p->classes) return exec_ragged(p, op, in, out, st);
   if (p->kind == QFT_KIND_R2C) return qft_launch_real(p, op, in, out, st);
   switch (p->dtype) {
@@ -321,7 +385,21 @@ extern "C" int qft_execute_backward(qft_plan p, const void* grad_out, void* grad
 extern "C" int qft_plan_sync_status(qft_plan p) {
   int rc = plan_check(p);
   if (rc != QFT_OK) return rc;
-  return qft_set_cuda(p, cudaStreamSynchronize(p->last_stream));
+  rc = qft_set_cuda(p, cudaStreamSynchronize(p->last_stream));
+  if (rc != QFT_OK) return rc;
+  // the plan's own status word and those of its sub-plans (ragged)
+  int st = 0;
+  rc = qft_set_cuda(p, cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (rc != QFT_OK) return rc;
+  cudaMemset(p->d_status, 0, sizeof(int));
+  for (int c = 0; c < p->nclasses && st == 0; ++c) {
+    int sc = 0;
+    if (cudaMemcpy(&sc, p->classes[c].sub->d_status, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && sc) {
+      st = sc;
+      cudaMemset(p->classes[c].sub->d_status, 0, sizeof(int));
+    }
+  }
+  return st;
 }
 
 extern "C" int qft_plan_last_cuda_error(qft_plan p) {

@@ -57,6 +57,8 @@ struct qft_plan_s {
   float* d_sec;
   int grid;
   int threads;
+  int* d_status;              // device status word (QFT_OK or QFT_ERR_TIMEOUT)
+  int64_t channels;           // spectral-filter plans: C (batch holds B)
   // large-row path (N > 2^kMaxRowLog2): schedule, scratch copies A and B
   QftLargePlan* large_host;
   QftLargePlan* d_large;
@@ -91,5 +93,9 @@ int qft_launch_c2c_f32(qft_plan p, int op, const void* in, void* out, cudaStream
 int qft_launch_c2c_f16(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
 int qft_launch_c2c_bf16(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
 int qft_launch_real(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
+int qft_launch_filter(qft_plan p, int backward, const float* x, const void* W, const float* gy, float* out,
+                      void* gW, cudaStream_t st);
+int qft_filter_smem(int N, int LF, int backward);
+int qft_filter_parts();
 int qft_launch_ragged_class(qft_plan sub, const QftIoArgs* d_args, const int64_t* d_offsets,
                             const int32_t* d_rows, cudaStream_t st);

@@ -199,3 +199,108 @@ struct IoC2R {
 };
 
 }  // namespace qft
+
+// --------------------------------------------------------- spectral filter
+// Layer y = irfft(W (.) rfft(x)) on row pairs (a, b) of one channel c.  The
+// spectrum stays in shared memory between the forward (R2C) and the inverse
+// (C2R) transform of the pair.  Complex products are evaluated as
+// re = wr*xr - wi*xi, im = wr*xi + wi*xr, each operation rounded separately.
+namespace qft {
+
+QFT_HD qc cmulc(qc w, qc x) {   // w * x
+  return mkc(fsub(fmul(w.x, x.x), fmul(w.y, x.y)), fadd(fmul(w.x, x.y), fmul(w.y, x.x)));
+}
+QFT_HD qc cmulcj(qc w, qc x) {  // conj(w) * x
+  return mkc(fadd(fmul(w.x, x.x), fmul(w.y, x.y)), fsub(fmul(w.x, x.y), fmul(w.y, x.x)));
+}
+
+// R2C of rows a, b whose spectrum goes to shared memory (spa, spb: N/2+1 cells),
+// optionally weighted like the adjoint of the real inverse (wscale != 0:
+// w_k * wscale, w = 1 at k = 0, N/2 and 2 elsewhere, Im = 0 at k = 0, N/2).
+struct IoR2CSpec {
+  const float* ina;
+  const float* inb;   // may be null
+  qc* spa;
+  qc* spb;
+  int N;
+  float wscale;
+  QFT_HD qc ld(int n) const { return mkc(ina[n], inb ? inb[n] : 0.f); }
+  QFT_HD void get_cd(int n, qc& c, qc& d) const {
+    const qc a = ld(n), b = ld(N - n);
+    c = cadd(a, b);
+    d = csub(a, b);
+  }
+  QFT_HD qc get_c(int n) const { return ld(n); }
+  QFT_HD void emit(int k, qc C, qc S) const {
+    qc xa, xb;
+    if (k == 0 || 2 * k == N) { xa = mkc(C.x, 0.f); xb = mkc(C.y, 0.f); }
+    else { xa = mkc(C.x, -S.x); xb = mkc(C.y, -S.y); }
+    if (wscale != 0.f) {
+      const float w = (k == 0 || 2 * k == N) ? wscale : fmul(2.f, wscale);
+      xa = mkc(fmul(xa.x, w), fmul(xa.y, w));
+      xb = mkc(fmul(xb.x, w), fmul(xb.y, w));
+    }
+    spa[k] = xa;
+    spb[k] = xb;
+  }
+};
+
+// R2C of rows a, b (the layer input) that accumulates the weight gradient:
+// acc[k] += G_a(k) conj(X_a(k)) + G_b(k) conj(X_b(k)), G from shared memory.
+struct IoR2CAccum {
+  const float* ina;
+  const float* inb;   // may be null
+  const qc* ga;
+  const qc* gb;
+  qc* acc;
+  int N;
+  QFT_HD qc ld(int n) const { return mkc(ina[n], inb ? inb[n] : 0.f); }
+  QFT_HD void get_cd(int n, qc& c, qc& d) const {
+    const qc a = ld(n), b = ld(N - n);
+    c = cadd(a, b);
+    d = csub(a, b);
+  }
+  QFT_HD qc get_c(int n) const { return ld(n); }
+  QFT_HD void emit(int k, qc C, qc S) const {
+    qc xa, xb;
+    if (k == 0 || 2 * k == N) { xa = mkc(C.x, 0.f); xb = mkc(C.y, 0.f); }
+    else { xa = mkc(C.x, -S.x); xb = mkc(C.y, -S.y); }
+    qc s = cadd(acc[k], cmulcj(xa, ga[k]));   // G conj(X) = conj(X) * G
+    if (inb) s = cadd(s, cmulcj(xb, gb[k]));
+    acc[k] = s;
+  }
+};
+
+// C2R of rows a, b whose half spectra are w (.) sp (conj(w) (.) sp if conjw),
+// with w the channel's weights (global), sp in shared memory.
+struct IoC2RFilt {
+  const qc* spa;
+  const qc* spb;   // may be null
+  const qc* w;
+  bool conjw;
+  float* outa;
+  float* outb;     // may be null
+  int N;
+  float wmid, scale;
+  QFT_HD qc ya(int n) const { return conjw ? cmulcj(w[n], spa[n]) : cmulc(w[n], spa[n]); }
+  QFT_HD qc yb(int n) const { return spb ? (conjw ? cmulcj(w[n], spb[n]) : cmulc(w[n], spb[n])) : mkc(0.f, 0.f); }
+  QFT_HD void get_cd(int n, qc& c, qc& d) const {
+    const qc a = ya(n), b = yb(n);
+    c = mkc(fmul(wmid, a.x), fmul(wmid, b.x));
+    d = mkc(fmul(wmid, a.y), fmul(wmid, b.y));
+  }
+  QFT_HD qc get_c(int n) const { return mkc(ya(n).x, yb(n).x); }
+  QFT_HD void emit(int k, qc A, qc B) const {
+    if (k == 0 || 2 * k == N) {
+      outa[k] = fmul(A.x, scale);
+      if (outb) outb[k] = fmul(A.y, scale);
+      return;
+    }
+    const qc lo = csub(A, B), hi = cadd(A, B);
+    outa[k] = fmul(lo.x, scale);
+    outa[N - k] = fmul(hi.x, scale);
+    if (outb) { outb[k] = fmul(lo.y, scale); outb[N - k] = fmul(hi.y, scale); }
+  }
+};
+
+}  // namespace qft

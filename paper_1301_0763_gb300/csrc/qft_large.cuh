@@ -178,9 +178,10 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
 }
 
 template <class FAC>
-static inline int launch_any(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
+static inline int launch_any(qft_plan p, FAC fac, int64_t items, cudaStream_t st, size_t stage_bytes = 0,
+                             bool stage_ok = false) {
   if (p->large_host) return launch_large<FAC>(p, fac, items, st);
-  return launch_rows<FAC>(p, fac, items, st);
+  return launch_rows<FAC>(p, fac, items, st, stage_bytes, stage_ok);
 }
 
 }  // namespace
@@ -226,7 +227,8 @@ static inline int exec_c2c(qft_plan p, int op, const void* in, void* out, cudaSt
     k_c2c_n2<ST><<<(unsigned)blocks, 128, 0, st>>>(f, p->batch);
     return qft_set_cuda(p, cudaGetLastError());
   }
-  return launch_any<FacC2C<ST>>(p, f, p->batch, st);
+  return launch_any<FacC2C<ST>>(p, f, p->batch, st, (size_t)p->n * sizeof(typename ST::elem),
+                                ((uintptr_t)in % 16) == 0);
 }
 
 static inline int exec_r2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
@@ -238,7 +240,7 @@ static inline int exec_r2c(qft_plan p, int op, const void* in, void* out, cudaSt
     f.out = static_cast<qc*>(out);
     f.rows = p->batch; f.N = N;
     f.wscale = op == QFT_OP_FORWARD ? 0.f : 1.f / (float)N;
-    return launch_any<FacR2C<StC64>>(p, f, items, st);
+    return launch_any<FacR2C<StC64>>(p, f, items, st, (size_t)2 * N * sizeof(float), ((uintptr_t)in % 16) == 0);
   }
   if (op == QFT_OP_INVERSE || op == QFT_OP_FORWARD_ADJOINT) {
     FacC2R<StC64> f;

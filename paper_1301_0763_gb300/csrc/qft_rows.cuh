@@ -24,6 +24,18 @@ struct FacC2C {
     io.N = N; io.in_op = in_op; io.out_op = out_op; io.scale = scale; io.scaled = scaled != 0;
     return io;
   }
+  // staging of the input row in shared memory by one bulk copy
+  static constexpr bool kCanStage = true;
+  __device__ __forceinline__ int stage_src(int64_t row, const void** src, uint32_t* bytes) const {
+    src[0] = in + row * (int64_t)N;
+    bytes[0] = (uint32_t)(N * sizeof(typename ST::elem));
+    return 1;
+  }
+  __device__ __forceinline__ IoC2C<ST> make_staged(int64_t row, const void* stage) const {
+    IoC2C<ST> io = make(row);
+    io.in = static_cast<const typename ST::elem*>(stage);
+    return io;
+  }
 };
 
 // Ragged C2C: item i is row rows[i] of a packed buffer, at complex offset
@@ -45,6 +57,9 @@ struct FacRaggedC2C {
     io.scaled = args->scaled != 0;
     return io;
   }
+  static constexpr bool kCanStage = false;
+  __device__ int stage_src(int64_t, const void**, uint32_t*) const { return 0; }
+  __device__ IoC2C<ST> make_staged(int64_t item, const void*) const { return make(item); }
 };
 
 template <class ST>
@@ -63,6 +78,20 @@ struct FacR2C {
     io.outa = out + a * H;
     io.outb = b < rows ? out + b * H : nullptr;
     io.N = N; io.wscale = wscale;
+    return io;
+  }
+  static constexpr bool kCanStage = true;
+  __device__ __forceinline__ int stage_src(int64_t item, const void** src, uint32_t* bytes) const {
+    const int64_t a = 2 * item, b = 2 * item + 1;
+    src[0] = in + a * (int64_t)N;
+    bytes[0] = (uint32_t)(N * sizeof(float));
+    if (b < rows) { src[1] = in + b * (int64_t)N; bytes[1] = bytes[0]; return 2; }
+    return 1;
+  }
+  __device__ __forceinline__ IoR2C<ST> make_staged(int64_t item, const void* stage) const {
+    IoR2C<ST> io = make(item);
+    io.ina = static_cast<const float*>(stage);
+    if (io.inb) io.inb = static_cast<const float*>(stage) + N;
     return io;
   }
 };
@@ -85,6 +114,9 @@ struct FacC2R {
     io.N = N; io.wmid = wmid; io.scale = scale;
     return io;
   }
+  static constexpr bool kCanStage = false;
+  __device__ int stage_src(int64_t, const void**, uint32_t*) const { return 0; }
+  __device__ IoC2R<ST> make_staged(int64_t item, const void*) const { return make(item); }
 };
 
 // ------------------------------------------------------------ row kernel
@@ -92,13 +124,48 @@ using qft_lib::off_sec;
 using qft_lib::off_side0;
 using qft_lib::side_bytes;
 
+// ------------------------------------------------------ bulk-copy staging
+// The input of the next row is copied into shared memory by one TMA bulk copy
+// (cp.async.bulk, completion on an mbarrier) while the current row computes;
+// the F1 phase then reads shared memory instead of waiting on HBM.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mb) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mb) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(mb), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: a bulk copy never takes that long
+
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // All phases of a QftRowPlan on the cells behind `e` (shared memory), by the
 // NT threads of one CTA.  `g` offsets every task index by g * count (the node
 // groups of the large-row path); 0 for whole rows.  Plain phases end with a
 // barrier; SLICE phases run in rounds of NT tasks, all reads of a round before
 // any of its writes (the plan guarantees a node's tasks never straddle rounds).
-template <int L1, int NT, class IO>
-__device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e, const IO& io, int g) {
+template <int L1, int NT, class IO, class HOOK = NoHook>
+__device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e, const IO& io, int g,
+                                               const HOOK& after_f1 = HOOK()) {
   const int tid = threadIdx.x;
   for (int p = 0; p < P.nphase; ++p) {
     const int nt = P.phase_ntasks[p];
@@ -124,6 +191,7 @@ __device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e
         run_plain_task<L1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin);
       }
       __syncthreads();
+      if (p == 0) after_f1();
     } else {
       for (int rb = 0; rb < nt; rb += NT) {
         const int tau = rb + tid;
@@ -146,15 +214,35 @@ __device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e
 template <class FAC, int L1, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT)
 k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int sec_stride,
-       int64_t nitems, FAC fac) {
-  extern __shared__ __align__(16) unsigned char smem[];
+       int64_t nitems, FAC fac, int stage_off, int* status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
   QftRowPlan& P = *reinterpret_cast<QftRowPlan*>(smem);
   {
     const int* src = reinterpret_cast<const int*>(gplan);
     int* dst = reinterpret_cast<int*>(smem);
     for (int i = threadIdx.x; i < (int)(sizeof(QftRowPlan) / 4); i += NT) dst[i] = src[i];
   }
+  const bool staged = FAC::kCanStage && stage_off > 0;
+  const uint32_t mb = smem_u32(&mbar);
+  unsigned char* stage = smem + (staged ? stage_off : 0);
+  const uint32_t stage_s = smem_u32(stage);
+  const auto issue = [&](int64_t item) {          // thread 0 only
+    const void* src[2];
+    uint32_t bytes[2];
+    const int np = fac.stage_src(item, src, bytes);
+    uint32_t total = 0;
+    for (int k = 0; k < np; ++k) total += bytes[k];
+    mbar_expect_tx(mb, total);
+    uint32_t off = 0;
+    for (int k = 0; k < np; ++k) { bulk_g2s(stage_s + off, src[k], bytes[k], mb); off += bytes[k]; }
+  };
+  if (staged && threadIdx.x == 0) {
+    mbar_init(mb, 1);
+    fence_mbar_init();
+  }
   __syncthreads();
+  if (staged && threadIdx.x == 0 && (int64_t)blockIdx.x < nitems) issue(blockIdx.x);
   const int r = P.r;
   const int N = 1 << r;
   float* sec = reinterpret_cast<float*>(smem + off_sec());
@@ -166,9 +254,33 @@ k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int
   e.side0 = side0; e.side1 = side1; e.sec = sec; e.r = r; e.N = N;
   e.tabC = reinterpret_cast<qc*>(smem + qft_lib::off_tab(N));
   e.tabS = e.tabC + (N >> P.LF) / 2 + 1;
+  uint32_t parity = 0;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const auto io = fac.make(item);
-    run_row_phases<L1, NT>(P, e, io, 0);
+    if (staged) {
+      // every thread waits for the bulk copy of this item (bounded)
+      const uint64_t t0 = global_ns();
+      bool ok = true;
+      while (!mbar_try_wait(mb, parity)) {
+        if (global_ns() - t0 > kWaitLimitNs) { ok = false; break; }
+      }
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicExch(status, QFT_ERR_TIMEOUT);
+        return;
+      }
+      parity ^= 1;
+      const auto io = fac.make_staged(item, stage);
+      const int64_t next = item + gridDim.x;
+      run_row_phases<L1, NT>(P, e, io, 0, [&]() {
+        // F1 has read the staged row: the buffer may take the next one
+        if (threadIdx.x == 0 && next < nitems) {
+          fence_proxy_async_smem();
+          issue(next);
+        }
+      });
+    } else {
+      const auto io = fac.make(item);
+      run_row_phases<L1, NT>(P, e, io, 0);
+    }
   }
 }
 
@@ -203,17 +315,29 @@ static int occupancy_grid(qft_plan p, K kernel, int nt, int64_t items) {
 
 // ------------------------------------------------------------ launchers
 template <class FAC, int L1, int NT>
-static inline int launch_rows_nt(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
+static inline int launch_rows_nt(qft_plan p, FAC fac, int64_t items, size_t stage_bytes, bool stage_ok,
+                                 cudaStream_t st) {
   auto kern = k_rows<FAC, L1, NT>;
+  // stage the input rows in shared memory when the staging buffer keeps two CTAs per SM
+  int stage_off = 0;
+  size_t smem = p->smem;
+  if (FAC::kCanStage && stage_ok && stage_bytes > 0) {
+    const size_t off = (p->smem + 127) & ~(size_t)127;
+    if (NT == 256 && off + stage_bytes <= (size_t)(227 * 1024) / 2) { stage_off = (int)off; smem = off + stage_bytes; }
+  }
+  const size_t keep = p->smem;
+  p->smem = smem;
   int rc = occupancy_grid(p, kern, NT, items);
+  p->smem = keep;
   if (rc != QFT_OK) return rc;
-  kern<<<p->grid, NT, p->smem, st>>>(p->d_plan, p->d_sec, 1, items, fac);
+  kern<<<p->grid, NT, smem, st>>>(p->d_plan, p->d_sec, 1, items, fac, stage_off, p->d_status);
   return qft_set_cuda(p, cudaGetLastError());
 }
 
 template <class FAC>
-static inline int launch_rows(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
-  if (p->threads == 512) return launch_rows_nt<FAC, qft_lib::kL1, 512>(p, fac, items, st);
-  return launch_rows_nt<FAC, qft_lib::kL1, 256>(p, fac, items, st);
+static inline int launch_rows(qft_plan p, FAC fac, int64_t items, cudaStream_t st, size_t stage_bytes = 0,
+                              bool stage_ok = false) {
+  if (p->threads == 512) return launch_rows_nt<FAC, qft_lib::kL1, 512>(p, fac, items, 0, false, st);
+  return launch_rows_nt<FAC, qft_lib::kL1, 256>(p, fac, items, stage_bytes, stage_ok, st);
 }
 

@@ -62,6 +62,9 @@ def load_library(path: str | None = None):
         lib.qft_plan_sync_status.argtypes = [vp]
         lib.qft_plan_last_cuda_error.argtypes = [vp]
         lib.qft_plan_info.argtypes = [vp] + [ctypes.POINTER(ci)] * 4
+        lib.qft_filter_create.argtypes = [ctypes.POINTER(vp), i64, i64, i64, ctypes.c_uint]
+        lib.qft_filter_forward.argtypes = [vp, vp, vp, vp, vp]
+        lib.qft_filter_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.qft_status_string.argtypes = [ci]
         lib.qft_status_string.restype = ctypes.c_char_p
         _lib = lib
@@ -145,6 +148,78 @@ class RaggedPlan(Plan):
                 ctypes.byref(self.handle), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                 lg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.count, KIND_C2C, DTYPE_F32, 0),
                 "qft_plan_create_ragged")
+
+
+class FilterPlan(Plan):
+    """Plan of the spectral-filter layer y = irfft(W (.) rfft(x)) for x [B, C, N]."""
+
+    def __init__(self, n: int, batch: int, channels: int, device=None):
+        self.lib = load_library()
+        self.n, self.batch, self.channels = int(n), int(batch), int(channels)
+        self.kind, self.dtype = -1, DTYPE_F32
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.qft_filter_create(ctypes.byref(self.handle), self.n, self.batch, self.channels, 0),
+                   "qft_filter_create")
+
+    def forward(self, x: torch.Tensor, W: torch.Tensor, y: torch.Tensor, stream=None):
+        with torch.cuda.device(self.device):
+            _check(self.lib.qft_filter_forward(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(W.data_ptr()),
+                                               ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(_stream_handle(stream))),
+                   "qft_filter_forward")
+        return y
+
+    def backward(self, x, W, gy, gx, gW, stream=None):
+        with torch.cuda.device(self.device):
+            _check(self.lib.qft_filter_backward(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(W.data_ptr()),
+                                                ctypes.c_void_p(gy.data_ptr()), ctypes.c_void_p(gx.data_ptr()),
+                                                ctypes.c_void_p(gW.data_ptr()), ctypes.c_void_p(_stream_handle(stream))),
+                   "qft_filter_backward")
+
+
+_filter_plans: dict = {}
+
+
+def _filter_plan(x: torch.Tensor) -> FilterPlan:
+    B, C, N = x.shape
+    key = (N, B, C, x.device.index)
+    p = _filter_plans.get(key)
+    if p is None:
+        p = FilterPlan(N, B, C, x.device)
+        _filter_plans[key] = p
+    return p
+
+
+class _SpectralFilter(torch.autograd.Function):
+    """y = irfft(W (.) rfft(x)); backward recomputes rfft(x) (nothing saved but x, W)."""
+
+    @staticmethod
+    def forward(ctx, x, W):
+        _need_cuda(x)
+        x = x.contiguous()
+        W = W.contiguous()
+        assert x.dtype == torch.float32 and W.dtype == torch.complex64 and x.dim() == 3
+        assert W.shape == (x.shape[1], x.shape[2] // 2 + 1)
+        y = torch.empty_like(x)
+        _filter_plan(x).forward(x, W, y)
+        ctx.save_for_backward(x, W)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, W = ctx.saved_tensors
+        gy = gy.contiguous()
+        gx = torch.empty_like(x)
+        gW = torch.empty_like(W)
+        _filter_plan(x).backward(x, W, gy, gx, gW)
+        return gx, gW
+
+
+def spectral_filter(x: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
+    """Spectral-filter layer y = irfft(W (.) rfft(x)) over the last dim of x [B, C, N]."""
+    return _SpectralFilter.apply(x, W)
 
 
 _plans: dict = {}

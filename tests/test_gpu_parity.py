@@ -313,3 +313,76 @@ def test_ragged_full_workload_sampled(q):
                     | {0, 4095})
     _ragged_check(q, log2n, seed=2, sample=sample)
     torch.cuda.empty_cache()
+
+
+def test_unstaged_fallback_and_status_word(q):
+    """An input that is 8- but not 16-byte aligned cannot be bulk-copied into
+    shared memory; the kernel then reads it directly -- same bits.  The device
+    status word stays clear."""
+    N, rows = 4096, 9
+    z = inputs.normal_complex(rows, N, seed=41)
+    buf = torch.zeros(rows * N + 1, dtype=torch.complex64, device="cuda")
+    buf[1:] = gpu(z).reshape(-1)
+    xin = buf[1:].view(rows, N)
+    assert xin.data_ptr() % 16 == 8
+    out = torch.empty(rows, N, dtype=torch.complex64, device="cuda")
+    p = q.Plan(N, rows)
+    p.execute(q.OP_FORWARD, xin, out)
+    assert p.sync_status() == 0
+    assert bits_equal(out.cpu().numpy(), orc.cdft(z, fp32=True).astype(np.complex64))
+    p.destroy()
+
+
+# ------------------------------------------------------------ spectral filter
+def test_spectral_filter_forward_backward(q):
+    """y = irfft(W (.) rfft(x)), x [64, 64, 4096] real, W [64, 2049] complex
+    (std 0.02), loss = sum(y^2): forward bit-exact against the FP32 oracle
+    composition, gradients within FP32 error of the FP64 oracle gradient (whose
+    own correctness is pinned by central finite differences in the CPU suite),
+    weight gradient deterministic."""
+    B, C, N = 64, 64, 4096
+    x = inputs.normal_real(B * C, N, seed=5).reshape(B, C, N)
+    W = inputs.filter_weights(C, N, seed=4)
+    xt = gpu(x).requires_grad_(True)
+    Wt = gpu(W).requires_grad_(True)
+    y = q.spectral_filter(xt, Wt)
+    loss = (y ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    yh = y.detach().cpu().numpy()
+    sub = slice(0, 4)   # oracle on a few batch rows (all channels)
+    ref32 = orc.filter_forward(x[sub], W, fp32=True).astype(np.float32)
+    assert bits_equal(yh[sub], ref32)
+    ref64 = orc.filter_forward(x[sub], W)
+    assert np.abs(yh[sub] - ref64).max() / np.abs(ref64).max() < 1e-5
+    gx_ref, _ = orc.filter_backward(x[sub], W, 2 * ref64)
+    gx = xt.grad.cpu().numpy()[sub]
+    assert np.linalg.norm(gx - gx_ref) / np.linalg.norm(gx_ref) < 2e-5
+    # gW over the whole batch against the FP64 oracle (all rows)
+    y64 = orc.filter_forward(x, W)
+    _, gW_ref = orc.filter_backward(x, W, 2 * y64)
+    gW = Wt.grad.cpu().numpy()
+    assert np.linalg.norm(gW - gW_ref) / np.linalg.norm(gW_ref) < 2e-5
+    # determinism of the batch reduction
+    gx2 = torch.empty_like(xt)
+    gW2 = torch.empty_like(Wt)
+    p = q._filter_plan(xt.detach())
+    p.backward(xt.detach(), Wt.detach(), (2 * y).detach().contiguous(), gx2, gW2)
+    torch.cuda.synchronize()
+    assert np.array_equal(gW2.cpu().numpy().view(np.uint32), Wt.grad.cpu().numpy().view(np.uint32))
+
+
+def test_spectral_filter_small_exhaustive(q):
+    """B = C = 2, N = 64: gradients against the FP64 oracle gradient."""
+    B, C, N = 3, 2, 64
+    x = inputs.normal_real(B * C, N, seed=6).reshape(B, C, N)
+    W = inputs.filter_weights(C, N, seed=7)
+    xt = gpu(x).requires_grad_(True)
+    Wt = gpu(W).requires_grad_(True)
+    y = q.spectral_filter(xt, Wt)
+    (y ** 2).sum().backward()
+    y64 = orc.filter_forward(x, W)
+    gx_ref, gW_ref = orc.filter_backward(x, W, 2 * y64)
+    assert np.abs(y.detach().cpu().numpy() - y64).max() < 1e-5 * np.abs(y64).max()
+    assert np.linalg.norm(xt.grad.cpu().numpy() - gx_ref) / np.linalg.norm(gx_ref) < 1e-5
+    assert np.linalg.norm(Wt.grad.cpu().numpy() - gW_ref) / np.linalg.norm(gW_ref) < 1e-5

@@ -290,3 +290,68 @@ def test_accuracy_metric_eq44_fp64_level():
     z = inputs.uniform_complex(8, N, seed=44, lo=-0.5, hi=0.5).astype(np.complex128)
     errs = [rel_l2(orc.cdft(r), orc.brute_dft(r)) for r in z]
     assert 1e-17 < np.mean(errs) < 3e-15
+
+
+# -------------------------------------------------- spectral-filter gradients
+def _filter_loss(x, W):
+    return float(np.sum(orc.filter_forward(x, W) ** 2))
+
+
+def test_filter_forward_matches_dense_definition():
+    B, C, N = 2, 3, 32
+    g = inputs.rng(50)
+    x = g.standard_normal((B, C, N))
+    W = 0.02 * (g.standard_normal((C, N // 2 + 1)) + 1j * g.standard_normal((C, N // 2 + 1)))
+    y = orc.filter_forward(x, W)
+    ref = np.fft.irfft(W[None] * np.fft.rfft(x, axis=-1), n=N, axis=-1)
+    assert np.abs(y - ref).max() < 1e-13
+
+
+def test_filter_gradients_by_central_differences_exhaustive_small():
+    """loss = sum(y^2) is quadratic, so central differences (eps = 1e-3, FP64)
+    are exact up to rounding: every coordinate of W (re and im) and of x."""
+    B, C, N = 2, 2, 64
+    g = inputs.rng(51)
+    x = g.standard_normal((B, C, N))
+    W = 0.02 * (g.standard_normal((C, N // 2 + 1)) + 1j * g.standard_normal((C, N // 2 + 1)))
+    y = orc.filter_forward(x, W)
+    gx, gW = orc.filter_backward(x, W, 2 * y)
+    eps = 1e-3
+    for c in range(C):
+        for k in range(N // 2 + 1):
+            for unit in (1.0, 1j):
+                Wp = W.copy(); Wp[c, k] += eps * unit
+                Wm = W.copy(); Wm[c, k] -= eps * unit
+                fd = (_filter_loss(x, Wp) - _filter_loss(x, Wm)) / (2 * eps)
+                an = gW[c, k].real if unit == 1.0 else gW[c, k].imag
+                assert abs(fd - an) < 1e-7 * max(1.0, abs(an)), (c, k, unit)
+    for idx in np.ndindex(B, C, N):
+        xp = x.copy(); xp[idx] += eps
+        xm = x.copy(); xm[idx] -= eps
+        fd = (_filter_loss(xp, W) - _filter_loss(xm, W)) / (2 * eps)
+        assert abs(fd - gx[idx]) < 1e-7 * max(1.0, abs(gx[idx]))
+
+
+def test_filter_gradients_by_central_differences_sampled():
+    """64 seeded coordinates of W and of x at channels=3, N=4096 (B=2)."""
+    B, C, N = 2, 3, 4096
+    g = inputs.rng(52)
+    x = g.standard_normal((B, C, N))
+    W = 0.02 * (g.standard_normal((C, N // 2 + 1)) + 1j * g.standard_normal((C, N // 2 + 1)))
+    y = orc.filter_forward(x, W)
+    gx, gW = orc.filter_backward(x, W, 2 * y)
+    eps = 1e-3
+    for _ in range(32):
+        c, k = int(g.integers(C)), int(g.integers(N // 2 + 1))
+        unit = 1.0 if g.integers(2) == 0 else 1j
+        Wp = W.copy(); Wp[c, k] += eps * unit
+        Wm = W.copy(); Wm[c, k] -= eps * unit
+        fd = (_filter_loss(x, Wp) - _filter_loss(x, Wm)) / (2 * eps)
+        an = gW[c, k].real if unit == 1.0 else gW[c, k].imag
+        assert abs(fd - an) < 1e-6 * max(1.0, abs(an))
+    for _ in range(32):
+        idx = (int(g.integers(B)), int(g.integers(C)), int(g.integers(N)))
+        xp = x.copy(); xp[idx] += eps
+        xm = x.copy(); xm[idx] -= eps
+        fd = (_filter_loss(xp, W) - _filter_loss(xm, W)) / (2 * eps)
+        assert abs(fd - gx[idx]) < 1e-6 * max(1.0, abs(gx[idx]))
