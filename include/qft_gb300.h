@@ -148,6 +148,33 @@ int qft_filter_forward(qft_plan plan, const float* x, const void* W, float* y, v
 int qft_filter_backward(qft_plan plan, const float* x, const void* W, const float* gy, float* gx, void* gW,
                         void* stream);
 
+/*
+ * qft_execute_static_scratch -- run op (QFT_OP_*) on `batch` C2C FP32 rows of
+ * length n, 2^15 <= n <= 2^20, like qft_execute on a QFT_KIND_C2C /
+ * QFT_DTYPE_F32 plan, but without a plan and without allocating.  The paper
+ * has no counterpart: this is a service entry point for callers that cannot
+ * allocate device memory at the point of use (all free memory held by another
+ * allocator, or a latency-bound loop where cudaMalloc / cudaFree would
+ * synchronise the device).  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   in, out  device pointers, [batch][n] complex64, 8-byte aligned; in == out
+ *            is allowed.  stream as in qft_execute.
+ * Storage: a 64 MiB scratch array, the secant table and the schedules are
+ * file-scope device arrays of the library, reserved when its module loads and
+ * shared by every call.  Nothing in them has to start at zero (each call writes
+ * every scratch cell before reading it).  Calls whose executions overlap (two
+ * streams, or host threads without ordering) race on the scratch: serialise
+ * them.  Batches larger than the rows the scratch holds (3 rows at n = 2^20,
+ * 120 at 2^15) run in successive chunks.
+ * Set-up: the first call on each device (with that device current) looks up the
+ * arrays with cudaGetSymbolAddress and fills the tables with blocking copies;
+ * make that first call before any stream capture begins.
+ * Errors: QFT_ERR_INVALID_N for n not a power of two or outside [2^15, 2^20]
+ * (the limit the static scratch sets); QFT_ERR_INVALID_BATCH, _INVALID_ARG (op,
+ * device ordinal >= 64), _NULLPTR, _ALIGN, _CUDA as for qft_execute.
+ */
+int qft_execute_static_scratch(int64_t n, int64_t batch, int op, const void* in, void* out, void* stream);
+
 /* Releases every resource of the plan.  Safe on NULL.  A destroyed plan must
  * not be used again; the library detects most such uses (QFT_ERR_DESTROYED). */
 int qft_plan_destroy(qft_plan plan);

@@ -65,6 +65,7 @@ def load_library(path: str | None = None):
         lib.qft_filter_create.argtypes = [ctypes.POINTER(vp), i64, i64, i64, ctypes.c_uint]
         lib.qft_filter_forward.argtypes = [vp, vp, vp, vp, vp]
         lib.qft_filter_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.qft_execute_static_scratch.argtypes = [i64, i64, ci, vp, vp, vp]
         lib.qft_status_string.argtypes = [ci]
         lib.qft_status_string.restype = ctypes.c_char_p
         _lib = lib
