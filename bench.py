@@ -185,13 +185,16 @@ def run_gpu(args):
     qft.load_library()
     logs = supported_logs()
     stream = torch.cuda.current_stream()
+    tune = not args.no_autotune
 
     # ------------------------------------------------------------ buffers
     gen = torch.Generator(device=dev).manual_seed(13010763 + rank)
     # re and im i.i.d. N(0, 1)
     zin = torch.randn(ELEMS, 2, dtype=torch.float32, device=dev, generator=gen).view(torch.complex64).view(ELEMS)
     zout = torch.empty_like(zin)
-    plans = {lg: qft.Plan(1 << lg, ELEMS >> lg) for lg in logs}
+    t_tune = time.perf_counter()
+    plans = {lg: qft.Plan(1 << lg, ELEMS >> lg, autotune=tune) for lg in logs}
+    tune_s = time.perf_counter() - t_tune
 
     def step(evs=None):
         for lg in logs:
@@ -212,6 +215,8 @@ def run_gpu(args):
 
     evs = {lg: [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
                 for _ in range(args.steps)] for lg in logs}
+    for lg in logs:
+        plans[lg].time_launches(True)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -233,6 +238,10 @@ def run_gpu(args):
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
+    kt = {}
+    for lg in logs:
+        kt[lg] = plans[lg].launch_times()
+        plans[lg].time_launches(False)
     bytes_per_step = 16 * ELEMS * len(logs)
     flops_per_step = sum(5 * ELEMS * lg for lg in logs)
     value = ws * bytes_per_step * args.steps / (ms * 1e-3) / 1e9
@@ -241,9 +250,9 @@ def run_gpu(args):
     for lg in logs:
         times = [e[0].elapsed_time(e[1]) for e in evs[lg]]
         per_size[lg] = sum(times) / len(times)
-    dom = max(per_size, key=per_size.get)
     peak, peak_src = measured_peaks()
-    achieved = 16 * ELEMS / (per_size[dom] * 1e-3) / 1e9
+    roof, kernel_share = roofline(kt, peak, peak_src)
+    launches = sum(n for lg in logs for (_, n) in kt[lg].values())
 
     # ------------------------------------------------------- accuracy sample
     err_max, err_mean = 0.0, [float("nan")]
@@ -260,9 +269,21 @@ def run_gpu(args):
         e = np.linalg.norm(Xs - ref, axis=1) / np.linalg.norm(ref, axis=1)
         err_max = max(err_max, float(e.max()))
         err_mean += e.tolist()
+    schedules = {f"2^{lg}": plans[lg].schedule() for lg in logs}
 
     # ------------------------------------------------------------- e2e
-    e2e = None if args.no_e2e else run_e2e(args, logs, dev, stream, torch, qft)
+    e2e = None
+    if not args.no_e2e:
+        del zout
+        e2e = run_e2e(args, logs, dev, stream, torch, qft, tune)
+    zin = zout = None
+    plans = None
+    torch.cuda.empty_cache()
+
+    extras = None
+    if not args.no_extras and rank == 0:
+        extras = run_extras(args, dev, stream, torch, qft, orc, tune, peak)
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -272,7 +293,6 @@ def run_gpu(args):
                "sample": "FP64 oracle, one pass over rows per size " +
                          ", ".join(f"2^{lg}:{rows[lg]}" for lg in logs)}
 
-    info = plans[dom].info()
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
@@ -282,35 +302,73 @@ def run_gpu(args):
                            ",".join(f"2^{l}" for l in logs), "elements_per_size": ELEMS,
                            "sizes_not_yet_supported": [f"2^{l}" for l in CONFIG_LOGS if l not in logs],
                            "l2": "inputs (2 GiB) larger than L2, no flush",
-                           "threads_per_cta": info["threads"], "ctas": info["ctas"]},
+                           "schedules": schedules, "autotune": tune, "autotune_s": round(tune_s, 2)},
                 "gflops_5nlog2n": round(gflops, 1),
                 "frac_of_hbm": round(value / peak, 4),
                 "rel_err_vs_fp64": {"max": err_max, "mean": float(np.nanmean(err_mean)) if len(err_mean) > 1 else None, "rows": len(err_mean) - 1},
                 "per_size_ms": {f"2^{lg}": round(per_size[lg], 4) for lg in logs},
                 "per_size_gbs": {f"2^{lg}": round(16 * ELEMS / (per_size[lg] * 1e-3) / 1e9, 1) for lg in logs},
-                "roofline": {"bound": "hbm", "kernel": f"k_rows C2C f32 (N=2^{dom})",
-                             "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src,
-                             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None},
+                "kernel_ms_per_step": kernel_share(args.steps),
+                "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": args.steps * len(logs)}
+                "gpu_launches": launches, "extras": extras}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
 
 
-def run_e2e(args, logs, dev, stream, torch, qft):
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel, from one
+# ncu capture of the named kernel at the stated size (scaled to a launch over
+# 2^28 elements); None once the kernel has changed since the capture.
+NCU_TRAFFIC = {}
+
+
+def roofline(kt, peak, peak_src):
+    """Roofline of the kernel with the largest summed time over the timed
+    region.  Every launch of every kernel of the path reads and writes each of
+    the 2^28 elements' 8-byte cells once (row kernel: the transform's 8N in +
+    8N out; large-row kernels: 8N of class data in and 8N out per pass), so its
+    algorithmic bytes per launch are 16 * 2^28 (one scratch chunk per size at
+    this workload)."""
+    tot = {}
+    per = {}
+    for lg, d in kt.items():
+        for k, (ms, n) in d.items():
+            tot[k] = tot.get(k, 0.0) + ms
+            a = per.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += n
+    dom = max(tot, key=tot.get)
+    ms, n = per[dom]
+    avg = ms / n
+    achieved = 16 * ELEMS / (avg * 1e-3) / 1e9
+    sizes = sorted(lg for lg in kt if dom in kt[lg])
+    roof = {"bound": "hbm", "kernel": dom, "sizes": [f"2^{lg}" for lg in sizes],
+            "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(dom),
+            "bytes_per_launch": 16 * ELEMS, "launches": n, "avg_launch_ms": round(avg, 4)}
+
+    def share(steps):
+        return {k: round(v / steps, 3) for k, v in sorted(tot.items(), key=lambda x: -x[1])}
+    return roof, share
+
+
+def run_e2e(args, logs, dev, stream, torch, qft, tune):
     """Same metric through the public API with host buffers: every step copies
-    its input from pinned host memory, transforms, and copies the spectrum back."""
-    lg = logs[0]
-    N = 1 << lg
-    rows = ELEMS // N
-    host_in = torch.randn(rows, N, dtype=torch.complex64).pin_memory()
+    each size's input (2 GiB) from pinned host memory, transforms it with
+    qft.fft, and copies the spectrum back."""
+    qft.set_autotune(tune)
+    host_in = torch.randn(ELEMS, dtype=torch.complex64).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     steps = max(1, min(args.steps, 3))
+
     def one():
-        d = host_in.to(dev, non_blocking=True)
-        X = qft.fft(d)
-        host_out.copy_(X, non_blocking=True)
+        for lg in logs:
+            N = 1 << lg
+            d = host_in.view(ELEMS // N, N).to(dev, non_blocking=True)
+            X = qft.fft(d)
+            host_out.view(ELEMS // N, N).copy_(X, non_blocking=True)
+            del d, X
     one()
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -321,10 +379,209 @@ def run_e2e(args, logs, dev, stream, torch, qft):
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
-    nbytes = 16 * ELEMS
+    nbytes = 16 * ELEMS * len(logs)
+    qft.set_autotune(False)
     return {"value": round(nbytes / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
-            "h2d_bytes_per_step": 8 * ELEMS, "d2h_bytes_per_step": 8 * ELEMS,
-            "workload": f"N=2^{lg}, batch {rows}, fft() on pinned host data"}
+            "h2d_bytes_per_step": 8 * ELEMS * len(logs), "d2h_bytes_per_step": 8 * ELEMS * len(logs),
+            "ms_per_step": round(ms, 3),
+            "workload": "the same sizes and batches, qft.fft() on pinned host data, copies included"}
+
+
+def _time(fn, torch, stream, reps=3, warm=2):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _rel_errs(Y, ref):
+    e = np.linalg.norm(Y - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    return {"max": float(e.max()), "mean": float(e.mean()), "rms": float(np.sqrt(np.mean(e * e)))}
+
+
+def run_extras(args, dev, stream, torch, qft, orc, tune, peak):
+    """The other measured forms of the path: single small transform, inverse,
+    real input, uneven batch, FP16/BF16 storage, spectral filter, 2^24."""
+    from paper_1301_0763_gb300 import inputs
+    ex = {}
+    gen = torch.Generator(device=dev).manual_seed(13010763 + 7)
+
+    # ---- N = 1024, batch 64 (latency) and N = 2^10 x 2^18 (bandwidth)
+    x = torch.from_numpy(inputs.uniform_complex(64, 1024, seed=1)).to(dev)
+    y = torch.empty_like(x)
+    p = qft.Plan(1024, 64, autotune=tune)
+    us_plain = 1e3 * _time(lambda: p.execute(qft.OP_FORWARD, x, y), torch, stream, reps=200, warm=10)
+    c1 = {"us_per_execute": round(us_plain, 2)}
+    try:
+        gs = torch.cuda.Stream()
+        gs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(gs):
+            p.execute(qft.OP_FORWARD, x, y)
+        torch.cuda.current_stream().wait_stream(gs)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            p.execute(qft.OP_FORWARD, x, y)
+        c1["us_graph_replay"] = round(1e3 * _time(graph.replay, torch, stream, reps=200, warm=10), 2)
+    except Exception as exc:  # noqa: BLE001  (report, do not fail the bench)
+        c1["graph_error"] = str(exc)[:200]
+    torch.cuda.synchronize()
+    ref = orc.cdft(x.cpu().numpy())
+    c1["rel_err_vs_fp64"] = _rel_errs(y.cpu().numpy().astype(np.complex128), ref)
+    z = torch.randn(1 << 28, 2, device=dev, generator=gen).view(torch.complex64).view(1 << 18, 1 << 10)
+    zo = torch.empty_like(z)
+    pb = qft.Plan(1 << 10, 1 << 18, autotune=tune)
+    ms = _time(lambda: pb.execute(qft.OP_FORWARD, z, zo), torch, stream)
+    c1["n1024_batch2^18_gbs"] = round(16 * (1 << 28) / (ms * 1e-3) / 1e9, 1)
+    ex["n1024"] = c1
+
+    # ---- inverse and real input at the batched sizes
+    inv, real = {}, {}
+    zv = z.view(-1)
+    for lg in CONFIG_LOGS:
+        N = 1 << lg
+        a, b = zv.view(-1, N), zo.view(-1, N)
+        pl = qft.Plan(N, a.shape[0], autotune=tune)
+        ms = _time(lambda: pl.execute(qft.OP_INVERSE, a, b), torch, stream)
+        inv[f"2^{lg}"] = round(16 * (1 << 28) / (ms * 1e-3) / 1e9, 1)
+        pl.destroy()
+        xr = zv.view(torch.float32)[: 1 << 28].view(-1, N)
+        yr = zo.view(-1)[: (xr.shape[0] * (N // 2 + 1))].view(xr.shape[0], N // 2 + 1)
+        pr = qft.Plan(N, xr.shape[0], kind=qft.KIND_R2C, autotune=tune)
+        ms = _time(lambda: pr.execute(qft.OP_FORWARD, xr, yr), torch, stream)
+        real[f"2^{lg}"] = round(xr.shape[0] * (4 * N + 8 * (N // 2 + 1)) / (ms * 1e-3) / 1e9, 1)
+        pr.destroy()
+    ex["inverse_gbs"] = inv
+    ex["real_forward_gbs"] = real
+    del z, zo, zv
+    torch.cuda.empty_cache()
+
+    # ---- uneven batch: one graph launch against a per-length loop
+    log2n = inputs.ragged_log2n(4096, seed=2)
+    off = inputs.ragged_offsets(log2n)
+    total = int(off[-1])
+    zr = torch.randn(total, 2, device=dev, generator=gen).view(torch.complex64).view(total)
+    yr = torch.empty_like(zr)
+    t_plan = time.perf_counter()
+    rp = qft.RaggedPlan(off, log2n, autotune=tune)
+    t_plan = time.perf_counter() - t_plan
+    ms_graph = _time(lambda: rp.execute(qft.OP_FORWARD, zr, yr), torch, stream)
+    # the same rows sorted by length into contiguous per-length buffers
+    order = np.argsort(log2n, kind="stable")
+    lens = np.left_shift(1, log2n[order].astype(np.int64))
+    classes = sorted(set(log2n.tolist()))
+    bufs, loop_plans, pos = [], [], 0
+    for r in classes:
+        cnt = int((log2n == r).sum())
+        n = cnt << r
+        bufs.append((zr[pos:pos + n].view(cnt, 1 << r), yr[pos:pos + n].view(cnt, 1 << r)))
+        loop_plans.append(qft.Plan(1 << r, cnt, autotune=tune))
+        pos += n
+    assert pos == total and int(lens.sum()) == total
+
+    def loop():
+        for pl, (a, b) in zip(loop_plans, bufs):
+            pl.execute(qft.OP_FORWARD, a, b)
+    ms_loop = _time(loop, torch, stream)
+    nbytes = 16 * total
+    ex["ragged_4096"] = {"total_complex": total, "classes": len(classes), "graph_ms": round(ms_graph, 3),
+                         "loop_ms": round(ms_loop, 3), "graph_gbs": round(nbytes / (ms_graph * 1e-3) / 1e9, 1),
+                         "loop_gbs": round(nbytes / (ms_loop * 1e-3) / 1e9, 1),
+                         "graph_speedup": round(ms_loop / ms_graph, 3), "plan_s": round(t_plan, 2),
+                         "loop": "one plain plan per length over the rows sorted by length"}
+    rp.destroy()
+    for pl in loop_plans:
+        pl.destroy()
+    del zr, yr, bufs
+    torch.cuda.empty_cache()
+
+    # ---- FP16 / BF16 storage
+    half = {}
+    for name, dt, code in (("fp16", torch.float16, qft.DTYPE_F16), ("bf16", torch.bfloat16, qft.DTYPE_BF16)):
+        for lg in (10, 13, 16):
+            N, B = 1 << lg, 1 << 14
+            xh = (torch.rand(B, N, 2, device=dev, generator=gen) * 2 - 1).to(dt)
+            yh = torch.empty_like(xh)
+            ph = qft.Plan(N, B, dtype=code, autotune=tune)
+            ms = _time(lambda: ph.execute(qft.OP_FORWARD, xh, yh), torch, stream)
+            ent = {"gbs": round(8 * N * B / (ms * 1e-3) / 1e9, 1)}
+            ph.destroy()
+            del xh, yh
+            rows = 32
+            ps = qft.Plan(N, rows, dtype=code)
+            pf = qft.Plan(N, rows)
+            for setname, z64 in (("uniform", inputs.uniform_complex(rows, N, seed=4, dtype=np.complex128)),
+                                 ("student_t3", inputs.student_t_complex(rows, N, seed=4))):
+                pair = torch.from_numpy(np.stack([z64.real, z64.imag], -1))
+                xs = pair.to(dt).to(dev)
+                ys = torch.empty_like(xs)
+                ps.execute(qft.OP_FORWARD, xs, ys)
+                torch.cuda.synchronize()
+                xr64 = xs.float().cpu().numpy().astype(np.float64)
+                xr64 = xr64[..., 0] + 1j * xr64[..., 1]
+                Y = ys.float().cpu().numpy().astype(np.float64)
+                Y = Y[..., 0] + 1j * Y[..., 1]
+                ref_a = orc.cdft(xr64)
+                ref_b = orc.cdft(z64)
+                x32 = torch.from_numpy(z64.astype(np.complex64)).to(dev)
+                y32 = torch.empty_like(x32)
+                pf.execute(qft.OP_FORWARD, x32, y32)
+                torch.cuda.synchronize()
+                ref_32 = orc.cdft(x32.cpu().numpy())
+                ent[setname] = {"vs_oracle_of_rounded_input": _rel_errs(Y, ref_a),
+                                "vs_oracle_of_fp64_input": _rel_errs(Y, ref_b),
+                                "fp32_path_vs_oracle": _rel_errs(y32.cpu().numpy().astype(np.complex128), ref_32),
+                                "rows": rows}
+            ps.destroy()
+            pf.destroy()
+            half[f"{name}_2^{lg}"] = ent
+    ex["half_storage"] = half
+    torch.cuda.empty_cache()
+
+    # ---- spectral filter y = irfft(W * rfft(x)), x [64, 64, 4096]
+    B, C, N = 64, 64, 4096
+    xf = torch.randn(B, C, N, device=dev, generator=gen)
+    W = (0.02 * torch.randn(C, N // 2 + 1, 2, device=dev, generator=gen)).view(torch.complex64).view(C, N // 2 + 1)
+    yf = torch.empty_like(xf)
+    gx = torch.empty_like(xf)
+    gW = torch.empty_like(W)
+    fp = qft.FilterPlan(N, B, C)
+    ms_f = _time(lambda: fp.forward(xf, W, yf), torch, stream, reps=10)
+    ms_b = _time(lambda: fp.backward(xf, W, yf, gx, gW), torch, stream, reps=10)
+    rowb = B * C * N * 4
+    ex["spectral_filter"] = {"forward_ms": round(ms_f, 4), "backward_ms": round(ms_b, 4),
+                             "forward_gbs": round((2 * rowb + W.numel() * 8) / (ms_f * 1e-3) / 1e9, 1),
+                             "backward_gbs": round((3 * rowb + 2 * W.numel() * 8) / (ms_b * 1e-3) / 1e9, 1),
+                             "bytes": "forward x + y + W; backward x + gy + gx + W + gW"}
+    fp.destroy()
+    del xf, yf, gx, gW, W
+    torch.cuda.empty_cache()
+
+    # ---- one N = 2^24 transform, forward and backward
+    N = 1 << 24
+    x = torch.randn(N, 2, device=dev, generator=gen).view(torch.complex64).view(1, N)
+    y = torch.empty_like(x)
+    g2 = torch.empty_like(x)
+    pl = qft.Plan(N, 1, autotune=tune)
+    pl.time_launches(True)
+    ms_f = _time(lambda: pl.execute(qft.OP_FORWARD, x, y), torch, stream, reps=3, warm=0)
+    kt = pl.launch_times()
+    ms_b = _time(lambda: pl.execute(qft.OP_FORWARD_ADJOINT, y, g2), torch, stream, reps=3, warm=0)
+    pl.time_launches(False)
+    launches = sum(n for (_, n) in kt.values()) // 3
+    ex["n2^24"] = {"forward_ms": round(ms_f, 3), "backward_ms": round(ms_b, 3),
+                   "forward_gbs": round(16 * N / (ms_f * 1e-3) / 1e9, 1),
+                   "launches_per_execute": launches,
+                   "bytes_moved_per_execute_est": 16 * N * launches,
+                   "schedule": pl.schedule()}
+    pl.destroy()
+    return ex
 
 
 def main():
@@ -337,6 +594,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true", help="default schedules instead of autotuned ones")
     ap.add_argument("--sizes", default="", help="comma-separated log2 N subset (profiling runs)")
     ap.add_argument("--elems-log2", type=int, default=28,
                     help="complex elements per size (28 = the benchmark; smaller for profiler captures)")

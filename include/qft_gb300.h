@@ -59,6 +59,9 @@ typedef struct qft_plan_s* qft_plan;
 #define QFT_OP_FORWARD_ADJOINT 2 /* = backward of the forward transform */
 #define QFT_OP_INVERSE_ADJOINT 3 /* = backward of the inverse transform */
 
+/* plan creation flags */
+#define QFT_PLAN_AUTOTUNE 1u /* time candidate schedules at creation and keep the fastest */
+
 /* status codes */
 #define QFT_OK 0
 #define QFT_ERR_INVALID_N (-1)     /* N not a power of two, or outside the supported range */
@@ -80,7 +83,13 @@ typedef struct qft_plan_s* qft_plan;
  *          4 <= n <= 2^24 (R2C).
  *   batch  number of rows (>= 0; 0 makes every execute a no-op).
  *   kind   QFT_KIND_C2C or QFT_KIND_R2C; dtype QFT_DTYPE_*.
- *   flags  reserved, must be 0.
+ *   flags  0 or QFT_PLAN_AUTOTUNE.  With QFT_PLAN_AUTOTUNE the plan times the
+ *          forward transform under candidate schedules (tile sizes of the
+ *          phases, threads per CTA, input staging, node size and node threads
+ *          for n > 2^14) on up to ~256 MB of its own rows, on a private stream,
+ *          and keeps the fastest.  The schedule never changes the result: every
+ *          schedule performs the same FP32 operations on the same operands.
+ *          Results are cached per (n, kind, dtype, rows, device) in the process.
  * The plan owns the FP32 secant table (Sec. 6.1, N/4 entries) and every
  * scratch buffer; it allocates them here, on the current CUDA device, and
  * frees them in qft_plan_destroy.  Executions must run on that device.
@@ -97,6 +106,8 @@ int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype
  *                 elements [offsets[i], offsets[i+1]) of the packed buffer;
  *                 offsets[0] == 0 and offsets[i+1]-offsets[i] == 2^log2n[i].
  *   log2n_host    count int32 entries (host memory), each in [1, 24].
+ *   flags         0 or QFT_PLAN_AUTOTUNE (each length class is tuned on its own
+ *                 row count before the graph is captured).
  * Data layout: one packed complex buffer for input and one for output.
  * Supported: QFT_KIND_C2C, QFT_DTYPE_F32.
  */
@@ -189,6 +200,28 @@ int qft_plan_last_cuda_error(qft_plan plan);
 /* Launch geometry chosen for the plan: threads per CTA, CTAs, dynamic shared
  * memory bytes, and the number of kernel launches one execute issues. */
 int qft_plan_info(qft_plan plan, int* threads, int* ctas, int* smem_bytes, int* launches);
+
+/* Schedule of a single-size plan (the default, or the one QFT_PLAN_AUTOTUNE
+ * chose).  values receives 9 ints: threads per CTA, L1 (levels done while
+ * loading), LS (levels per in-place forward phase), LL (forward levels of the
+ * leaf tasks, 0 = per class), LB (backward levels per slice phase), LF
+ * (class-combine levels per final task), staging allowed (1/0), and for
+ * n > 2^14 the node size log2 and the node kernel's threads (else 0, 0). */
+int qft_plan_schedule(qft_plan plan, int* values);
+
+/*
+ * Launch timing (diagnostics, single-size plans).  qft_plan_time_launches(plan,
+ * 1) makes every following execute record a CUDA event pair around each of its
+ * kernel launches, on the execute's stream; 0 stops it.  Events are created on
+ * demand and owned by the plan.  qft_plan_launch_times synchronises with the
+ * recorded events and writes, per kernel kind, the summed milliseconds
+ * ms[4] and the number of launches launches[4] since timing was enabled (or
+ * since the previous read), then starts a new count.  Kinds: 0 the row kernel
+ * (n <= 2^14), 1 the large-row F1 / forward / final kernel, 2 the NODE kernel,
+ * 3 the SLICE kernel.  Ragged plans return QFT_ERR_INVALID_ARG.
+ */
+int qft_plan_time_launches(qft_plan plan, int enable);
+int qft_plan_launch_times(qft_plan plan, float* ms, int* launches);
 
 /* Human-readable text of a status code (static storage). */
 const char* qft_status_string(int status);

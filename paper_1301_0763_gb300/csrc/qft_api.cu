@@ -42,7 +42,16 @@ static int plan_check(qft_plan p) {
   return g_dead.count(p) ? QFT_ERR_DESTROYED : QFT_ERR_INVALID_ARG;
 }
 
+static void free_timing(qft_plan p) {
+  for (int i = 0; i < 2 * p->tev_cap; ++i)
+    if (p->tev[i]) cudaEventDestroy(p->tev[i]);
+  free(p->tev);
+  free(p->tev_kind);
+  p->tev = nullptr; p->tev_kind = nullptr; p->tev_n = 0; p->tev_cap = 0; p->timing = 0;
+}
+
 static void free_resources(qft_plan p) {
+  free_timing(p);
   cudaFree(p->d_status);
   p->d_status = nullptr;
   cudaFree(p->d_plan);
@@ -51,6 +60,40 @@ static void free_resources(qft_plan p) {
   cudaFree(p->scratch);
   free(p->large_host);
   p->d_plan = nullptr; p->d_sec = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->large_host = nullptr;
+}
+
+// (Re)builds the schedule of a plan of length 2^r >= 4 for the given tile
+// sizes, threads per CTA (row engine) and node size / NODE threads (large-row
+// path), and copies it to the device.  Returns QFT_ERR_INVALID_N if the
+// planner rejects the combination; the plan's previous schedule is then kept.
+static int plan_schedule(qft_plan p, QftTune t, int threads, int node_log2, int node_nt) {
+  const int r = p->r;
+  cudaError_t e = cudaSuccess;
+  if (r <= qft_lib::kMaxRowLog2) {
+    QftRowPlan hp;
+    if (qft_build_row_plan(r, t, &hp, threads) != 0 || hp.max_slice_nodes > threads) return QFT_ERR_INVALID_N;
+    const size_t smem = qft_lib::row_smem_bytes((int)p->n, hp.LF);
+    if (smem > (size_t)227 * 1024) return QFT_ERR_INVALID_N;
+    if (!p->d_plan) e = cudaMalloc(&p->d_plan, sizeof(QftRowPlan));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_plan, &hp, sizeof(QftRowPlan), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return qft_set_cuda(p, e);
+    p->host_plan = hp;
+    p->smem = smem;
+    p->threads = threads;
+  } else {
+    QftLargePlan* lp = (QftLargePlan*)malloc(sizeof(QftLargePlan));
+    if (!lp) return QFT_ERR_CUDA;
+    if (qft_build_large_plan(r, t, node_log2, node_nt, lp) != 0) { free(lp); return QFT_ERR_INVALID_N; }
+    if (!p->d_large) e = cudaMalloc(&p->d_large, sizeof(QftLargePlan));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_large, lp, sizeof(QftLargePlan), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free(lp); return qft_set_cuda(p, e); }
+    memcpy(p->large_host, lp, sizeof(QftLargePlan));
+    free(lp);
+    p->node_log2 = node_log2;
+    p->node_nt = node_nt;
+  }
+  p->tune = t;
+  return QFT_OK;
 }
 
 // Fills a freshly allocated plan for `batch` rows of length 2^r: schedule,
@@ -64,11 +107,15 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
   p->graph = nullptr; p->gexec = nullptr; p->graph_kernels = 0;
   p->d_status = nullptr;
   p->channels = 0;
+  p->timing = 0; p->tev_n = 0; p->tev_cap = 0; p->tev = nullptr; p->tev_kind = nullptr;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
   if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); return rc; }
+  p->no_stage = 0;
+  p->node_log2 = qft_lib::kNodeLog2;
+  p->node_nt = qft_lib::kNodeThreads;
   if (r >= 2) {
     p->tune = qft_default_tune(r);
     p->tune.L1 = qft_lib::kL1;
@@ -85,22 +132,9 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
     if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); return rc; }
     if (r <= qft_lib::kMaxRowLog2) {
       p->threads = qft_default_threads(r);
-      if (qft_build_row_plan(r, p->tune, &p->host_plan) != 0 || p->host_plan.max_slice_nodes > p->threads) {
-        free_resources(p);
-        return QFT_ERR_INVALID_N;
-      }
-      e = cudaMalloc(&p->d_plan, sizeof(QftRowPlan));
-      if (e == cudaSuccess) e = cudaMemcpy(p->d_plan, &p->host_plan, sizeof(QftRowPlan), cudaMemcpyHostToDevice);
-      p->smem = qft_lib::row_smem_bytes((int)N, p->host_plan.LF);
     } else {
       p->large_host = (QftLargePlan*)malloc(sizeof(QftLargePlan));
-      if (!p->large_host ||
-          qft_build_large_plan(r, p->tune, qft_lib::kNodeLog2, qft_lib::kNodeThreads, p->large_host) != 0) {
-        free_resources(p);
-        return QFT_ERR_INVALID_N;
-      }
-      e = cudaMalloc(&p->d_large, sizeof(QftLargePlan));
-      if (e == cudaSuccess) e = cudaMemcpy(p->d_large, p->large_host, sizeof(QftLargePlan), cudaMemcpyHostToDevice);
+      if (!p->large_host) { free_resources(p); return QFT_ERR_CUDA; }
       p->side_len = qft_side_len((int)N);
       const int64_t items = kind == QFT_KIND_R2C ? (batch + 1) / 2 : batch;
       const int64_t per_row = 2 * 2 * (int64_t)p->side_len * 8;
@@ -110,17 +144,179 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
       if (rows < 1) rows = 1;
       p->scratch_rows = rows;
       p->threads = 256;
-      if (e == cudaSuccess && items > 0) e = cudaMalloc(&p->scratch, (size_t)(rows * per_row));
+      if (items > 0) e = cudaMalloc(&p->scratch, (size_t)(rows * per_row));
+      if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); return rc; }
     }
-    if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); return rc; }
+    const int rc = plan_schedule(p, p->tune, p->threads, p->node_log2, p->node_nt);
+    if (rc != QFT_OK) { free_resources(p); return rc; }
   }
   return QFT_OK;
+}
+
+// The kernels of one execute of a single-size plan (arguments already checked).
+static int launch_plain(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
+  if (p->kind == QFT_KIND_R2C) return qft_launch_real(p, op, in, out, st);
+  switch (p->dtype) {
+  case QFT_DTYPE_F32: return qft_launch_c2c_f32(p, op, in, out, st);
+  case QFT_DTYPE_F16: return qft_launch_c2c_f16(p, op, in, out, st);
+  case QFT_DTYPE_BF16: return qft_launch_c2c_bf16(p, op, in, out, st);
+  default: return QFT_ERR_DTYPE;
+  }
+}
+
+// ------------------------------------------------------------------ autotuner
+// The schedule knobs (tile sizes of the phases, threads per CTA, input staging,
+// node size and NODE threads of the large-row path) change how the work is cut,
+// never an arithmetic operation or its operands, so every schedule gives the
+// same bits.  The tuner times the forward execute of candidate schedules on
+// the plan's own row count (capped so that a candidate moves ~256 MB) and keeps
+// the fastest, by coordinate descent from the default: one knob at a time over
+// its values, two sweeps.  Results are cached per (length, kind, dtype, rows,
+// device) for the life of the process.
+struct QftSched {
+  QftTune t;
+  int threads, no_stage, node_log2, node_nt;
+};
+
+static std::mutex g_tune_mu;
+struct TuneKey {
+  int r, kind, dtype, dev;
+  int64_t rows;
+  bool operator==(const TuneKey& o) const {
+    return r == o.r && kind == o.kind && dtype == o.dtype && dev == o.dev && rows == o.rows;
+  }
+};
+static TuneKey g_tune_keys[256];
+static QftSched g_tune_vals[256];
+static int g_tune_n = 0;
+
+static QftSched sched_of(qft_plan p) {
+  QftSched c;
+  c.t = p->tune; c.threads = p->threads; c.no_stage = p->no_stage;
+  c.node_log2 = p->node_log2; c.node_nt = p->node_nt;
+  return c;
+}
+
+static int sched_apply(qft_plan p, const QftSched& c) {
+  const int rc = plan_schedule(p, c.t, c.threads, c.node_log2, c.node_nt);
+  if (rc == QFT_OK) p->no_stage = c.no_stage;
+  return rc;
+}
+
+// Mean milliseconds of one forward execute on `rows` rows (or -1 if the
+// schedule cannot launch).
+static float tune_time(qft_plan p, const void* din, void* dout, int64_t rows, cudaStream_t st, cudaEvent_t e0,
+                       cudaEvent_t e1) {
+  const int64_t keep = p->batch;
+  p->batch = rows;
+  float ms = -1.f;
+  int rc = QFT_OK;
+  for (int w = 0; w < 2 && rc == QFT_OK; ++w) rc = launch_plain(p, QFT_OP_FORWARD, din, dout, st);
+  const int reps = 3;
+  if (rc == QFT_OK) {
+    cudaEventRecord(e0, st);
+    for (int k = 0; k < reps && rc == QFT_OK; ++k) rc = launch_plain(p, QFT_OP_FORWARD, din, dout, st);
+    cudaEventRecord(e1, st);
+  }
+  if (cudaStreamSynchronize(st) == cudaSuccess && rc == QFT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+    ms /= reps;
+  else
+    ms = -1.f;
+  cudaGetLastError();   // a schedule that cannot launch leaves no error behind
+  p->batch = keep;
+  p->last_cuda = cudaSuccess;
+  return ms;
+}
+
+static int autotune(qft_plan p) {
+  if (p->r < 3 || p->batch == 0) return QFT_OK;
+  const int64_t N = p->n;
+  const int64_t items = p->kind == QFT_KIND_R2C ? (p->batch + 1) / 2 : p->batch;
+  const int64_t row_bytes = p->kind == QFT_KIND_R2C ? 4 * N + 8 * (N / 2 + 1)
+                                                    : (p->dtype == QFT_DTYPE_F32 ? 16 : 8) * N;
+  int64_t cap = ((int64_t)256 << 20) / row_bytes;
+  if (cap < 1) cap = 1;
+  const int64_t rows = p->batch < cap ? p->batch : cap;
+  const TuneKey key{p->r, p->kind, p->dtype, p->device, rows};
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    for (int i = 0; i < g_tune_n; ++i)
+      if (g_tune_keys[i] == key) return sched_apply(p, g_tune_vals[i]);
+  }
+  (void)items;
+  void* din = nullptr;
+  void* dout = nullptr;
+  const size_t bytes = (size_t)rows * (size_t)N * 8 + 64;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&din, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&dout, bytes);
+  if (e == cudaSuccess) e = cudaMemset(din, 0, bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int rc = qft_set_cuda(p, e);
+  QftSched best = sched_of(p);
+  if (rc == QFT_OK) {
+    float best_ms = tune_time(p, din, dout, rows, st, e0, e1);
+    const bool large = p->r > qft_lib::kMaxRowLog2;
+    static const int kThreads[] = {256, 512};
+    static const int kLS[] = {2, 3, 4};
+    static const int kLL[] = {0, 2, 3, 4};
+    static const int kLB[] = {2, 3};
+    static const int kLF[] = {1, 2, 3};
+    static const int kStage[] = {0, 1};
+    static const int kNB[] = {10, 11, 12};
+    for (int sweep = 0; sweep < 2; ++sweep) {
+      for (int knob = 0; knob < 8; ++knob) {
+        const int* vals = nullptr;
+        int nv = 0;
+        switch (knob) {
+        case 0: if (!large) { vals = kThreads; nv = 2; } break;
+        case 1: vals = kLS; nv = 3; break;
+        case 2: vals = kLL; nv = 4; break;
+        case 3: vals = kLB; nv = 2; break;
+        case 4: if (!large) { vals = kLF; nv = 3; } break;
+        case 5: if (!large) { vals = kStage; nv = 2; } break;
+        case 6: if (large) { vals = kNB; nv = 3; } break;
+        case 7: if (large) { vals = kThreads; nv = 2; } break;
+        }
+        for (int v = 0; v < nv; ++v) {
+          QftSched c = best;
+          switch (knob) {
+          case 0: c.threads = vals[v]; break;
+          case 1: c.t.LS = vals[v]; break;
+          case 2: c.t.LL = vals[v]; break;
+          case 3: c.t.LB = vals[v]; break;
+          case 4: c.t.LF = vals[v]; break;
+          case 5: c.no_stage = vals[v]; break;
+          case 6: c.node_log2 = vals[v]; break;
+          case 7: c.node_nt = vals[v]; break;
+          }
+          if (memcmp(&c, &best, sizeof c) == 0) continue;
+          if (sched_apply(p, c) != QFT_OK) continue;
+          const float ms = tune_time(p, din, dout, rows, st, e0, e1);
+          if (ms > 0.f && (best_ms < 0.f || ms < 0.98f * best_ms)) { best = c; best_ms = ms; }
+        }
+        sched_apply(p, best);
+      }
+    }
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    if (g_tune_n < 256) { g_tune_keys[g_tune_n] = key; g_tune_vals[g_tune_n] = best; ++g_tune_n; }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(din);
+  cudaFree(dout);
+  if (rc == QFT_OK) rc = sched_apply(p, best);
+  return rc;
 }
 
 extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
   *out = nullptr;
-  if (flags != 0) return QFT_ERR_INVALID_ARG;
+  if ((flags & ~QFT_PLAN_AUTOTUNE) != 0) return QFT_ERR_INVALID_ARG;
   if (kind != QFT_KIND_C2C && kind != QFT_KIND_R2C) return QFT_ERR_DTYPE;
   if (dtype != QFT_DTYPE_F32 && dtype != QFT_DTYPE_F16 && dtype != QFT_DTYPE_BF16) return QFT_ERR_DTYPE;
   if (kind == QFT_KIND_R2C && dtype != QFT_DTYPE_F32) return QFT_ERR_DTYPE;
@@ -133,8 +329,12 @@ extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind
 
   qft_plan p = new (std::nothrow) qft_plan_s();
   if (!p) return QFT_ERR_CUDA;
-  const int rc = plan_init(p, r, batch, kind, dtype);
+  int rc = plan_init(p, r, batch, kind, dtype);
   if (rc != QFT_OK) { delete p; return rc; }
+  if (flags & QFT_PLAN_AUTOTUNE) {
+    rc = autotune(p);
+    if (rc != QFT_OK) { free_resources(p); delete p; return rc; }
+  }
   register_plan(p);
   *out = p;
   return QFT_OK;
@@ -171,7 +371,7 @@ extern "C" int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host
                                       int64_t count, int kind, int dtype, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
   *out = nullptr;
-  if (flags != 0) return QFT_ERR_INVALID_ARG;
+  if ((flags & ~QFT_PLAN_AUTOTUNE) != 0) return QFT_ERR_INVALID_ARG;
   if (kind != QFT_KIND_C2C || dtype != QFT_DTYPE_F32) return QFT_ERR_DTYPE;
   if (count < 0 || count > (int64_t(1) << 31)) return QFT_ERR_INVALID_BATCH;
   if (count > 0 && (!offsets_host || !log2n_host)) return QFT_ERR_NULLPTR;
@@ -202,6 +402,10 @@ extern "C" int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host
     if (!C.sub) { rc = QFT_ERR_CUDA; break; }
     rc = plan_init(C.sub, r, C.count, kind, dtype);
     if (rc != QFT_OK) { delete C.sub; C.sub = nullptr; break; }
+    if (flags & QFT_PLAN_AUTOTUNE) {
+      rc = autotune(C.sub);
+      if (rc != QFT_OK) break;
+    }
     int32_t* rows = (int32_t*)malloc(sizeof(int32_t) * (size_t)C.count);
     if (!rows) { rc = QFT_ERR_CUDA; break; }
     int64_t k = 0;
@@ -363,13 +567,7 @@ extern "C" int qft_execute(qft_plan p, int op, const void* in, void* out, void* 
   if (cur != p->device) return QFT_ERR_INVALID_ARG;
   if (p->kind == kKindFilter) return QFT_ERR_INVALID_ARG;
   if (p->classes) return exec_ragged(p, op, in, out, st);
-  if (p->kind == QFT_KIND_R2C) return qft_launch_real(p, op, in, out, st);
-  switch (p->dtype) {
-  case QFT_DTYPE_F32: return qft_launch_c2c_f32(p, op, in, out, st);
-  case QFT_DTYPE_F16: return qft_launch_c2c_f16(p, op, in, out, st);
-  case QFT_DTYPE_BF16: return qft_launch_c2c_bf16(p, op, in, out, st);
-  default: return QFT_ERR_DTYPE;
-  }
+  return launch_plain(p, op, in, out, st);
 }
 
 extern "C" int qft_execute_forward(qft_plan p, const void* in, void* out, void* stream) {
@@ -411,9 +609,49 @@ extern "C" int qft_plan_info(qft_plan p, int* threads, int* ctas, int* smem_byte
   int rc = plan_check(p);
   if (rc != QFT_OK) return rc;
   if (threads) *threads = p->threads;
-  if (ctas) *ctas = p->grid;
+  // large-row plans: the NODE launch's CTAs and every launch of every scratch chunk
+  const int64_t items = p->kind == QFT_KIND_R2C ? (p->batch + 1) / 2 : p->batch;
+  const int64_t chunks = p->scratch_rows > 0 ? (items + p->scratch_rows - 1) / p->scratch_rows : 0;
+  if (ctas) *ctas = p->large_host ? (int)(p->large_host->node_ctas * (p->scratch_rows < items ? p->scratch_rows : items))
+                                  : p->grid;
   if (smem_bytes) *smem_bytes = (int)p->smem;
-  if (launches) *launches = p->classes ? 1 + p->graph_kernels : (p->large_host ? p->large_host->nphase : 1);
+  if (launches) *launches = p->classes ? 1 + p->graph_kernels : (p->large_host ? (int)(p->large_host->nphase * chunks) : 1);
+  return QFT_OK;
+}
+
+extern "C" int qft_plan_time_launches(qft_plan p, int enable) {
+  int rc = plan_check(p);
+  if (rc != QFT_OK) return rc;
+  if (p->classes) return QFT_ERR_INVALID_ARG;
+  p->timing = enable ? 1 : 0;
+  p->tev_n = 0;
+  return QFT_OK;
+}
+
+extern "C" int qft_plan_launch_times(qft_plan p, float* ms, int* launches) {
+  int rc = plan_check(p);
+  if (rc != QFT_OK) return rc;
+  if (!ms || !launches) return QFT_ERR_NULLPTR;
+  for (int k = 0; k < QFT_KERNEL_KINDS; ++k) { ms[k] = 0.f; launches[k] = 0; }
+  for (int i = 0; i < p->tev_n; ++i) {
+    cudaError_t e = cudaEventSynchronize(p->tev[2 * i + 1]);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p->tev[2 * i], p->tev[2 * i + 1]);
+    if (e != cudaSuccess) return qft_set_cuda(p, e);
+    ms[p->tev_kind[i]] += t;
+    launches[p->tev_kind[i]] += 1;
+  }
+  p->tev_n = 0;
+  return QFT_OK;
+}
+
+extern "C" int qft_plan_schedule(qft_plan p, int* v) {
+  int rc = plan_check(p);
+  if (rc != QFT_OK) return rc;
+  if (!v) return QFT_ERR_NULLPTR;
+  v[0] = p->threads; v[1] = p->tune.L1; v[2] = p->tune.LS; v[3] = p->tune.LL; v[4] = p->tune.LB;
+  v[5] = p->tune.LF; v[6] = p->no_stage ? 0 : 1; v[7] = p->large_host ? p->node_log2 : 0;
+  v[8] = p->large_host ? p->node_nt : 0;
   return QFT_OK;
 }
 

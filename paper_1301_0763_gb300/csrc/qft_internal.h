@@ -57,6 +57,8 @@ struct qft_plan_s {
   float* d_sec;
   int grid;
   int threads;
+  int no_stage;               // 1: never stage input rows in shared memory
+  int node_log2, node_nt;     // large-row path: largest node group (log2 cells), NODE kernel threads
   int* d_status;              // device status word (QFT_OK or QFT_ERR_TIMEOUT)
   int64_t channels;           // spectral-filter plans: C (batch holds B)
   // large-row path (N > 2^kMaxRowLog2): schedule, scratch copies A and B
@@ -79,7 +81,43 @@ struct qft_plan_s {
   int sms;
   cudaError_t last_cuda;
   cudaStream_t last_stream;
+  // launch timing (qft_plan_time_launches): an event pair around each launch
+  int timing;
+  int tev_n, tev_cap;
+  cudaEvent_t* tev;           // 2 per recorded launch
+  int* tev_kind;              // QFT_KERNEL_* of each recorded launch
 };
+
+// Kernel kinds reported by qft_plan_launch_times.
+enum { QFT_KERNEL_ROWS = 0, QFT_KERNEL_GLOBAL = 1, QFT_KERNEL_NODE = 2, QFT_KERNEL_SLICE = 3, QFT_KERNEL_KINDS = 4 };
+
+// Records the start event of a launch of kind `kind` on `st` when timing is on.
+static inline void qft_time_begin(qft_plan p, cudaStream_t st, int kind) {
+  if (!p->timing) return;
+  if (p->tev_n == p->tev_cap) {
+    const int cap = p->tev_cap ? 2 * p->tev_cap : 64;
+    cudaEvent_t* ev = (cudaEvent_t*)realloc(p->tev, sizeof(cudaEvent_t) * 2 * (size_t)cap);
+    if (!ev) return;
+    p->tev = ev;
+    int* k = (int*)realloc(p->tev_kind, sizeof(int) * (size_t)cap);
+    if (!k) return;
+    p->tev_kind = k;
+    for (int i = 2 * p->tev_cap; i < 2 * cap; ++i) p->tev[i] = nullptr;
+    p->tev_cap = cap;
+  }
+  cudaEvent_t* pair = p->tev + 2 * p->tev_n;
+  if (!pair[0] && cudaEventCreate(&pair[0]) != cudaSuccess) return;
+  if (!pair[1] && cudaEventCreate(&pair[1]) != cudaSuccess) return;
+  p->tev_kind[p->tev_n] = kind;
+  cudaEventRecord(pair[0], st);
+}
+
+// Records the end event of the launch started by qft_time_begin.
+static inline void qft_time_end(qft_plan p, cudaStream_t st) {
+  if (!p->timing || p->tev_n >= p->tev_cap || !p->tev[2 * p->tev_n + 1]) return;
+  cudaEventRecord(p->tev[2 * p->tev_n + 1], st);
+  p->tev_n++;
+}
 
 
 static inline int qft_set_cuda(qft_plan p, cudaError_t e) {

@@ -12,7 +12,6 @@ namespace {
 
 constexpr int kLargeNT = 256;   // threads of the GLOBAL / SLICE kernels
 constexpr int kLargeTPT = 4;    // tasks per thread per CTA in those kernels
-constexpr int kNodeNT = 512;    // threads of the NODE kernel (top node SLICE: up to 512 tasks)
 
 struct LargeArgs {
   const QftLargePlan* plan;   // device copy of the plan
@@ -91,8 +90,8 @@ __host__ __device__ inline size_t node_smem_bytes(int NB) {
 // into shared memory, the sub-plan runs on them, and they are written to copy
 // `dst`.  base is a multiple of 16, so the padded layout of the window is the
 // padded layout of the scratch row shifted by qft_pidx(base).
-template <int L1>
-__global__ void __launch_bounds__(kNodeNT, 1) k_large_node(LargeArgs a) {
+template <int L1, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_sub;
   const QftLargePlan* LP = a.plan;
@@ -109,11 +108,11 @@ __global__ void __launch_bounds__(kNodeNT, 1) k_large_node(LargeArgs a) {
   {
     const int* src = reinterpret_cast<const int*>(&S.plan);
     int* dst = reinterpret_cast<int*>(smem);
-    for (int i = threadIdx.x; i < (int)(sizeof(QftRowPlan) / 4); i += kNodeNT) dst[i] = src[i];
+    for (int i = threadIdx.x; i < (int)(sizeof(QftRowPlan) / 4); i += NT) dst[i] = src[i];
   }
   const int NB = LP->NB;
   float* sec = reinterpret_cast<float*>(smem + qft_lib::align16(sizeof(QftRowPlan)));
-  for (int m = threadIdx.x; m <= (1 << NB); m += kNodeNT) sec[m] = a.gsec[m];
+  for (int m = threadIdx.x; m <= (1 << NB); m += NT) sec[m] = a.gsec[m];
   qc* cells = reinterpret_cast<qc*>(smem + qft_lib::align16(sizeof(QftRowPlan)) +
                                     qft_lib::align16(sizeof(float) * ((1 << NB) + 1)));
   const int g = cta - S.cta_begin;
@@ -123,7 +122,7 @@ __global__ void __launch_bounds__(kNodeNT, 1) k_large_node(LargeArgs a) {
   const int pn = qft_pidx(ncell - 1) + 1;
   const Eng ea = large_eng(a, 0, row);
   const qc* srcp = side_ptr(ea, S.side) + pb;
-  for (int i = threadIdx.x; i < pn; i += kNodeNT) cells[i] = srcp[i];
+  for (int i = threadIdx.x; i < pn; i += NT) cells[i] = srcp[i];
   __syncthreads();
   Eng e;
   e.side0 = cells - pb;     // the window maps class-level index base -> cells[0]
@@ -133,10 +132,10 @@ __global__ void __launch_bounds__(kNodeNT, 1) k_large_node(LargeArgs a) {
   e.N = 1 << a.r;
   e.tabC = nullptr;
   e.tabS = nullptr;
-  run_row_phases<L1, kNodeNT>(Q, e, NoIO(), g);
+  run_row_phases<L1, NT>(Q, e, NoIO(), g);
   const Eng ed = large_eng(a, S.dst, row);
   qc* dstp = side_ptr(ed, S.side) + pb;
-  for (int i = threadIdx.x; i < pn; i += kNodeNT) dstp[i] = cells[i];
+  for (int i = threadIdx.x; i < pn; i += NT) dstp[i] = cells[i];
 }
 
 // One execute on the large-row path: every phase of the plan, in order, for
@@ -153,8 +152,13 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
   a.side_len = p->side_len;
   a.r = p->r;
   const size_t node_smem = node_smem_bytes(H.NB);
-  cudaError_t e = cudaFuncSetAttribute(k_large_node<qft_lib::kL1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)node_smem);
+  // node kernel: 512 threads (one CTA per SM) unless the plan asks for 256
+  const bool n256 = p->node_nt == 256;
+  const int node_nt = n256 ? 256 : 512;
+  cudaError_t e = n256 ? cudaFuncSetAttribute(k_large_node<qft_lib::kL1, 256>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)node_smem)
+                       : cudaFuncSetAttribute(k_large_node<qft_lib::kL1, 512>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)node_smem);
   if (e != cudaSuccess) return qft_set_cuda(p, e);
   for (int64_t r0 = 0; r0 < items; r0 += p->scratch_rows) {
     const int64_t rows = items - r0 < p->scratch_rows ? items - r0 : p->scratch_rows;
@@ -162,14 +166,21 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
     for (int ph = 0; ph < H.nphase; ++ph) {
       const QftLargePhase& P = H.phases[ph];
       if (P.kind == QFT_LPH_NODE) {
-        k_large_node<qft_lib::kL1><<<dim3((unsigned)H.node_ctas, (unsigned)rows), kNodeNT, node_smem, st>>>(a);
+        const dim3 grid((unsigned)H.node_ctas, (unsigned)rows);
+        qft_time_begin(p, st, QFT_KERNEL_NODE);
+        if (n256) k_large_node<qft_lib::kL1, 256><<<grid, 256, node_smem, st>>>(a);
+        else k_large_node<qft_lib::kL1, 512><<<grid, node_nt, node_smem, st>>>(a);
       } else {
         const unsigned bx = (unsigned)((P.ntasks + kLargeNT * kLargeTPT - 1) / (kLargeNT * kLargeTPT));
-        if (P.kind == QFT_LPH_SLICE)
+        if (P.kind == QFT_LPH_SLICE) {
+          qft_time_begin(p, st, QFT_KERNEL_SLICE);
           k_large_slice<<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph);
-        else
+        } else {
+          qft_time_begin(p, st, QFT_KERNEL_GLOBAL);
           k_large_global<FAC, qft_lib::kL1><<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph, fac);
+        }
       }
+      qft_time_end(p, st);
       e = cudaGetLastError();
       if (e != cudaSuccess) return qft_set_cuda(p, e);
     }

@@ -49,6 +49,7 @@ struct QftRowPlan {
   int32_t nphase;
   int32_t nseg;
   int32_t max_slice_nodes;  // largest number of tasks sharing one node in a SLICE phase
+  int32_t in_last_phase;    // last phase whose tasks read the input row (F1 tasks)
   int32_t phase_ntasks[QFT_MAX_PHASES];
   int32_t phase_seg0[QFT_MAX_PHASES + 1];
   int32_t phase_is_slice[QFT_MAX_PHASES];

@@ -86,7 +86,12 @@ struct Builder {
 }  // namespace qft_planner_detail
 
 // Returns 0 on success, -1 for an unsupported r or tuning.
-static inline int qft_build_row_plan(int r, QftTune t, QftRowPlan* P) {
+// nt > 0 (threads per CTA) balances the phases for that CTA size: the F1 tasks
+// of the small classes and the base cells move to the next plain phase when
+// that saves an F1 round, and (nt >= 128) the special FINAL tasks, which do
+// not use the C/S tables, run in the table phase on the warps that do not
+// build the tables.
+static inline int qft_build_row_plan(int r, QftTune t, QftRowPlan* P, int nt = 0) {
   using qft_planner_detail::Builder;
   memset(P, 0, sizeof *P);
   if (r < 2 || r > 24) return -1;
@@ -109,13 +114,23 @@ static inline int qft_build_row_plan(int r, QftTune t, QftRowPlan* P) {
   Builder B;
   B.P = P;
   // ---- F1
+  int n_big = 0, n_small = 1;
+  for (int j = 0; j < ncls; ++j) {
+    if (big[j]) n_big += 1 << (r - 2 - j - t.L1);
+    else ++n_small;
+  }
+  const bool defer_small = nt > 0 && n_big > 0 && (n_big + n_small + nt - 1) / nt > (n_big + nt - 1) / nt;
+  const auto add_small = [&]() -> bool {
+    for (int j = 0; j < ncls; ++j)
+      if (!big[j] && !B.add(QFT_SEG_F1_SMALL, 0, j, r - 2 - j, 0, 1)) return false;
+    return B.add(QFT_SEG_F1_BASE, 0, 0, 0, 0, 1);
+  };
   B.begin(0);
   for (int j = 0; j < ncls; ++j)
     if (big[j] && !B.add(QFT_SEG_F1_BIG, 0, j, t.L1, 0, 1 << (r - 2 - j - t.L1))) return -1;
-  for (int j = 0; j < ncls; ++j)
-    if (!big[j] && !B.add(QFT_SEG_F1_SMALL, 0, j, r - 2 - j, 0, 1)) return -1;
-  if (!B.add(QFT_SEG_F1_BASE, 0, 0, 0, 0, 1)) return -1;
+  if (!defer_small && !add_small()) return -1;
   B.end();
+  bool small_pending = defer_small;
   // ---- DIF phases
   for (;;) {
     int Ls[32];
@@ -133,6 +148,11 @@ static inline int qft_build_row_plan(int r, QftTune t, QftRowPlan* P) {
     for (int side = 0; side < 2; ++side)
       for (int j = 0; j < ncls; ++j)
         if (Ls[j] > 0 && !B.add(QFT_SEG_DIF, side, j, Ls[j], depth[j], 1 << (r - 2 - j - Ls[j]))) return -1;
+    if (small_pending) {
+      if (!add_small()) return -1;
+      small_pending = false;
+      P->in_last_phase = P->nphase;
+    }
     B.end();
     for (int j = 0; j < ncls; ++j) depth[j] += Ls[j];
   }
@@ -145,6 +165,11 @@ static inline int qft_build_row_plan(int r, QftTune t, QftRowPlan* P) {
         if (L < 1 || L > 4) return -1;
         if (!B.add(QFT_SEG_LEAF, side, j, L, depth[j], 1 << depth[j])) return -1;
       }
+  if (small_pending) {
+    if (!add_small()) return -1;
+    small_pending = false;
+    P->in_last_phase = P->nphase;
+  }
   B.end();
   // ---- SLICE phases (segments sorted by decreasing node task count S)
   for (;;) {
@@ -172,14 +197,21 @@ static inline int qft_build_row_plan(int r, QftTune t, QftRowPlan* P) {
     B.end();
     for (int j = 0; j < ncls; ++j) depth[j] -= Ls[j];
   }
-  // ---- tables of C_Mt, S_Mt for the FINAL tasks (no tasks: built by two warps)
+  // ---- tables of C_Mt, S_Mt for the FINAL tasks (built by warps 0 and 1; the
+  // other warps may run the special FINAL tasks meanwhile)
+  const bool spec_in_tab = nt >= 128;
   B.begin(2);
-  B.end_empty();
+  if (spec_in_tab) {
+    if (!B.add(QFT_SEG_FIN_SPEC, 0, 0, LF, 0, (1 << LF) + 1)) return -1;
+    B.end();
+  } else {
+    B.end_empty();
+  }
   // ---- FINAL
   B.begin(0);
   const int W = 1 << (r - LF - 1);
   if (W >= 2 && !B.add(QFT_SEG_FIN_REG, 0, 0, LF, 0, W - 1)) return -1;
-  if (!B.add(QFT_SEG_FIN_SPEC, 0, 0, LF, 0, (1 << LF) + 1)) return -1;
+  if (!spec_in_tab && !B.add(QFT_SEG_FIN_SPEC, 0, 0, LF, 0, (1 << LF) + 1)) return -1;
   B.end();
   return 0;
 }

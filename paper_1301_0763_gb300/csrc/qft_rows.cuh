@@ -176,6 +176,15 @@ __device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e
         for (int m = 1; m <= mt; ++m) { tab_level_c(e, m, lane, 32); __syncwarp(); }
       } else if (warp == 1) {
         for (int m = 2; m <= mt; ++m) { tab_level_s(e, m, lane, 32); __syncwarp(); }
+      } else {
+        // the phase's own tasks (special FINAL tasks, which read no table)
+        int sgi = P.phase_seg0[p];
+        const int sge = P.phase_seg0[p + 1];
+        for (int tau = tid - 64; tau < nt; tau += NT - 64) {
+          while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
+          const QftSeg& sg = P.segs[sgi];
+          run_plain_task<L1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin);
+        }
       }
       __syncthreads();
       continue;
@@ -191,7 +200,7 @@ __device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e
         run_plain_task<L1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin);
       }
       __syncthreads();
-      if (p == 0) after_f1();
+      if (p == P.in_last_phase) after_f1();
     } else {
       for (int rb = 0; rb < nt; rb += NT) {
         const int tau = rb + tid;
@@ -321,7 +330,7 @@ static inline int launch_rows_nt(qft_plan p, FAC fac, int64_t items, size_t stag
   // stage the input rows in shared memory when the staging buffer keeps two CTAs per SM
   int stage_off = 0;
   size_t smem = p->smem;
-  if (FAC::kCanStage && stage_ok && stage_bytes > 0) {
+  if (FAC::kCanStage && stage_ok && stage_bytes > 0 && !p->no_stage) {
     const size_t off = (p->smem + 127) & ~(size_t)127;
     if (NT == 256 && off + stage_bytes <= (size_t)(227 * 1024) / 2) { stage_off = (int)off; smem = off + stage_bytes; }
   }
@@ -330,7 +339,9 @@ static inline int launch_rows_nt(qft_plan p, FAC fac, int64_t items, size_t stag
   int rc = occupancy_grid(p, kern, NT, items);
   p->smem = keep;
   if (rc != QFT_OK) return rc;
+  qft_time_begin(p, st, QFT_KERNEL_ROWS);
   kern<<<p->grid, NT, smem, st>>>(p->d_plan, p->d_sec, 1, items, fac, stage_off, p->d_status);
+  qft_time_end(p, st);
   return qft_set_cuda(p, cudaGetLastError());
 }
 

@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(_PKG, "_qft_gb300.so")
 KIND_C2C, KIND_R2C = 0, 1
 DTYPE_F32, DTYPE_F16, DTYPE_BF16 = 0, 1, 2
 OP_FORWARD, OP_INVERSE, OP_FORWARD_ADJOINT, OP_INVERSE_ADJOINT = 0, 1, 2, 3
+PLAN_AUTOTUNE = 1
 
 _lib = None
 _lock = threading.Lock()
@@ -66,6 +67,9 @@ def load_library(path: str | None = None):
         lib.qft_filter_forward.argtypes = [vp, vp, vp, vp, vp]
         lib.qft_filter_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.qft_execute_static_scratch.argtypes = [i64, i64, ci, vp, vp, vp]
+        lib.qft_plan_schedule.argtypes = [vp, ctypes.POINTER(ci)]
+        lib.qft_plan_time_launches.argtypes = [vp, ci]
+        lib.qft_plan_launch_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ci)]
         lib.qft_status_string.argtypes = [ci]
         lib.qft_status_string.restype = ctypes.c_char_p
         _lib = lib
@@ -89,7 +93,8 @@ def _stream_handle(stream=None) -> int:
 class Plan:
     """A plan of `batch` transforms of length `n` (see qft_plan_create)."""
 
-    def __init__(self, n: int, batch: int, kind: int = KIND_C2C, dtype: int = DTYPE_F32, device=None):
+    def __init__(self, n: int, batch: int, kind: int = KIND_C2C, dtype: int = DTYPE_F32, device=None,
+                 autotune: bool = False):
         self.lib = load_library()
         self.n, self.batch, self.kind, self.dtype = int(n), int(batch), int(kind), int(dtype)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
@@ -97,7 +102,25 @@ class Plan:
         self.handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(self.lib.qft_plan_create(ctypes.byref(self.handle), self.n, self.batch, self.kind,
-                                            self.dtype, 0), "qft_plan_create")
+                                            self.dtype, PLAN_AUTOTUNE if autotune else 0), "qft_plan_create")
+
+    def time_launches(self, enable: bool = True):
+        _check(self.lib.qft_plan_time_launches(self.handle, 1 if enable else 0), "qft_plan_time_launches")
+
+    def launch_times(self) -> dict:
+        """{kernel kind: (summed ms, launches)} of the executes since timing was enabled."""
+        ms = (ctypes.c_float * 4)()
+        n = (ctypes.c_int * 4)()
+        _check(self.lib.qft_plan_launch_times(self.handle, ms, n), "qft_plan_launch_times")
+        names = ("k_rows", "k_large_global", "k_large_node", "k_large_slice")
+        return {names[k]: (float(ms[k]), int(n[k])) for k in range(4) if n[k]}
+
+    def schedule(self) -> dict:
+        """The plan's schedule (see qft_plan_schedule)."""
+        v = (ctypes.c_int * 9)()
+        _check(self.lib.qft_plan_schedule(self.handle, v), "qft_plan_schedule")
+        keys = ("threads", "L1", "LS", "LL", "LB", "LF", "staging", "node_log2", "node_threads")
+        return dict(zip(keys, list(v)))
 
     def execute(self, op: int, inp: torch.Tensor, out: torch.Tensor, stream=None):
         with torch.cuda.device(self.device):
@@ -133,7 +156,7 @@ class RaggedPlan(Plan):
     [offsets[i], offsets[i+1]) and has length 2^log2n[i].  One execute is one
     CUDA-graph launch of every length class."""
 
-    def __init__(self, offsets, log2n, device=None):
+    def __init__(self, offsets, log2n, device=None, autotune: bool = False):
         import numpy as np
         self.lib = load_library()
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
@@ -147,7 +170,8 @@ class RaggedPlan(Plan):
         with torch.cuda.device(self.device):
             _check(self.lib.qft_plan_create_ragged(
                 ctypes.byref(self.handle), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                lg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.count, KIND_C2C, DTYPE_F32, 0),
+                lg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.count, KIND_C2C, DTYPE_F32,
+                PLAN_AUTOTUNE if autotune else 0),
                 "qft_plan_create_ragged")
 
 
@@ -226,11 +250,21 @@ def spectral_filter(x: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
 _plans: dict = {}
 
 
+_autotune = False
+
+
+def set_autotune(enable: bool):
+    """Make the plans that fft / ifft / rfft / irfft create from now on autotuned
+    (QFT_PLAN_AUTOTUNE); plans already cached keep their schedule."""
+    global _autotune
+    _autotune = bool(enable)
+
+
 def get_plan(n: int, batch: int, kind: int, dtype: int, device: torch.device) -> Plan:
-    key = (n, batch, kind, dtype, device.index)
+    key = (n, batch, kind, dtype, device.index, _autotune)
     p = _plans.get(key)
     if p is None:
-        p = Plan(n, batch, kind, dtype, device)
+        p = Plan(n, batch, kind, dtype, device, autotune=_autotune)
         _plans[key] = p
     return p
 

@@ -24,6 +24,16 @@ static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr, i
       const int mt = P.r - P.LF;
       for (int m = 1; m <= mt; ++m) for (int lane = 0; lane < 32; ++lane) tab_level_c(e, m, lane, 32);
       for (int m = 2; m <= mt; ++m) for (int lane = 0; lane < 32; ++lane) tab_level_s(e, m, lane, 32);
+      for (int tau = 0; tau < nt; ++tau) {
+        const QftSeg& sg = find_seg(P, p, tau);
+        switch (P.L1) {
+        case 0: run_plain_task<0>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+        case 1: run_plain_task<1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+        case 2: run_plain_task<2>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+        case 3: run_plain_task<3>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+        default: run_plain_task<4>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+        }
+      }
       continue;
     }
     if (!P.phase_is_slice[p]) {
@@ -71,7 +81,7 @@ struct Row {
     if (nthr <= 0) nthr = qft_default_threads(r);
     QftTune t = qft_default_tune(r);
     if (tune) { t.L1 = tune[0]; t.LS = tune[1]; t.LL = tune[2]; t.LB = tune[3]; t.LF = tune[4]; }
-    ok = qft_build_row_plan(r, t, &P) == 0 && P.max_slice_nodes <= nthr;
+    ok = qft_build_row_plan(r, t, &P, nthr) == 0 && P.max_slice_nodes <= nthr;
     s0.assign(qft_side_len(N), mkc(NAN, NAN));
     s1.assign(qft_side_len(N), mkc(NAN, NAN));
     sec.assign(N / 4 + 1, 0.f);

@@ -386,3 +386,67 @@ def test_spectral_filter_small_exhaustive(q):
     assert np.abs(y.detach().cpu().numpy() - y64).max() < 1e-5 * np.abs(y64).max()
     assert np.linalg.norm(xt.grad.cpu().numpy() - gx_ref) / np.linalg.norm(gx_ref) < 1e-5
     assert np.linalg.norm(Wt.grad.cpu().numpy() - gW_ref) / np.linalg.norm(gW_ref) < 1e-5
+
+
+# ------------------------------------------------------------------ autotuner
+@pytest.mark.parametrize("r,rows,kind,dtype", [(10, 512, 0, 0), (12, 256, 0, 0), (14, 64, 0, 0), (13, 64, 1, 0),
+                                               (12, 128, 0, 1), (11, 128, 0, 2), (16, 24, 0, 0), (17, 9, 1, 0)])
+def test_autotuned_plan_same_bits(q, r, rows, kind, dtype):
+    """A plan created with QFT_PLAN_AUTOTUNE may pick another schedule (tile
+    sizes, threads, staging, node size); its output is the same bits as the
+    default plan's, for every operation."""
+    N = 1 << r
+    pd = q.Plan(N, rows, kind=kind, dtype=dtype)
+    pt = q.Plan(N, rows, kind=kind, dtype=dtype, autotune=True)
+    sd, st = pd.schedule(), pt.schedule()
+    assert st["threads"] in (256, 512) and 1 <= st["LB"] <= 3 and 0 <= st["LF"] <= 3
+    if r > 14:
+        assert st["node_log2"] in (10, 11, 12) and st["node_threads"] in (256, 512)
+    if kind == 1:
+        x = gpu(inputs.normal_real(rows, N, seed=51))
+        outs = []
+        for p in (pd, pt):
+            y = torch.empty(rows, N // 2 + 1, dtype=torch.complex64, device="cuda")
+            p.execute(q.OP_FORWARD, x, y)
+            z = torch.empty(rows, N, dtype=torch.float32, device="cuda")
+            p.execute(q.OP_INVERSE, y, z)
+            outs.append((y.cpu().numpy(), z.cpu().numpy()))
+        assert bits_equal(outs[0][0], outs[1][0]) and bits_equal(outs[0][1], outs[1][1])
+    else:
+        z = inputs.normal_complex(rows, N, seed=52)
+        if dtype == 0:
+            x = gpu(z.astype(np.complex64))
+        else:
+            pair = np.stack([z.real, z.imag], -1).astype(np.float32)
+            t = torch.from_numpy(pair).cuda()
+            x = (t.half() if dtype == 1 else t.bfloat16()).contiguous()
+        for op in (q.OP_FORWARD, q.OP_INVERSE, q.OP_FORWARD_ADJOINT):
+            ya = torch.empty_like(x)
+            yb = torch.empty_like(x)
+            pd.execute(op, x, ya)
+            pt.execute(op, x, yb)
+            torch.cuda.synchronize()
+            assert torch.equal(ya.view(torch.int16) if dtype else ya.view(torch.int32),
+                               yb.view(torch.int16) if dtype else yb.view(torch.int32)), (op, sd, st)
+    pd.destroy()
+    pt.destroy()
+
+
+def test_autotuned_ragged_same_bits(q):
+    """The uneven batch with every length class autotuned: same bits as the
+    default ragged plan."""
+    g = inputs.rng(61)
+    log2n = np.concatenate([np.arange(4, 18), g.integers(4, 15, 30)]).astype(np.int32)
+    g.shuffle(log2n)
+    offsets = inputs.ragged_offsets(log2n)
+    total = int(offsets[-1])
+    z = gpu(inputs.ragged_values(total, seed=61).astype(np.complex64))
+    outs = []
+    for tune in (False, True):
+        p = q.RaggedPlan(offsets, log2n, autotune=tune)
+        y = torch.empty_like(z)
+        p.execute(q.OP_FORWARD, z, y)
+        torch.cuda.synchronize()
+        outs.append(y.cpu().numpy())
+        p.destroy()
+    assert bits_equal(outs[0], outs[1])
