@@ -110,6 +110,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, ws: int, device=None) -> float:
+    """The timed region's length as the job sees it: the maximum over ranks
+    (every rank holds the same per-GPU workload; no data-path collective)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(bytes_per_step_per_rank: int, steps: int, ms: float, ws: int) -> float:
+    """Whole-job algorithmic GB/s: the bytes all ranks processed over the max time."""
+    return ws * bytes_per_step_per_rank * steps / (ms * 1e-3) / 1e9
+
+
 def cpu_reference_run(logs, steps, warmup, sample_elems, threads):
     """Times the FP64 oracle (as it stands) on a bounded sample of each size."""
     from oracle import oracle as orc
@@ -233,18 +250,14 @@ def run_gpu(args):
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
-    ms = t0.elapsed_time(t1)
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t0.elapsed_time(t1), ws, dev)
     kt = {}
     for lg in logs:
         kt[lg] = plans[lg].launch_times()
         plans[lg].time_launches(False)
     bytes_per_step = 16 * ELEMS * len(logs)
     flops_per_step = sum(5 * ELEMS * lg for lg in logs)
-    value = ws * bytes_per_step * args.steps / (ms * 1e-3) / 1e9
+    value = job_value(bytes_per_step, args.steps, ms, ws)
     gflops = ws * flops_per_step * args.steps / (ms * 1e-3) / 1e9
     per_size = {}
     for lg in logs:
