@@ -202,12 +202,20 @@ int qft_plan_last_cuda_error(qft_plan plan);
 int qft_plan_info(qft_plan plan, int* threads, int* ctas, int* smem_bytes, int* launches);
 
 /* Schedule of a single-size plan (the default, or the one QFT_PLAN_AUTOTUNE
- * chose).  values receives 9 ints: threads per CTA, L1 (levels done while
+ * chose).  values receives 10 ints: threads per CTA, L1 (levels done while
  * loading), LS (levels per in-place forward phase), LL (forward levels of the
  * leaf tasks, 0 = per class), LB (backward levels per slice phase), LF
  * (class-combine levels per final task), staging allowed (1/0), and for
- * n > 2^14 the node size log2 and the node kernel's threads (else 0, 0). */
+ * n > 2^14 the node size log2, the node kernel's threads and the rows per
+ * launch sequence (fewer rows keep a chunk's scratch copies in L2) (else 0). */
 int qft_plan_schedule(qft_plan plan, int* values);
+
+/* Sets the schedule of a single-size plan from the same 10 values (L1 must be
+ * the library's 3, LB at most 3; threads and node threads 256 or 512).  Every
+ * schedule gives the same results; QFT_ERR_INVALID_N if the planner rejects the
+ * combination for this n (the previous schedule is kept), QFT_ERR_INVALID_ARG
+ * for ragged or filter plans or out-of-range values. */
+int qft_plan_set_schedule(qft_plan plan, const int* values);
 
 /*
  * Launch timing (diagnostics, single-size plans).  qft_plan_time_launches(plan,

@@ -102,6 +102,7 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
   p->magic = kMagic; p->kind = kind; p->dtype = dtype; p->n = int64_t(1) << r; p->batch = batch; p->r = r;
   p->d_plan = nullptr; p->d_sec = nullptr; p->last_cuda = cudaSuccess; p->last_stream = nullptr;
   p->large_host = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->scratch_rows = 0; p->side_len = 0;
+  p->chunk_rows = 0;
   p->grid = 0; p->threads = 0; p->smem = 0;
   p->nclasses = 0; p->classes = nullptr; p->d_offsets = nullptr; p->d_args = nullptr; p->h_args = nullptr;
   p->graph = nullptr; p->gexec = nullptr; p->graph_kernels = 0;
@@ -176,6 +177,7 @@ static int launch_plain(qft_plan p, int op, const void* in, void* out, cudaStrea
 struct QftSched {
   QftTune t;
   int threads, no_stage, node_log2, node_nt;
+  int64_t chunk_rows;
 };
 
 static std::mutex g_tune_mu;
@@ -190,16 +192,23 @@ static TuneKey g_tune_keys[256];
 static QftSched g_tune_vals[256];
 static int g_tune_n = 0;
 
+static bool sched_same(const QftSched& a, const QftSched& b) {
+  return a.t.L1 == b.t.L1 && a.t.LS == b.t.LS && a.t.LL == b.t.LL && a.t.LB == b.t.LB && a.t.LF == b.t.LF &&
+         a.threads == b.threads && a.no_stage == b.no_stage && a.node_log2 == b.node_log2 &&
+         a.node_nt == b.node_nt && a.chunk_rows == b.chunk_rows;
+}
+
 static QftSched sched_of(qft_plan p) {
   QftSched c;
   c.t = p->tune; c.threads = p->threads; c.no_stage = p->no_stage;
   c.node_log2 = p->node_log2; c.node_nt = p->node_nt;
+  c.chunk_rows = p->chunk_rows;
   return c;
 }
 
 static int sched_apply(qft_plan p, const QftSched& c) {
   const int rc = plan_schedule(p, c.t, c.threads, c.node_log2, c.node_nt);
-  if (rc == QFT_OK) p->no_stage = c.no_stage;
+  if (rc == QFT_OK) { p->no_stage = c.no_stage; p->chunk_rows = c.chunk_rows; }
   return rc;
 }
 
@@ -293,7 +302,7 @@ static int autotune(qft_plan p) {
           case 6: c.node_log2 = vals[v]; break;
           case 7: c.node_nt = vals[v]; break;
           }
-          if (memcmp(&c, &best, sizeof c) == 0) continue;
+          if (sched_same(c, best)) continue;
           if (sched_apply(p, c) != QFT_OK) continue;
           const float ms = tune_time(p, din, dout, rows, st, e0, e1);
           if (ms > 0.f && (best_ms < 0.f || ms < 0.98f * best_ms)) { best = c; best_ms = ms; }
@@ -611,8 +620,9 @@ extern "C" int qft_plan_info(qft_plan p, int* threads, int* ctas, int* smem_byte
   if (threads) *threads = p->threads;
   // large-row plans: the NODE launch's CTAs and every launch of every scratch chunk
   const int64_t items = p->kind == QFT_KIND_R2C ? (p->batch + 1) / 2 : p->batch;
-  const int64_t chunks = p->scratch_rows > 0 ? (items + p->scratch_rows - 1) / p->scratch_rows : 0;
-  if (ctas) *ctas = p->large_host ? (int)(p->large_host->node_ctas * (p->scratch_rows < items ? p->scratch_rows : items))
+  const int64_t crow = p->chunk_rows > 0 && p->chunk_rows < p->scratch_rows ? p->chunk_rows : p->scratch_rows;
+  const int64_t chunks = crow > 0 ? (items + crow - 1) / crow : 0;
+  if (ctas) *ctas = p->large_host ? (int)(p->large_host->node_ctas * (crow < items ? crow : items))
                                   : p->grid;
   if (smem_bytes) *smem_bytes = (int)p->smem;
   if (launches) *launches = p->classes ? 1 + p->graph_kernels : (p->large_host ? (int)(p->large_host->nphase * chunks) : 1);
@@ -652,7 +662,29 @@ extern "C" int qft_plan_schedule(qft_plan p, int* v) {
   v[0] = p->threads; v[1] = p->tune.L1; v[2] = p->tune.LS; v[3] = p->tune.LL; v[4] = p->tune.LB;
   v[5] = p->tune.LF; v[6] = p->no_stage ? 0 : 1; v[7] = p->large_host ? p->node_log2 : 0;
   v[8] = p->large_host ? p->node_nt : 0;
+  v[9] = p->large_host ? (int)(p->chunk_rows > 0 && p->chunk_rows < p->scratch_rows ? p->chunk_rows : p->scratch_rows) : 0;
   return QFT_OK;
+}
+
+extern "C" int qft_plan_set_schedule(qft_plan p, const int* v) {
+  int rc = plan_check(p);
+  if (rc != QFT_OK) return rc;
+  if (!v) return QFT_ERR_NULLPTR;
+  if (p->classes || p->kind == kKindFilter || p->r < 2) return QFT_ERR_INVALID_ARG;
+  QftSched c = sched_of(p);
+  c.threads = p->large_host ? p->threads : v[0];
+  if (!p->large_host && c.threads != 256 && c.threads != 512) return QFT_ERR_INVALID_ARG;
+  if (v[1] != qft_lib::kL1) return QFT_ERR_INVALID_ARG;
+  c.t.LS = v[2]; c.t.LL = v[3]; c.t.LB = v[4]; c.t.LF = v[5];
+  if (c.t.LB > qft_lib::kLB) return QFT_ERR_INVALID_ARG;
+  c.no_stage = v[6] ? 0 : 1;
+  if (p->large_host) {
+    if (v[8] != 256 && v[8] != 512) return QFT_ERR_INVALID_ARG;
+    if (v[9] < 0) return QFT_ERR_INVALID_ARG;
+    c.node_log2 = v[7]; c.node_nt = v[8];
+    c.chunk_rows = v[9] >= p->scratch_rows ? 0 : v[9];
+  }
+  return sched_apply(p, c);
 }
 
 extern "C" const char* qft_status_string(int s) {

@@ -56,10 +56,13 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #define QFT_HD __host__ __device__ __forceinline__
+// tasks that run a few times per row (inlined like the others: out-of-line calls cost spills)
+#define QFT_RARE __host__ __device__ __forceinline__
 typedef float2 qc;
 #else
 #include <string.h>
 #define QFT_HD inline
+#define QFT_RARE inline
 struct qc { float x, y; };
 #endif
 
@@ -239,7 +242,7 @@ QFT_HD void task_f1_big(const Eng& e, const IO& io, int j, int ilo) {
 // Class r-2 (one cell, n = N/4) has no DST class; its DST value d(N/4) is the
 // dst(4) base case and goes to the DST base cell.
 template <int L, class IO>
-QFT_HD void task_f1_small(const Eng& e, const IO& io, int j) {
+QFT_RARE void task_f1_small(const Eng& e, const IO& io, int j) {
   qc vc[1 << L], vs[1 << L];
 #pragma unroll
   for (int g = 0; g < (1 << L); ++g) io.get_cd((2 * ig_c(g) + 1) << j, vc[g], vs[g]);
@@ -356,7 +359,7 @@ QFT_HD qc cls_out(const Eng& e, int s, int j, int k) {
 // class outputs bottom-up in the recursion's order.  Branch-free: every lane
 // executes the same instructions (the eq qft_6 case keeps v; v - O is computed
 // as v + (-O), which is the same IEEE operation).
-QFT_HD qc chain_c(const Eng& e, int m, int k) {
+QFT_RARE qc chain_c(const Eng& e, int m, int k) {
   uint64_t ops = 0;
   const int nl = m - 1;
   for (int i = 0; i < nl; ++i) {
@@ -386,7 +389,7 @@ QFT_HD qc chain_c(const Eng& e, int m, int k) {
 // S_M(k), k in [1, M/2-1]: same walk for the dst recursion; it stops at
 // k = M/4 (S_M(M/4) = O(M/4)) or at the dst(4) base.  The walk runs over every
 // level in every lane; levels below the stop only carry a dummy in-range index.
-QFT_HD qc chain_s(const Eng& e, int m, int k) {
+QFT_RARE qc chain_s(const Eng& e, int m, int k) {
   uint64_t ops = 0;
   const int nl = m - 2;                  // levels M = 2^m .. 8 above the dst(4) base
   int stop = nl;                         // first level (from the top) with k == M/4
@@ -422,7 +425,7 @@ QFT_HD qc chain_s(const Eng& e, int m, int k) {
 // (m = 1 builds C_2 from c(0), c(N/2)); tab_level_s(m) builds S_{2^m}
 // (m = 2 is the dst(4) base).  Lanes split the k range; levels are separated
 // by a (warp) barrier.
-QFT_HD void tab_level_c(const Eng& e, int m, int lane, int nl) {
+QFT_RARE void tab_level_c(const Eng& e, int m, int lane, int nl) {
   if (m == 1) {
     if (lane == 0) {
       const qc c0 = e.side0[qft_pidx(e.N / 2 - 1)], c1 = e.side0[qft_pidx(e.N / 2)];
@@ -441,7 +444,7 @@ QFT_HD void tab_level_c(const Eng& e, int m, int lane, int nl) {
   }
 }
 
-QFT_HD void tab_level_s(const Eng& e, int m, int lane, int nl) {
+QFT_RARE void tab_level_s(const Eng& e, int m, int lane, int nl) {
   if (m == 2) {
     if (lane == 0) e.tabS[1] = e.side1[qft_pidx(e.N / 2 - 2)];
     return;
@@ -493,7 +496,7 @@ QFT_HD void task_fin_reg(const Eng& e, const IO& io, int k0) {
 
 // Multiples of N/2^(LF+1): one bin pair per task, full chain from periodization N.
 template <class IO>
-QFT_HD void task_fin_spec(const Eng& e, const IO& io, int LF, int mi) {
+QFT_RARE void task_fin_spec(const Eng& e, const IO& io, int LF, int mi) {
   const int k = mi * (e.N >> (LF + 1));
   const qc C = chain_c(e, e.r, k);
   const qc S = (k > 0 && k < e.N / 2) ? chain_s(e, e.r, k) : mkc(0.f, 0.f);

@@ -64,6 +64,7 @@ __device__ __forceinline__ Eng filt_setup(unsigned char* smem, const FiltArgs& a
   return e;
 }
 
+#ifndef QFT_FILTER_BACKWARD_TU
 __global__ void __launch_bounds__(kFiltNT, 2) k_filter_fwd(FiltArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Eng e = filt_setup(smem, a);
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(kFiltNT, 2) k_filter_fwd(FiltArgs a) {
   }
 }
 
+#else
 // blockIdx.x = c * kFiltParts + part
 __global__ void __launch_bounds__(kFiltNT, 1) k_filter_bwd(FiltArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -142,20 +144,51 @@ __global__ void k_filter_reduce(const qc* __restrict__ gwpart, qc* __restrict__ 
   for (int p = 1; p < kFiltParts; ++p) s = cadd(s, gwpart[((int64_t)c * kFiltParts + p) * H + k]);
   gw[i] = s;
 }
+#endif  // QFT_FILTER_BACKWARD_TU
 
-}  // namespace
-
-int qft_filter_smem(int N, int LF, int backward) { return (int)filt_layout(N, LF, backward != 0).total; }
-int qft_filter_parts() { return kFiltParts; }
-
-int qft_launch_filter(qft_plan p, int backward, const float* x, const void* W, const float* gy, float* out,
-                      void* gW, cudaStream_t st) {
+FiltArgs filt_args(qft_plan p, const float* x, const void* W, const float* gy, float* out) {
   FiltArgs a;
   a.plan = p->d_plan; a.gsec = p->d_sec; a.x = x; a.W = static_cast<const qc*>(W); a.gy = gy; a.y = out;
   a.gwpart = reinterpret_cast<qc*>(p->scratch);
   a.B = (int)p->batch; a.C = (int)p->channels; a.N = (int)p->n;
+  return a;
+}
+
+}  // namespace
+
+// The backward kernels are compiled in their own translation unit
+// (qft_filter_bwd.cu), in parallel with the forward one.
+int qft_launch_filter_bwd(qft_plan p, const float* x, const void* W, const float* gy, float* gx, void* gW,
+                          cudaStream_t st);
+
+#ifdef QFT_FILTER_BACKWARD_TU
+int qft_launch_filter_bwd(qft_plan p, const float* x, const void* W, const float* gy, float* gx, void* gW,
+                          cudaStream_t st) {
+  const FiltArgs a = filt_args(p, x, W, gy, gx);
+  const int smem = (int)filt_layout(a.N, p->host_plan.LF, true).total;
+  cudaError_t e = cudaFuncSetAttribute(k_filter_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return qft_set_cuda(p, e);
+  k_filter_bwd<<<(unsigned)(a.C * kFiltParts), kFiltNT, smem, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return qft_set_cuda(p, e);
+  const int H = a.N / 2 + 1;
+  const int64_t n = (int64_t)a.C * H;
+  k_filter_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.gwpart, static_cast<qc*>(gW), a.C, H);
+  return qft_set_cuda(p, cudaGetLastError());
+}
+#else
+
+#ifndef QFT_FILTER_BACKWARD_TU
+int qft_filter_smem(int N, int LF, int backward) { return (int)filt_layout(N, LF, backward != 0).total; }
+int qft_filter_parts() { return kFiltParts; }
+#endif
+
+int qft_launch_filter(qft_plan p, int backward, const float* x, const void* W, const float* gy, float* out,
+                      void* gW, cudaStream_t st) {
+  if (backward) return qft_launch_filter_bwd(p, x, W, gy, out, gW, st);
+  const FiltArgs a = filt_args(p, x, W, gy, out);
   const int smem = qft_filter_smem(a.N, p->host_plan.LF, backward);
-  if (!backward) {
+  {
     cudaError_t e = cudaFuncSetAttribute(k_filter_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return qft_set_cuda(p, e);
     int per_sm = 1;
@@ -168,13 +201,5 @@ int qft_launch_filter(qft_plan p, int backward, const float* x, const void* W, c
     k_filter_fwd<<<(unsigned)grid, kFiltNT, smem, st>>>(a);
     return qft_set_cuda(p, cudaGetLastError());
   }
-  cudaError_t e = cudaFuncSetAttribute(k_filter_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return qft_set_cuda(p, e);
-  k_filter_bwd<<<(unsigned)(a.C * kFiltParts), kFiltNT, smem, st>>>(a);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return qft_set_cuda(p, e);
-  const int H = a.N / 2 + 1;
-  const int64_t n = (int64_t)a.C * H;
-  k_filter_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.gwpart, static_cast<qc*>(gW), a.C, H);
-  return qft_set_cuda(p, cudaGetLastError());
 }
+#endif  // QFT_FILTER_BACKWARD_TU

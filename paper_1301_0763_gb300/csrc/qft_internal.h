@@ -65,7 +65,8 @@ struct qft_plan_s {
   QftLargePlan* large_host;
   QftLargePlan* d_large;
   qc_storage* scratch;
-  int64_t scratch_rows;
+  int64_t scratch_rows;       // rows the scratch copies hold
+  int64_t chunk_rows;         // rows per launch sequence (0: scratch_rows); fewer keep a chunk's copies in L2
   int side_len;
   // ragged plans (qft_plan_create_ragged)
   int nclasses;

@@ -8,11 +8,6 @@
 #pragma once
 #include "qft_rows.cuh"
 
-namespace {
-
-constexpr int kLargeNT = 256;   // threads of the GLOBAL / SLICE kernels
-constexpr int kLargeTPT = 4;    // tasks per thread per CTA in those kernels
-
 struct LargeArgs {
   const QftLargePlan* plan;   // device copy of the plan
   const float* gsec;          // Gray-ordered secants, N/4 + 1 entries
@@ -22,6 +17,18 @@ struct LargeArgs {
   int side_len;               // padded cells per side
   int r;
 };
+
+// The NODE and SLICE kernels do not depend on the IO of the transform; they
+// are compiled once (qft_k_node.cu) and launched through these helpers, which
+// return the CUDA error of the launch.
+cudaError_t qft_large_node_prepare(int nt, size_t smem);
+cudaError_t qft_large_node_launch(const LargeArgs& a, dim3 grid, int nt, size_t smem, cudaStream_t st);
+cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st);
+
+namespace {
+
+constexpr int kLargeNT = 256;   // threads of the GLOBAL / SLICE kernels
+constexpr int kLargeTPT = 4;    // tasks per thread per CTA in those kernels
 
 __device__ __forceinline__ Eng large_eng(const LargeArgs& a, int copy, int64_t row) {
   Eng e;
@@ -59,6 +66,12 @@ __global__ void __launch_bounds__(kLargeNT, 2) k_large_global(LargeArgs a, int p
   }
 }
 
+__host__ __device__ inline size_t node_smem_bytes(int NB) {
+  return qft_lib::align16(sizeof(QftRowPlan)) + qft_lib::align16(sizeof(float) * (((size_t)1 << NB) + 1)) +
+         qft_lib::align16(8 * (size_t)qft_pidx(1 << NB));
+}
+
+#ifdef QFT_NODE_TU
 // SLICE phase above the node depth: reads copy sg.pad[0], writes copy sg.pad[1].
 __global__ void __launch_bounds__(kLargeNT, 2) k_large_slice(LargeArgs a, int phase) {
   const QftLargePlan* P = a.plan;
@@ -80,10 +93,6 @@ __global__ void __launch_bounds__(kLargeNT, 2) k_large_slice(LargeArgs a, int ph
   }
 }
 
-__host__ __device__ inline size_t node_smem_bytes(int NB) {
-  return qft_lib::align16(sizeof(QftRowPlan)) + qft_lib::align16(sizeof(float) * (((size_t)1 << NB) + 1)) +
-         qft_lib::align16(8 * (size_t)qft_pidx(1 << NB));
-}
 
 // NODE phase: blockIdx.x = node group (over all subs), blockIdx.y = row.  The
 // group's cells [base, base + group * 2^nb) of one side (copy A) are loaded
@@ -137,6 +146,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a) {
   qc* dstp = side_ptr(ed, S.side) + pb;
   for (int i = threadIdx.x; i < pn; i += NT) dstp[i] = cells[i];
 }
+#endif  // QFT_NODE_TU
 
 // One execute on the large-row path: every phase of the plan, in order, for
 // `items` rows (or real row pairs) starting at row0, in chunks that fit the
@@ -153,28 +163,26 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
   a.r = p->r;
   const size_t node_smem = node_smem_bytes(H.NB);
   // node kernel: 512 threads (one CTA per SM) unless the plan asks for 256
-  const bool n256 = p->node_nt == 256;
-  const int node_nt = n256 ? 256 : 512;
-  cudaError_t e = n256 ? cudaFuncSetAttribute(k_large_node<qft_lib::kL1, 256>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)node_smem)
-                       : cudaFuncSetAttribute(k_large_node<qft_lib::kL1, 512>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)node_smem);
+  const int node_nt = p->node_nt == 256 ? 256 : 512;
+  cudaError_t e = qft_large_node_prepare(node_nt, node_smem);
   if (e != cudaSuccess) return qft_set_cuda(p, e);
-  for (int64_t r0 = 0; r0 < items; r0 += p->scratch_rows) {
-    const int64_t rows = items - r0 < p->scratch_rows ? items - r0 : p->scratch_rows;
+  const int64_t chunk = p->chunk_rows > 0 && p->chunk_rows < p->scratch_rows ? p->chunk_rows : p->scratch_rows;
+  for (int64_t r0 = 0; r0 < items; r0 += chunk) {
+    const int64_t rows = items - r0 < chunk ? items - r0 : chunk;
     a.row0 = r0;
     for (int ph = 0; ph < H.nphase; ++ph) {
       const QftLargePhase& P = H.phases[ph];
       if (P.kind == QFT_LPH_NODE) {
         const dim3 grid((unsigned)H.node_ctas, (unsigned)rows);
         qft_time_begin(p, st, QFT_KERNEL_NODE);
-        if (n256) k_large_node<qft_lib::kL1, 256><<<grid, 256, node_smem, st>>>(a);
-        else k_large_node<qft_lib::kL1, 512><<<grid, node_nt, node_smem, st>>>(a);
+        e = qft_large_node_launch(a, grid, node_nt, node_smem, st);
+        if (e != cudaSuccess) return qft_set_cuda(p, e);
       } else {
         const unsigned bx = (unsigned)((P.ntasks + kLargeNT * kLargeTPT - 1) / (kLargeNT * kLargeTPT));
         if (P.kind == QFT_LPH_SLICE) {
           qft_time_begin(p, st, QFT_KERNEL_SLICE);
-          k_large_slice<<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph);
+          e = qft_large_slice_launch(a, ph, dim3(bx, (unsigned)rows), st);
+          if (e != cudaSuccess) return qft_set_cuda(p, e);
         } else {
           qft_time_begin(p, st, QFT_KERNEL_GLOBAL);
           k_large_global<FAC, qft_lib::kL1><<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph, fac);

@@ -52,9 +52,10 @@ struct QftRowPlan {
   int32_t in_last_phase;    // last phase whose tasks read the input row (F1 tasks)
   int32_t phase_ntasks[QFT_MAX_PHASES];
   int32_t phase_seg0[QFT_MAX_PHASES + 1];
-  int32_t phase_is_slice[QFT_MAX_PHASES];
+  int32_t phase_is_slice[QFT_MAX_PHASES];   // 0 plain, 1 SLICE, 2 C/S tables
   QftSeg segs[QFT_MAX_SEGS];
 };
+
 
 // ---------------------------------------------------------------------------
 // Rows too long for one CTA's shared memory (N > 2^14) are transformed by a

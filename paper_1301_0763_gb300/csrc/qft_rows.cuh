@@ -154,6 +154,12 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: a bulk copy never takes that long
 
+// Bulk prefetch of a global range into L2 (no shared memory, no completion to
+// wait for); used for the next row when it cannot be staged in shared memory.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 struct NoHook {
   __device__ __forceinline__ void operator()() const {}
 };
@@ -169,32 +175,29 @@ __device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e
   const int tid = threadIdx.x;
   for (int p = 0; p < P.nphase; ++p) {
     const int nt = P.phase_ntasks[p];
-    if (P.phase_is_slice[p] == 2) {          // C_Mt / S_Mt tables: warp 0 and warp 1
-      const int warp = tid >> 5, lane = tid & 31;
-      const int mt = P.r - P.LF;
-      if (warp == 0) {
-        for (int m = 1; m <= mt; ++m) { tab_level_c(e, m, lane, 32); __syncwarp(); }
-      } else if (warp == 1) {
-        for (int m = 2; m <= mt; ++m) { tab_level_s(e, m, lane, 32); __syncwarp(); }
-      } else {
-        // the phase's own tasks (special FINAL tasks, which read no table)
-        int sgi = P.phase_seg0[p];
-        const int sge = P.phase_seg0[p + 1];
-        for (int tau = tid - 64; tau < nt; tau += NT - 64) {
-          while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
-          const QftSeg& sg = P.segs[sgi];
-          run_plain_task<L1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin);
-        }
-      }
-      __syncthreads();
-      continue;
-    }
+    const int kind = P.phase_is_slice[p];
     // tasks are visited in increasing order, so the segment is found by
     // advancing from the previous one (amortised O(1) per task)
     int sgi = P.phase_seg0[p];
     const int sge = P.phase_seg0[p + 1];
-    if (!P.phase_is_slice[p]) {
-      for (int tau = tid; tau < nt; tau += NT) {
+    if (kind != 1) {
+      // plain tasks (kind 0) and the phase's own tasks of the table phase (kind
+      // 2: warps 0 and 1 build the C_Mt / S_Mt tables, the other warps run the
+      // special FINAL tasks, which read no table).  One task loop: the task
+      // code is inlined once per kernel.
+      int t0 = tid, stride = NT;
+      if (kind == 2) {
+        const int warp = tid >> 5, lane = tid & 31;
+        const int mt = P.r - P.LF;
+        if (warp == 0) {
+          for (int m = 1; m <= mt; ++m) { tab_level_c(e, m, lane, 32); __syncwarp(); }
+        } else if (warp == 1) {
+          for (int m = 2; m <= mt; ++m) { tab_level_s(e, m, lane, 32); __syncwarp(); }
+        }
+        t0 = tid < 64 ? nt : tid - 64;
+        stride = NT - 64;
+      }
+      for (int tau = t0; tau < nt; tau += stride) {
         while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
         const QftSeg& sg = P.segs[sgi];
         run_plain_task<L1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin);
@@ -287,6 +290,17 @@ k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int
         }
       });
     } else {
+      if constexpr (FAC::kCanStage) {
+        // the next row of this CTA goes to L2 while this one is transformed
+        const int64_t next = item + gridDim.x;
+        if (threadIdx.x == 0 && next < nitems) {
+          const void* src[2];
+          uint32_t bytes[2];
+          const int np = fac.stage_src(next, src, bytes);
+          for (int k = 0; k < np; ++k)
+            if (((uintptr_t)src[k] & 15) == 0 && (bytes[k] & 15) == 0) prefetch_l2(src[k], bytes[k]);
+        }
+      }
       const auto io = fac.make(item);
       run_row_phases<L1, NT>(P, e, io, 0);
     }

@@ -27,6 +27,7 @@ KIND_C2C, KIND_R2C = 0, 1
 DTYPE_F32, DTYPE_F16, DTYPE_BF16 = 0, 1, 2
 OP_FORWARD, OP_INVERSE, OP_FORWARD_ADJOINT, OP_INVERSE_ADJOINT = 0, 1, 2, 3
 PLAN_AUTOTUNE = 1
+SCHEDULE_KEYS = ("threads", "L1", "LS", "LL", "LB", "LF", "staging", "node_log2", "node_threads", "chunk_rows")
 
 _lib = None
 _lock = threading.Lock()
@@ -68,6 +69,7 @@ def load_library(path: str | None = None):
         lib.qft_filter_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.qft_execute_static_scratch.argtypes = [i64, i64, ci, vp, vp, vp]
         lib.qft_plan_schedule.argtypes = [vp, ctypes.POINTER(ci)]
+        lib.qft_plan_set_schedule.argtypes = [vp, ctypes.POINTER(ci)]
         lib.qft_plan_time_launches.argtypes = [vp, ci]
         lib.qft_plan_launch_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ci)]
         lib.qft_status_string.argtypes = [ci]
@@ -117,10 +119,16 @@ class Plan:
 
     def schedule(self) -> dict:
         """The plan's schedule (see qft_plan_schedule)."""
-        v = (ctypes.c_int * 9)()
+        v = (ctypes.c_int * 10)()
         _check(self.lib.qft_plan_schedule(self.handle, v), "qft_plan_schedule")
-        keys = ("threads", "L1", "LS", "LL", "LB", "LF", "staging", "node_log2", "node_threads")
-        return dict(zip(keys, list(v)))
+        return dict(zip(SCHEDULE_KEYS, list(v)))
+
+    def set_schedule(self, **kw):
+        """Change some schedule values (keys of schedule()); the result is unchanged."""
+        cur = self.schedule()
+        cur.update(kw)
+        v = (ctypes.c_int * 10)(*[int(cur[k]) for k in SCHEDULE_KEYS])
+        _check(self.lib.qft_plan_set_schedule(self.handle, v), "qft_plan_set_schedule")
 
     def execute(self, op: int, inp: torch.Tensor, out: torch.Tensor, stream=None):
         with torch.cuda.device(self.device):
