@@ -368,8 +368,9 @@ def roofline(kt, peak, peak_src):
 
 def run_e2e(args, logs, dev, stream, torch, qft, tune):
     """Same metric through the public API with host buffers: every step copies
-    each size's input (2 GiB) from pinned host memory, transforms it with
-    qft.fft, and copies the spectrum back."""
+    each size's input (2 GiB) from pinned host memory, transforms it and copies
+    the spectrum back (qft.fft_host: chunks, copies overlapped with the
+    transforms)."""
     qft.set_autotune(tune)
     host_in = torch.randn(ELEMS, dtype=torch.complex64).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -378,10 +379,7 @@ def run_e2e(args, logs, dev, stream, torch, qft, tune):
     def one():
         for lg in logs:
             N = 1 << lg
-            d = host_in.view(ELEMS // N, N).to(dev, non_blocking=True)
-            X = qft.fft(d)
-            host_out.view(ELEMS // N, N).copy_(X, non_blocking=True)
-            del d, X
+            qft.fft_host(host_in.view(ELEMS // N, N), host_out.view(ELEMS // N, N))
     one()
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -397,7 +395,8 @@ def run_e2e(args, logs, dev, stream, torch, qft, tune):
     return {"value": round(nbytes / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": 8 * ELEMS * len(logs), "d2h_bytes_per_step": 8 * ELEMS * len(logs),
             "ms_per_step": round(ms, 3),
-            "workload": "the same sizes and batches, qft.fft() on pinned host data, copies included"}
+            "workload": "the same sizes and batches, qft.fft_host() on pinned host data (chunked; copies "
+                        "in and out overlap the transforms on three streams), copies included"}
 
 
 def _time(fn, torch, stream, reps=3, warm=2):
@@ -472,6 +471,19 @@ def run_extras(args, dev, stream, torch, qft, orc, tune, peak):
         pr.destroy()
     ex["inverse_gbs"] = inv
     ex["real_forward_gbs"] = real
+    # standalone DCT-0 / DST-0 (eqs qft_0B, qft_0C): 2^28 reals in and out per size
+    r2r = {}
+    for lg in (12, 16, 20):
+        N = 1 << lg
+        for name, kind, L in (("dct0", qft.KIND_DCT0, N // 2 + 1), ("dst0", qft.KIND_DST0, N // 2 - 1)):
+            rows = (1 << 28) // L
+            xr = zv.view(torch.float32)[: rows * L].view(rows, L)
+            yr = zo.view(-1).view(torch.float32)[: rows * L].view(rows, L)
+            pr = qft.Plan(N, rows, kind=kind, autotune=tune)
+            ms = _time(lambda: pr.execute(qft.OP_FORWARD, xr, yr), torch, stream)
+            r2r[f"{name}_2^{lg}"] = round(8 * rows * L / (ms * 1e-3) / 1e9, 1)
+            pr.destroy()
+    ex["dct0_dst0_gbs"] = r2r
     del z, zo, zv
     torch.cuda.empty_cache()
 

@@ -25,7 +25,7 @@
  *   - Execution is asynchronous and ordered on the CUDA stream passed as
  *     `stream` (a cudaStream_t; NULL means the legacy default stream).  No
  *     call synchronises the host except qft_plan_sync_status.
- *   - C2C transforms may run in place (in == out); R2C may not.
+ *   - C2C, DCT-0 and DST-0 transforms may run in place (in == out); R2C may not.
  *   - Every call returns QFT_OK (0) or a negative QFT_ERR_* code and never
  *     throws.  CUDA errors are reported as QFT_ERR_CUDA; the CUDA error code is
  *     kept in the plan (qft_plan_last_cuda_error).
@@ -47,6 +47,10 @@ typedef struct qft_plan_s* qft_plan;
 #define QFT_KIND_C2C 0 /* complex -> complex, length N */
 #define QFT_KIND_R2C 1 /* forward: real N -> complex N/2+1 (Hermitian-pruned, rdft of Sec. 4.2);
                           inverse: complex N/2+1 -> real N (1/N scaled)                      */
+#define QFT_KIND_DCT0 2 /* DCT-0 of periodization N (eq qft_0B, the dct recursion of Sec. 5):
+                           real c(n), n in [0, N/2] -> C(k) = sum_n c(n) cos(2 pi n k/N), k in [0, N/2] */
+#define QFT_KIND_DST0 3 /* DST-0 of periodization N (eq qft_0C, the dst recursion of Sec. 5):
+                           real d(n), n in [1, N/2-1] -> S(k) = sum_n d(n) sin(2 pi n k/N), k in [1, N/2-1] */
 
 /* storage dtypes */
 #define QFT_DTYPE_F32 0  /* complex64 (C2C) / float32 real + complex64 spectrum (R2C) */
@@ -79,8 +83,8 @@ typedef struct qft_plan_s* qft_plan;
  * qft_plan_create -- plan `batch` transforms of length n (eq qft_0A with N = n).
  *   out    receives the plan handle (owned by the caller, release with
  *          qft_plan_destroy).
- *   n      transform length, a power of two, 2 <= n <= 2^24 (C2C) or
- *          4 <= n <= 2^24 (R2C).
+ *   n      transform length (periodization for DCT-0 / DST-0), a power of two,
+ *          2 <= n <= 2^24 (C2C) or 4 <= n <= 2^24 (the real kinds).
  *   batch  number of rows (>= 0; 0 makes every execute a no-op).
  *   kind   QFT_KIND_C2C or QFT_KIND_R2C; dtype QFT_DTYPE_*.
  *   flags  0 or QFT_PLAN_AUTOTUNE.  With QFT_PLAN_AUTOTUNE the plan times the
@@ -127,6 +131,10 @@ int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host, const int
  *                     imaginary parts at k = 0, N/2 set to zero)
  * For QFT_KIND_C2C every op maps [batch][N] complex to [batch][N] complex:
  *   FORWARD = F, INVERSE = F^-1, FORWARD_ADJOINT = F^H, INVERSE_ADJOINT = F / N.
+ * For QFT_KIND_DCT0 (rows of N/2+1 floats) and QFT_KIND_DST0 (rows of N/2-1
+ * floats, d(1..N/2-1) -> S(1..N/2-1)): FORWARD, or FORWARD_ADJOINT, which is
+ * the same map (both matrices are symmetric); other ops return
+ * QFT_ERR_INVALID_ARG.  FP32 only, 4-byte aligned, in place allowed.
  */
 int qft_execute(qft_plan plan, int op, const void* in, void* out, void* stream);
 

@@ -174,20 +174,30 @@ def irdft_adjoint(g, threads: int = 0, fp32: bool = False) -> np.ndarray:
     return Y
 
 
-def dct0(c) -> np.ndarray:
+def dct0(c, fp32: bool = False) -> np.ndarray:
+    """DCT-0 of periodization N = 2 (len - 1) of each row of c [..., N/2+1]
+    (eq qft_0B, the dct recursion of Sec. 5); fp32=True evaluates it in FP32."""
     c = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
     N = 2 * (c.shape[-1] - 1)
     out = np.empty_like(c)
-    _check(_load().oracle_dct0(N, _dp(c), _dp(out)))
+    lib = _load32() if fp32 else _load()
+    rows_in, rows_out = c.reshape(-1, N // 2 + 1), out.reshape(-1, N // 2 + 1)
+    for i in range(rows_in.shape[0]):
+        _check(lib.oracle_dct0(N, _dp(rows_in[i]), _dp(rows_out[i])))
     return out
 
 
-def dst0(d, N: int) -> np.ndarray:
-    """DST-0 of periodization N; d indexed by n in [0, N/2] (ends ignored)."""
+def dst0(d, N: int, fp32: bool = False) -> np.ndarray:
+    """DST-0 of periodization N (eq qft_0C, the dst recursion of Sec. 5) of each
+    row of d [..., N/2+1] indexed by n (the ends n = 0, N/2 are ignored; the
+    output is 0 there); fp32=True evaluates it in FP32."""
     d = np.ascontiguousarray(np.asarray(d, dtype=np.float64))
     assert d.shape[-1] == N // 2 + 1
     out = np.empty_like(d)
-    _check(_load().oracle_dst0(N, _dp(d), _dp(out)))
+    lib = _load32() if fp32 else _load()
+    rows_in, rows_out = d.reshape(-1, N // 2 + 1), out.reshape(-1, N // 2 + 1)
+    for i in range(rows_in.shape[0]):
+        _check(lib.oracle_dst0(N, _dp(rows_in[i]), _dp(rows_out[i])))
     return out
 
 

@@ -137,7 +137,7 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
       p->large_host = (QftLargePlan*)malloc(sizeof(QftLargePlan));
       if (!p->large_host) { free_resources(p); return QFT_ERR_CUDA; }
       p->side_len = qft_side_len((int)N);
-      const int64_t items = kind == QFT_KIND_R2C ? (batch + 1) / 2 : batch;
+      const int64_t items = kind == QFT_KIND_C2C ? batch : (batch + 1) / 2;   // real kinds: row pairs
       const int64_t per_row = 2 * 2 * (int64_t)p->side_len * 8;
       int64_t rows = qft_lib::kScratchBudget / per_row;
       if (rows > items) rows = items;
@@ -157,6 +157,7 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
 // The kernels of one execute of a single-size plan (arguments already checked).
 static int launch_plain(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
   if (p->kind == QFT_KIND_R2C) return qft_launch_real(p, op, in, out, st);
+  if (p->kind == QFT_KIND_DCT0 || p->kind == QFT_KIND_DST0) return qft_launch_r2r(p, in, out, st);
   switch (p->dtype) {
   case QFT_DTYPE_F32: return qft_launch_c2c_f32(p, op, in, out, st);
   case QFT_DTYPE_F16: return qft_launch_c2c_f16(p, op, in, out, st);
@@ -240,9 +241,10 @@ static float tune_time(qft_plan p, const void* din, void* dout, int64_t rows, cu
 static int autotune(qft_plan p) {
   if (p->r < 3 || p->batch == 0) return QFT_OK;
   const int64_t N = p->n;
-  const int64_t items = p->kind == QFT_KIND_R2C ? (p->batch + 1) / 2 : p->batch;
+  const int64_t items = p->kind == QFT_KIND_C2C ? p->batch : (p->batch + 1) / 2;
   const int64_t row_bytes = p->kind == QFT_KIND_R2C ? 4 * N + 8 * (N / 2 + 1)
-                                                    : (p->dtype == QFT_DTYPE_F32 ? 16 : 8) * N;
+                            : p->kind == QFT_KIND_C2C ? (p->dtype == QFT_DTYPE_F32 ? 16 : 8) * N
+                                                      : 4 * N;   // DCT-0 / DST-0: N/2 reals in and out
   int64_t cap = ((int64_t)256 << 20) / row_bytes;
   if (cap < 1) cap = 1;
   const int64_t rows = p->batch < cap ? p->batch : cap;
@@ -326,11 +328,12 @@ extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind
   if (!out) return QFT_ERR_NULLPTR;
   *out = nullptr;
   if ((flags & ~QFT_PLAN_AUTOTUNE) != 0) return QFT_ERR_INVALID_ARG;
-  if (kind != QFT_KIND_C2C && kind != QFT_KIND_R2C) return QFT_ERR_DTYPE;
+  if (kind != QFT_KIND_C2C && kind != QFT_KIND_R2C && kind != QFT_KIND_DCT0 && kind != QFT_KIND_DST0)
+    return QFT_ERR_DTYPE;
   if (dtype != QFT_DTYPE_F32 && dtype != QFT_DTYPE_F16 && dtype != QFT_DTYPE_BF16) return QFT_ERR_DTYPE;
-  if (kind == QFT_KIND_R2C && dtype != QFT_DTYPE_F32) return QFT_ERR_DTYPE;
+  if (kind != QFT_KIND_C2C && dtype != QFT_DTYPE_F32) return QFT_ERR_DTYPE;
   if (n < 2 || (n & (n - 1)) != 0) return QFT_ERR_INVALID_N;
-  if (kind == QFT_KIND_R2C && n < 4) return QFT_ERR_INVALID_N;
+  if (kind != QFT_KIND_C2C && n < 4) return QFT_ERR_INVALID_N;
   int r = 0;
   while ((int64_t(1) << r) < n) ++r;
   if (r > qft_lib::kMaxLog2) return QFT_ERR_INVALID_N;
@@ -482,7 +485,7 @@ static int exec_ragged(qft_plan p, int op, const void* in, void* out, cudaStream
 }
 
 // ---------------------------------------------------------- spectral filter
-static const int kKindFilter = 2;   // internal kind of filter plans
+static const int kKindFilter = 100;   // internal kind of filter plans (not a QFT_KIND_*)
 
 extern "C" int qft_filter_create(qft_plan* out, int64_t n, int64_t batch, int64_t channels, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
@@ -563,6 +566,10 @@ extern "C" int qft_execute(qft_plan p, int op, const void* in, void* out, void* 
   const size_t al_c = p->dtype == QFT_DTYPE_F32 ? 8 : 4;
   if (p->kind == QFT_KIND_C2C) {
     if (((uintptr_t)in % al_c) || ((uintptr_t)out % al_c)) return QFT_ERR_ALIGN;
+  } else if (p->kind == QFT_KIND_DCT0 || p->kind == QFT_KIND_DST0) {
+    // symmetric matrices: the adjoint is the transform itself; no inverse op
+    if (op != QFT_OP_FORWARD && op != QFT_OP_FORWARD_ADJOINT) return QFT_ERR_INVALID_ARG;
+    if (((uintptr_t)in % 4) || ((uintptr_t)out % 4)) return QFT_ERR_ALIGN;
   } else {
     const bool real_in = (op == QFT_OP_FORWARD || op == QFT_OP_INVERSE_ADJOINT);
     if (((uintptr_t)in % (real_in ? 4 : 8)) || ((uintptr_t)out % (real_in ? 8 : 4))) return QFT_ERR_ALIGN;
@@ -619,7 +626,7 @@ extern "C" int qft_plan_info(qft_plan p, int* threads, int* ctas, int* smem_byte
   if (rc != QFT_OK) return rc;
   if (threads) *threads = p->threads;
   // large-row plans: the NODE launch's CTAs and every launch of every scratch chunk
-  const int64_t items = p->kind == QFT_KIND_R2C ? (p->batch + 1) / 2 : p->batch;
+  const int64_t items = p->kind == QFT_KIND_C2C ? p->batch : (p->batch + 1) / 2;
   const int64_t crow = p->chunk_rows > 0 && p->chunk_rows < p->scratch_rows ? p->chunk_rows : p->scratch_rows;
   const int64_t chunks = crow > 0 ? (items + crow - 1) / crow : 0;
   if (ctas) *ctas = p->large_host ? (int)(p->large_host->node_ctas * (crow < items ? crow : items))

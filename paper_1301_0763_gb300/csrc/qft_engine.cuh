@@ -117,6 +117,9 @@ QFT_HD float fsub(float a, float b) { return a - b; }
 
 // ------------------------------------------------------------ geometry
 QFT_HD int qft_pidx(int i) { return i + (i >> 4); }
+// Padded index of cell base + t*2^h (h >= 4, base's low 4 bits below 2^h):
+// pidx(base) + t * qft_pstride(h), one add per access instead of a shift and two adds.
+QFT_HD int qft_pstride(int h) { return (1 << h) + (1 << (h - 4)); }
 QFT_HD int qft_side_len(int N) { return qft_pidx(N / 2) + 1; }   // padded cells per side
 QFT_HD int cls_off(int r, int j) { return (1 << (r - 1)) - (1 << (r - 1 - j)); }
 QFT_HD int cls_bits(int r, int j) { return r - 2 - j; }
@@ -231,10 +234,19 @@ QFT_HD void task_f1_big(const Eng& e, const IO& io, int j, int ilo) {
   dif_regs<L1, 0>(vc, b, lo, e.sec);
   dif_regs<L1, 1>(vs, b, lo, e.sec);
   const int off = cls_off(e.r, j);
+  if (h >= 4) {   // off is a multiple of 16 here
+    const int p0 = qft_pidx(off + lo), ps = qft_pstride(h);
 #pragma unroll
-  for (int t = 0; t < (1 << L1); ++t) {
-    e.side0[qft_pidx(off + t * H + lo)] = vc[t];
-    e.side1[qft_pidx(off + t * H + lo)] = vs[t];
+    for (int t = 0; t < (1 << L1); ++t) {
+      e.side0[p0 + t * ps] = vc[t];
+      e.side1[p0 + t * ps] = vs[t];
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < (1 << L1); ++t) {
+      e.side0[qft_pidx(off + t * H + lo)] = vc[t];
+      e.side1[qft_pidx(off + t * H + lo)] = vs[t];
+    }
   }
 }
 
@@ -246,16 +258,17 @@ QFT_RARE void task_f1_small(const Eng& e, const IO& io, int j) {
   qc vc[1 << L], vs[1 << L];
 #pragma unroll
   for (int g = 0; g < (1 << L); ++g) io.get_cd((2 * ig_c(g) + 1) << j, vc[g], vs[g]);
-  const int off = cls_off(e.r, j);
+  // off is a multiple of 2^(L+1): the 2^L <= 16 cells lie in one padded block
+  const int p0 = qft_pidx(cls_off(e.r, j));
   dif_regs<L, 0>(vc, L, 0, e.sec);
   bwd_chunk<L, 0>(vc, vc, false);
 #pragma unroll
-  for (int k = 0; k < (1 << L); ++k) e.side0[qft_pidx(off + k)] = vc[k];
+  for (int k = 0; k < (1 << L); ++k) e.side0[p0 + k] = vc[k];
   if (j <= e.r - 3) {
     dif_regs<L, 1>(vs, L, 0, e.sec);
     bwd_chunk<L, 1>(vs, vs, false);
 #pragma unroll
-    for (int k = 0; k < (1 << L); ++k) e.side1[qft_pidx(off + k)] = vs[k];
+    for (int k = 0; k < (1 << L); ++k) e.side1[p0 + k] = vs[k];
   } else {
     e.side1[qft_pidx(e.N / 2 - 2)] = vs[0];
   }
@@ -277,24 +290,38 @@ QFT_HD void task_dif(const Eng& e, int j, int D, int tau) {
   qc* A = side_ptr(e, SIDE);
   const int base = cls_off(e.r, j) + (q << nb) + lo;
   qc v[1 << L];
+  const bool lin = h >= 4;   // then base - lo is a multiple of 16
+  const int p0 = qft_pidx(base), ps = lin ? qft_pstride(h) : 0;
+  if (lin) {
 #pragma unroll
-  for (int t = 0; t < (1 << L); ++t) v[t] = A[qft_pidx(base + (t << h))];
+    for (int t = 0; t < (1 << L); ++t) v[t] = A[p0 + t * ps];
+  } else {
+#pragma unroll
+    for (int t = 0; t < (1 << L); ++t) v[t] = A[qft_pidx(base + (t << h))];
+  }
   dif_regs<L, SIDE>(v, nb, lo, e.sec);
+  if (lin) {
 #pragma unroll
-  for (int t = 0; t < (1 << L); ++t) A[qft_pidx(base + (t << h))] = v[t];
+    for (int t = 0; t < (1 << L); ++t) A[p0 + t * ps] = v[t];
+  } else {
+#pragma unroll
+    for (int t = 0; t < (1 << L); ++t) A[qft_pidx(base + (t << h))] = v[t];
+  }
 }
 
 template <int L, int SIDE>
 QFT_HD void task_leaf(const Eng& e, int j, int q) {
   qc* A = side_ptr(e, SIDE);
   const int base = cls_off(e.r, j) + (q << L);
+  // base is a multiple of 2^L <= 16: the node's cells lie in one padded block
+  const int p0 = qft_pidx(base);
   qc v[1 << L];
 #pragma unroll
-  for (int t = 0; t < (1 << L); ++t) v[t] = A[qft_pidx(base + t)];
+  for (int t = 0; t < (1 << L); ++t) v[t] = A[p0 + t];
   dif_regs<L, SIDE>(v, L, 0, e.sec);
   bwd_chunk<L, SIDE>(v, v, false);
 #pragma unroll
-  for (int t = 0; t < (1 << L); ++t) A[qft_pidx(base + t)] = v[t];
+  for (int t = 0; t < (1 << L); ++t) A[p0 + t] = v[t];
 }
 
 // --------------------------------------------------------------- SLICE
@@ -324,13 +351,25 @@ QFT_HD void task_slice_read(const Eng& e, int j, int D, int tau, SliceRegs& s) {
   const int rr = tau & (S - 1);
   const qc* A = side_ptr(e, SIDE);
   const int nbase = cls_off(e.r, j) + (q << nb);
-#pragma unroll
-  for (int t = 0; t < (1 << L); ++t) s.w[t] = A[qft_pidx(nbase + t * S + rr)];
   const bool hv = SIDE == 0 ? (rr + 1 < S) : (rr >= 1);
   const int hoff = SIDE == 0 ? rr + 1 : rr - 1;
-  if (hv) {
+  if (sb >= 4) {   // nbase is a multiple of 16 here
+    const int ps = qft_pstride(sb);
+    const int pw = qft_pidx(nbase + rr);
 #pragma unroll
-    for (int t = 1; t < (1 << L); ++t) s.h[t] = A[qft_pidx(nbase + t * S + hoff)];
+    for (int t = 0; t < (1 << L); ++t) s.w[t] = A[pw + t * ps];
+    if (hv) {
+      const int ph = qft_pidx(nbase + hoff);
+#pragma unroll
+      for (int t = 1; t < (1 << L); ++t) s.h[t] = A[ph + t * ps];
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < (1 << L); ++t) s.w[t] = A[qft_pidx(nbase + t * S + rr)];
+    if (hv) {
+#pragma unroll
+      for (int t = 1; t < (1 << L); ++t) s.h[t] = A[qft_pidx(nbase + t * S + hoff)];
+    }
   }
   s.hv = hv;
   s.base = nbase + (rr << L);
@@ -343,8 +382,9 @@ QFT_HD void task_slice_write(const Eng& e, SliceRegs& s) {
   for (int t = 0; t < (1 << L); ++t) w[t] = s.w[t];
   bwd_chunk<L, SIDE>(w, s.h, s.hv);
   qc* A = side_ptr(e, SIDE);
+  const int p0 = qft_pidx(s.base);   // s.base is a multiple of 2^L <= 16
 #pragma unroll
-  for (int t = 0; t < (1 << L); ++t) A[qft_pidx(s.base + t)] = w[t];
+  for (int t = 0; t < (1 << L); ++t) A[p0 + t] = w[t];
 }
 
 // --------------------------------------------------------------- FINAL

@@ -132,6 +132,7 @@ int qft_launch_c2c_f32(qft_plan p, int op, const void* in, void* out, cudaStream
 int qft_launch_c2c_f16(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
 int qft_launch_c2c_bf16(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
 int qft_launch_real(qft_plan p, int op, const void* in, void* out, cudaStream_t st);
+int qft_launch_r2r(qft_plan p, const void* in, void* out, cudaStream_t st);
 int qft_launch_filter(qft_plan p, int backward, const float* x, const void* W, const float* gy, float* out,
                       void* gW, cudaStream_t st);
 int qft_filter_smem(int N, int LF, int backward);

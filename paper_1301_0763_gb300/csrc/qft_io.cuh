@@ -131,6 +131,40 @@ struct IoC2C {
   }
 };
 
+// ---------------------------------------------------------- DCT-0 / DST-0
+// The standalone real transforms of periodization N (eqs qft_0B, qft_0C) on
+// two real rows (a in lane x, b in lane y; b may be absent):
+//   DCT-0: c(n), n in [0, N/2]   -> C(k) = sum_n c(n) cos(2 pi n k / N), k in [0, N/2];
+//   DST-0: d(n), n in [1, N/2-1] -> S(k) = sum_n d(n) sin(2 pi n k / N), k in [1, N/2-1],
+//          stored at n-1 and k-1.
+// The input feeds one side of the network directly (no fold); the other side
+// carries zeros.
+template <bool DST>
+struct IoR2R {
+  const float* ina;
+  const float* inb;
+  float* outa;
+  float* outb;
+  int N;
+  QFT_HD qc ld(int i) const { return mkc(ina[i], inb ? inb[i] : 0.f); }
+  QFT_HD void get_cd(int n, qc& c, qc& d) const {
+    const qc z = mkc(0.f, 0.f);
+    if (DST) { c = z; d = ld(n - 1); }
+    else { c = ld(n); d = z; }
+  }
+  QFT_HD qc get_c(int n) const { return DST ? mkc(0.f, 0.f) : ld(n); }
+  QFT_HD void emit(int k, qc C, qc S) const {
+    if (DST) {
+      if (k < 1 || 2 * k >= N) return;
+      outa[k - 1] = S.x;
+      if (outb) outb[k - 1] = S.y;
+    } else {
+      outa[k] = C.x;
+      if (outb) outb[k] = C.y;
+    }
+  }
+};
+
 // ---------------------------------------------------------------- R2C
 // Two real rows (a in lane x, b in lane y).  b may be absent (odd batch).
 // Output row: N/2+1 complex.  Optional per-bin weight w_k * scale (used by

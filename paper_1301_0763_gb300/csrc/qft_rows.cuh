@@ -119,6 +119,30 @@ struct FacC2R {
   __device__ IoC2R<ST> make_staged(int64_t item, const void*) const { return make(item); }
 };
 
+// DCT-0 / DST-0 of periodization N: item i = real rows 2i and 2i+1 of
+// length N/2+1 (DCT) or N/2-1 (DST).
+template <bool DST>
+struct FacR2R {
+  const float* in;
+  float* out;
+  int64_t rows;
+  int N;
+  __device__ __forceinline__ IoR2R<DST> make(int64_t item) const {
+    IoR2R<DST> io;
+    const int64_t L = DST ? N / 2 - 1 : N / 2 + 1;
+    const int64_t a = 2 * item, b = 2 * item + 1;
+    io.ina = in + a * L;
+    io.inb = b < rows ? in + b * L : nullptr;
+    io.outa = out + a * L;
+    io.outb = b < rows ? out + b * L : nullptr;
+    io.N = N;
+    return io;
+  }
+  static constexpr bool kCanStage = false;
+  __device__ int stage_src(int64_t, const void**, uint32_t*) const { return 0; }
+  __device__ IoR2R<DST> make_staged(int64_t item, const void*) const { return make(item); }
+};
+
 // ------------------------------------------------------------ row kernel
 using qft_lib::off_sec;
 using qft_lib::off_side0;

@@ -23,7 +23,7 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_qft_gb300.so")
 
-KIND_C2C, KIND_R2C = 0, 1
+KIND_C2C, KIND_R2C, KIND_DCT0, KIND_DST0 = 0, 1, 2, 3
 DTYPE_F32, DTYPE_F16, DTYPE_BF16 = 0, 1, 2
 OP_FORWARD, OP_INVERSE, OP_FORWARD_ADJOINT, OP_INVERSE_ADJOINT = 0, 1, 2, 3
 PLAN_AUTOTUNE = 1
@@ -372,6 +372,93 @@ class _IRFFT(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         return _real_fwd(g, OP_INVERSE_ADJOINT), None
+
+
+def dct0(c: torch.Tensor) -> torch.Tensor:
+    """DCT-0 of periodization N = 2 (c.shape[-1] - 1) of each row (eq qft_0B):
+    C(k) = sum_{n=0}^{N/2} c(n) cos(2 pi n k / N), k in [0, N/2]."""
+    _need_cuda(c)
+    c = c.contiguous()
+    assert c.dtype == torch.float32
+    N = 2 * (c.shape[-1] - 1)
+    rows = _rows(c, c.shape[-1])
+    out = torch.empty_like(c)
+    get_plan(N, rows, KIND_DCT0, DTYPE_F32, c.device).execute(OP_FORWARD, c, out)
+    return out
+
+
+def dst0(d: torch.Tensor) -> torch.Tensor:
+    """DST-0 of periodization N = 2 (d.shape[-1] + 1) of each row (eq qft_0C):
+    d holds d(1..N/2-1); S(k) = sum_{n=1}^{N/2-1} d(n) sin(2 pi n k / N), k in [1, N/2-1]."""
+    _need_cuda(d)
+    d = d.contiguous()
+    assert d.dtype == torch.float32
+    N = 2 * (d.shape[-1] + 1)
+    rows = _rows(d, d.shape[-1])
+    out = torch.empty_like(d)
+    get_plan(N, rows, KIND_DST0, DTYPE_F32, d.device).execute(OP_FORWARD, d, out)
+    return out
+
+
+_host_streams: dict = {}
+
+
+def fft_host(x: torch.Tensor, out: torch.Tensor | None = None, chunk_bytes: int = 256 << 20,
+             device=None) -> torch.Tensor:
+    """Forward DFT of complex64 rows [..., N] held in pinned host memory, written
+    to pinned host memory (``out``, allocated if None).  The rows move in chunks
+    of about ``chunk_bytes``: the copy of chunk i+1 to the device, the transform
+    of chunk i and the copy of chunk i-1 back run on three streams and overlap.
+    Returns ``out`` once the current stream has been ordered after the last copy
+    (synchronise before reading it on the host)."""
+    if x.is_cuda or not x.is_pinned():
+        raise ValueError("fft_host takes a pinned host tensor")
+    assert x.dtype == torch.complex64
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    N = x.shape[-1]
+    rows = x.numel() // N if N else 0
+    if out is None:
+        out = torch.empty(x.shape, dtype=x.dtype).pin_memory()
+    if rows == 0:
+        return out
+    xv, ov = x.view(rows, N), out.view(rows, N)
+    chunk = max(1, min(rows, chunk_bytes // (8 * N)))
+    key = dev.index
+    if key not in _host_streams:
+        _host_streams[key] = tuple(torch.cuda.Stream(device=dev) for _ in range(3))
+    s_in, s_cmp, s_out = _host_streams[key]
+    nbuf = 3
+    din = [torch.empty(chunk, N, dtype=torch.complex64, device=dev) for _ in range(nbuf)]
+    dout = [torch.empty(chunk, N, dtype=torch.complex64, device=dev) for _ in range(nbuf)]
+    ev_in = [torch.cuda.Event() for _ in range(nbuf)]
+    ev_cmp = [torch.cuda.Event() for _ in range(nbuf)]
+    ev_free = [None] * nbuf
+    cur = torch.cuda.current_stream(dev)
+    for s in (s_in, s_cmp, s_out):
+        s.wait_stream(cur)
+    for i, r0 in enumerate(range(0, rows, chunk)):
+        b = i % nbuf
+        n = min(chunk, rows - r0)
+        with torch.cuda.stream(s_in):
+            if ev_free[b] is not None:
+                s_in.wait_event(ev_free[b])          # buffer b's previous chunk has left the device
+            din[b][:n].copy_(xv[r0:r0 + n], non_blocking=True)
+            ev_in[b].record(s_in)
+        s_cmp.wait_event(ev_in[b])
+        get_plan(N, n, KIND_C2C, DTYPE_F32, dev).execute(OP_FORWARD, din[b][:n], dout[b][:n], s_cmp)
+        ev_cmp[b].record(s_cmp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_cmp[b])
+            ov[r0:r0 + n].copy_(dout[b][:n], non_blocking=True)
+            e = torch.cuda.Event()
+            e.record(s_out)
+            ev_free[b] = e
+    cur.wait_stream(s_out)
+    for t in din + dout:
+        t.record_stream(s_in)
+        t.record_stream(s_cmp)
+        t.record_stream(s_out)
+    return out
 
 
 def fft(x: torch.Tensor) -> torch.Tensor:

@@ -114,3 +114,16 @@ def r2c_large(x, op, N):
     if rc != 0:
         raise ValueError("emulation rejected")
     return out
+
+
+def r2r(x, N, dst, nthr=0):
+    """DCT-0 (dst=False, rows of N/2+1) or DST-0 (dst=True, rows of N/2-1)."""
+    lib = load()
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    out = np.empty_like(x)
+    lib.emu_r2r.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    rows = x.size // x.shape[-1]
+    rc = lib.emu_r2r(N, rows, x.ctypes.data, out.ctypes.data, 1 if dst else 0, nthr)
+    if rc != 0:
+        raise ValueError(f"emulation rejected N={N} (rc={rc})")
+    return out

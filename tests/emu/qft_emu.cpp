@@ -119,6 +119,29 @@ extern "C" int emu_c2c(int N, int64_t batch, const float* in, float* out, int op
   return 0;
 }
 
+// DCT-0 (dst = 0, rows of N/2+1) or DST-0 (dst = 1, rows of N/2-1) of
+// periodization N, two rows per pass as on the device.
+extern "C" int emu_r2r(int N, int64_t batch, const float* in, float* out, int dst, int nthr) {
+  Row R(N, nullptr, nthr);
+  if (!R.ok) return -2;
+  const int64_t L = dst ? N / 2 - 1 : N / 2 + 1;
+  for (int64_t it = 0; it < (batch + 1) / 2; ++it) {
+    const int64_t a = 2 * it, b = 2 * it + 1;
+    if (dst) {
+      IoR2R<true> io;
+      io.ina = in + a * L; io.inb = b < batch ? in + b * L : nullptr;
+      io.outa = out + a * L; io.outb = b < batch ? out + b * L : nullptr; io.N = N;
+      run_row(R.P, R.e, io, nthr);
+    } else {
+      IoR2R<false> io;
+      io.ina = in + a * L; io.inb = b < batch ? in + b * L : nullptr;
+      io.outa = out + a * L; io.outb = b < batch ? out + b * L : nullptr; io.N = N;
+      run_row(R.P, R.e, io, nthr);
+    }
+  }
+  return 0;
+}
+
 // dtype 1: fp16 pairs, 2: bf16 pairs (uint16 pairs in memory)
 extern "C" int emu_c2c_half(int N, int64_t batch, const uint16_t* in, uint16_t* out, int dtype, int op, int nthr) {
   Row R(N, nullptr, nthr);

@@ -152,3 +152,20 @@ def test_large_path_real():
     assert bits_equal(emu.r2c_large(X, 1, N), orc.irdft(X, N, fp32=True).astype(np.float32))
     assert bits_equal(emu.r2c_large(X, 2, N), orc.rdft_adjoint(X, N, fp32=True).astype(np.float32))
     assert bits_equal(emu.r2c_large(x, 3, N), orc.irdft_adjoint(x, fp32=True).astype(np.complex64))
+
+
+@pytest.mark.parametrize("lg", [2, 3, 4, 6, 9, 12, 14])
+@pytest.mark.parametrize("rows", [1, 3])
+def test_dct0_dst0_bit_exact(lg, rows):
+    """Standalone DCT-0 / DST-0 of periodization N (eqs qft_0B, qft_0C): the
+    bits of the dct / dst recursions of the oracle evaluated in FP32."""
+    N = 1 << lg
+    g = inputs.rng(400 + lg)
+    c = g.standard_normal((rows, N // 2 + 1)).astype(np.float32)
+    C = emu.r2r(c, N, dst=False)
+    assert bits_equal(C, orc.dct0(c, fp32=True).astype(np.float32))
+    d = g.standard_normal((rows, N // 2 - 1)).astype(np.float32)
+    S = emu.r2r(d, N, dst=True)
+    dfull = np.zeros((rows, N // 2 + 1))
+    dfull[:, 1:-1] = d
+    assert bits_equal(S, orc.dst0(dfull, N, fp32=True)[:, 1:-1].astype(np.float32))

@@ -450,3 +450,62 @@ def test_autotuned_ragged_same_bits(q):
         outs.append(y.cpu().numpy())
         p.destroy()
     assert bits_equal(outs[0], outs[1])
+
+
+# ----------------------------------------------------- standalone DCT-0 / DST-0
+@pytest.mark.parametrize("lg,rows", [(2, 3), (3, 2), (5, 5), (10, 33), (12, 64), (14, 16), (16, 5), (18, 3)])
+def test_dct0_dst0_bit_exact(q, lg, rows):
+    """DCT-0 / DST-0 of periodization N (eqs qft_0B, qft_0C) through the C ABI:
+    the bits of the oracle's dct / dst recursions evaluated in FP32 (large N on
+    the large-row path), odd row counts included, and in place."""
+    N = 1 << lg
+    g = inputs.rng(500 + lg)
+    c = g.standard_normal((rows, N // 2 + 1)).astype(np.float32)
+    d = g.standard_normal((rows, N // 2 - 1)).astype(np.float32)
+    dfull = np.zeros((rows, N // 2 + 1))
+    dfull[:, 1:-1] = d
+    sample = sorted({0, rows - 1, rows // 2})
+    refC = orc.dct0(c[sample], fp32=True).astype(np.float32)
+    refS = orc.dst0(dfull[sample], N, fp32=True)[:, 1:-1].astype(np.float32)
+    for kind, x, ref in ((q.KIND_DCT0, c, refC), (q.KIND_DST0, d, refS)):
+        p = q.Plan(N, rows, kind=kind)
+        xt = gpu(x)
+        y = torch.empty_like(xt)
+        p.execute(q.OP_FORWARD, xt, y)
+        torch.cuda.synchronize()
+        assert bits_equal(y.cpu().numpy()[sample], ref), (kind, N)
+        yadj = torch.empty_like(xt)
+        p.execute(q.OP_FORWARD_ADJOINT, xt, yadj)          # symmetric matrix: same map
+        p.execute(q.OP_FORWARD, xt, xt)                    # in place
+        torch.cuda.synchronize()
+        assert torch.equal(yadj, y) and torch.equal(xt, y)
+        with pytest.raises(q.QFTError):
+            p.execute(q.OP_INVERSE, gpu(x), y)
+        p.destroy()
+
+
+def test_dct0_dst0_python_api(q):
+    """qft.dct0 / qft.dst0 on [..., N/2+1] / [..., N/2-1] float32 tensors."""
+    N = 256
+    g = inputs.rng(77)
+    c = g.standard_normal((4, 3, N // 2 + 1)).astype(np.float32)
+    d = g.standard_normal((4, 3, N // 2 - 1)).astype(np.float32)
+    C = q.dct0(gpu(c)).cpu().numpy()
+    S = q.dst0(gpu(d)).cpu().numpy()
+    dfull = np.zeros((12, N // 2 + 1))
+    dfull[:, 1:-1] = d.reshape(12, -1)
+    assert bits_equal(C.reshape(12, -1), orc.dct0(c.reshape(12, -1), fp32=True).astype(np.float32))
+    assert bits_equal(S.reshape(12, -1), orc.dst0(dfull, N, fp32=True)[:, 1:-1].astype(np.float32))
+
+
+def test_fft_host_pipelined_matches_device_fft(q):
+    """qft.fft_host (pinned host rows, chunked, copies overlapped with the
+    transforms on three streams) gives the bits of the device transform,
+    including a partial last chunk."""
+    N, rows = 4096, 37
+    z = inputs.normal_complex(rows, N, seed=91)
+    host = torch.from_numpy(z).pin_memory()
+    out = q.fft_host(host, chunk_bytes=5 * N * 8)       # 8 chunks, the last one of 2 rows
+    torch.cuda.synchronize()
+    ref = q.fft(gpu(z)).cpu().numpy()
+    assert bits_equal(out.numpy(), ref)

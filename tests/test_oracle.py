@@ -355,3 +355,25 @@ def test_filter_gradients_by_central_differences_sampled():
         xm = x.copy(); xm[idx] -= eps
         fd = (_filter_loss(xp, W) - _filter_loss(xm, W)) / (2 * eps)
         assert abs(fd - gx[idx]) < 1e-6 * max(1.0, abs(gx[idx]))
+
+
+@pytest.mark.parametrize("N", [4, 8, 16, 64, 256])
+def test_dct0_dst0_batched_match_definitions(N):
+    """The standalone DCT-0 / DST-0 of periodization N (eqs qft_0B, qft_0C):
+    C(k) = sum_{n=0}^{N/2} c(n) cos(2 pi n k / N), k in [0, N/2];
+    S(k) = sum_{n=1}^{N/2-1} d(n) sin(2 pi n k / N), k in [1, N/2-1];
+    batched rows, in FP64 and (within FP32 error) in FP32."""
+    g = inputs.rng(300 + N)
+    c = g.standard_normal((3, N // 2 + 1))
+    d = g.standard_normal((3, N // 2 + 1))
+    n = np.arange(N // 2 + 1)
+    Cm = np.cos(2 * np.pi * np.outer(n, n) / N)
+    Sm = np.sin(2 * np.pi * np.outer(n, n) / N)
+    Sm[0, :] = Sm[-1, :] = 0
+    C_ref = c @ Cm
+    S_ref = d @ Sm
+    S_ref[:, 0] = S_ref[:, -1] = 0
+    assert np.abs(orc.dct0(c) - C_ref).max() < 1e-13 * N
+    assert np.abs(orc.dst0(d, N) - S_ref).max() < 1e-13 * N
+    assert np.abs(orc.dct0(c, fp32=True) - C_ref).max() < 1e-5 * N
+    assert np.abs(orc.dst0(d, N, fp32=True) - S_ref).max() < 1e-5 * N
