@@ -151,7 +151,7 @@ int qft_execute_backward(qft_plan plan, const void* grad_out, void* grad_in, voi
  *   qft_filter_create: plan for x, y of shape [batch][channels][n] (float32,
  *     device, contiguous) and weights W of shape [channels][n/2+1] (complex64).
  *     4 <= n <= 2^13 power of two; batch, channels >= 1.  The plan owns a
- *     scratch of channels * 4 * (n/2+1) complex partial gradients.
+ *     scratch of channels * 16 * (n/2+1) complex partial gradients.
  *   qft_filter_forward:  y = irfft(W[c] (.) rfft(x[b][c])) for every b, c.
  *   qft_filter_backward: given x, W and gy = dL/dy, writes
  *     gx = dL/dx = rfft^H(conj(W) (.) irfft^H(gy))  (shape of x) and

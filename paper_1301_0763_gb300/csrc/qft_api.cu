@@ -148,7 +148,11 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
       if (items > 0) e = cudaMalloc(&p->scratch, (size_t)(rows * per_row));
       if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); return rc; }
     }
-    const int rc = plan_schedule(p, p->tune, p->threads, p->node_log2, p->node_nt);
+    // large rows: the NODE kernel at 256 threads (two CTAs per SM) where the
+    // planner accepts it (nodes of at most 2^11 cells), else 512
+    int rc = QFT_ERR_INVALID_N;
+    if (p->large_host) rc = plan_schedule(p, p->tune, p->threads, p->node_log2, 256);
+    if (rc != QFT_OK) rc = plan_schedule(p, p->tune, p->threads, p->node_log2, p->node_nt);
     if (rc != QFT_OK) { free_resources(p); return rc; }
   }
   return QFT_OK;

@@ -16,7 +16,7 @@
 namespace {
 
 constexpr int kFiltNT = 256;
-constexpr int kFiltParts = 4;   // row-pair slices per channel in the backward pass
+constexpr int kFiltParts = 16;  // row-pair slices per channel in the backward pass (CTAs = channels x 16)
 
 struct FiltLayout {
   size_t spec_off, spec_cells, acc_off, total;

@@ -18,12 +18,12 @@ struct QftTune {
 };
 
 // The library's schedule: register tiles of 8 cells per side in F1 and SLICE,
-// 16 in DIF, 8 in LEAF, 16 output bins per FINAL task; 256 threads per CTA
-// (512 for N = 2^14, whose top SLICE phase has 512 tasks per node).
+// 16 in DIF (8 from N = 2^13 on, where the autotuner prefers them), 8 in LEAF,
+// 16 output bins per FINAL task; 256 threads per CTA (512 for N = 2^14, whose
+// top SLICE phase has 512 tasks per node).
 static inline QftTune qft_default_tune(int r) {
   QftTune t;
-  t.L1 = 3; t.LS = 4; t.LL = 0; t.LB = 3; t.LF = 3;
-  (void)r;
+  t.L1 = 3; t.LS = r >= 13 ? 3 : 4; t.LL = 0; t.LB = 3; t.LF = 3;
   return t;
 }
 

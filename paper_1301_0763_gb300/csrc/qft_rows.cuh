@@ -300,7 +300,15 @@ k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int
         if (global_ns() - t0 > kWaitLimitNs) { ok = false; break; }
       }
       if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) atomicExch(status, QFT_ERR_TIMEOUT);
+        if (threadIdx.x == 0) {
+          atomicExch(status, QFT_ERR_TIMEOUT);
+          // the copy in flight writes this CTA's shared memory: give it a
+          // second bounded wait before the CTA leaves
+          const uint64_t t1 = global_ns();
+          while (!mbar_try_wait(mb, parity) && global_ns() - t1 < kWaitLimitNs) {
+          }
+        }
+        __syncthreads();
         return;
       }
       parity ^= 1;
