@@ -281,7 +281,10 @@ static int autotune(qft_plan p) {
     static const int kLB[] = {2, 3};
     static const int kLF[] = {1, 2, 3};
     static const int kStage[] = {0, 1};
-    static const int kNB[] = {10, 11, 12};
+    // node size and NODE threads are tried together: 256 threads need smaller
+    // nodes at large N, which one knob at a time would never reach
+    static const int kNode[] = {(12 << 16) | 512, (12 << 16) | 256, (11 << 16) | 256, (11 << 16) | 512,
+                                (10 << 16) | 256, (10 << 16) | 512};
     for (int sweep = 0; sweep < 2; ++sweep) {
       for (int knob = 0; knob < 8; ++knob) {
         const int* vals = nullptr;
@@ -293,8 +296,7 @@ static int autotune(qft_plan p) {
         case 3: vals = kLB; nv = 2; break;
         case 4: if (!large) { vals = kLF; nv = 3; } break;
         case 5: if (!large) { vals = kStage; nv = 2; } break;
-        case 6: if (large) { vals = kNB; nv = 3; } break;
-        case 7: if (large) { vals = kThreads; nv = 2; } break;
+        case 6: if (large) { vals = kNode; nv = 6; } break;   // (node size, NODE threads) pairs
         }
         for (int v = 0; v < nv; ++v) {
           QftSched c = best;
@@ -305,8 +307,7 @@ static int autotune(qft_plan p) {
           case 3: c.t.LB = vals[v]; break;
           case 4: c.t.LF = vals[v]; break;
           case 5: c.no_stage = vals[v]; break;
-          case 6: c.node_log2 = vals[v]; break;
-          case 7: c.node_nt = vals[v]; break;
+          case 6: c.node_log2 = vals[v] >> 16; c.node_nt = vals[v] & 0xffff; break;
           }
           if (sched_same(c, best)) continue;
           if (sched_apply(p, c) != QFT_OK) continue;
