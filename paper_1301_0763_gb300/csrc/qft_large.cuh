@@ -22,7 +22,8 @@ struct LargeArgs {
 // are compiled once (qft_k_node.cu) and launched through these helpers, which
 // return the CUDA error of the launch.
 cudaError_t qft_large_node_prepare(int nt, size_t smem);
-cudaError_t qft_large_node_launch(const LargeArgs& a, dim3 grid, int nt, size_t smem, cudaStream_t st);
+cudaError_t qft_large_node_launch(const LargeArgs& a, int64_t rows, int64_t items, int nt, size_t smem,
+                                  cudaStream_t st);
 cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st);
 
 namespace {
@@ -100,51 +101,55 @@ __global__ void __launch_bounds__(kLargeNT, 2) k_large_slice(LargeArgs a, int ph
 // `dst`.  base is a multiple of 16, so the padded layout of the window is the
 // padded layout of the scratch row shifted by qft_pidx(base).
 template <int L1, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_t rows) {
+  // Persistent: item = node CTA index * rows + row, visited in steps of the
+  // grid, so one CTA's items keep the same sub (and sub-plan) for long runs;
+  // the secants are loaded once per CTA and the sub-plan only when the sub changes.
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_sub;
   const QftLargePlan* LP = a.plan;
-  const int cta = blockIdx.x;
-  const int64_t row = blockIdx.y;
-  if (threadIdx.x == 0) {
-    int k = 0;
-    while (k + 1 < LP->nsub && LP->subs[k + 1].cta_begin <= cta) ++k;
-    s_sub = k;
-  }
-  __syncthreads();
-  const QftNodeSub& S = LP->subs[s_sub];
   QftRowPlan& Q = *reinterpret_cast<QftRowPlan*>(smem);
-  {
-    const int* src = reinterpret_cast<const int*>(&S.plan);
-    int* dst = reinterpret_cast<int*>(smem);
-    for (int i = threadIdx.x; i < (int)(sizeof(QftRowPlan) / 4); i += NT) dst[i] = src[i];
-  }
   const int NB = LP->NB;
   float* sec = reinterpret_cast<float*>(smem + qft_lib::align16(sizeof(QftRowPlan)));
   for (int m = threadIdx.x; m <= (1 << NB); m += NT) sec[m] = a.gsec[m];
   qc* cells = reinterpret_cast<qc*>(smem + qft_lib::align16(sizeof(QftRowPlan)) +
                                     qft_lib::align16(sizeof(float) * ((1 << NB) + 1)));
-  const int g = cta - S.cta_begin;
-  const int ncell = S.group << S.nb;
-  const int base = cls_off(a.r, S.cls) + g * ncell;
-  const int pb = qft_pidx(base);
-  const int pn = qft_pidx(ncell - 1) + 1;
-  const Eng ea = large_eng(a, 0, row);
-  const qc* srcp = side_ptr(ea, S.side) + pb;
-  for (int i = threadIdx.x; i < pn; i += NT) cells[i] = srcp[i];
-  __syncthreads();
-  Eng e;
-  e.side0 = cells - pb;     // the window maps class-level index base -> cells[0]
-  e.side1 = cells - pb;
-  e.sec = sec;
-  e.r = a.r;
-  e.N = 1 << a.r;
-  e.tabC = nullptr;
-  e.tabS = nullptr;
-  run_row_phases<L1, NT>(Q, e, NoIO(), g);
-  const Eng ed = large_eng(a, S.dst, row);
-  qc* dstp = side_ptr(ed, S.side) + pb;
-  for (int i = threadIdx.x; i < pn; i += NT) dstp[i] = cells[i];
+  const int64_t items = (int64_t)LP->node_ctas * rows;
+  int cur = -1;
+  int k = 0;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int cta = (int)(it / rows);
+    const int64_t row = it - (int64_t)cta * rows;
+    while (k + 1 < LP->nsub && LP->subs[k + 1].cta_begin <= cta) ++k;   // cta never decreases
+    const QftNodeSub& S = LP->subs[k];
+    if (k != cur) {
+      const int* src = reinterpret_cast<const int*>(&S.plan);
+      int* dst = reinterpret_cast<int*>(smem);
+      for (int i = threadIdx.x; i < (int)(sizeof(QftRowPlan) / 4); i += NT) dst[i] = src[i];
+      cur = k;
+    }
+    const int g = cta - S.cta_begin;
+    const int ncell = S.group << S.nb;
+    const int base = cls_off(a.r, S.cls) + g * ncell;
+    const int pb = qft_pidx(base);
+    const int pn = qft_pidx(ncell - 1) + 1;
+    const Eng ea = large_eng(a, 0, row);
+    const qc* srcp = side_ptr(ea, S.side) + pb;
+    for (int i = threadIdx.x; i < pn; i += NT) cells[i] = srcp[i];
+    __syncthreads();
+    Eng e;
+    e.side0 = cells - pb;     // the window maps class-level index base -> cells[0]
+    e.side1 = cells - pb;
+    e.sec = sec;
+    e.r = a.r;
+    e.N = 1 << a.r;
+    e.tabC = nullptr;
+    e.tabS = nullptr;
+    run_row_phases<L1, NT>(Q, e, NoIO(), g);
+    const Eng ed = large_eng(a, S.dst, row);
+    qc* dstp = side_ptr(ed, S.side) + pb;
+    for (int i = threadIdx.x; i < pn; i += NT) dstp[i] = cells[i];
+    __syncthreads();   // the next item overwrites the cells (and maybe the sub-plan)
+  }
 }
 #endif  // QFT_NODE_TU
 
@@ -173,9 +178,8 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
     for (int ph = 0; ph < H.nphase; ++ph) {
       const QftLargePhase& P = H.phases[ph];
       if (P.kind == QFT_LPH_NODE) {
-        const dim3 grid((unsigned)H.node_ctas, (unsigned)rows);
         qft_time_begin(p, st, QFT_KERNEL_NODE);
-        e = qft_large_node_launch(a, grid, node_nt, node_smem, st);
+        e = qft_large_node_launch(a, rows, (int64_t)H.node_ctas * rows, node_nt, node_smem, st);
         if (e != cudaSuccess) return qft_set_cuda(p, e);
       } else {
         const unsigned bx = (unsigned)((P.ntasks + kLargeNT * kLargeTPT - 1) / (kLargeNT * kLargeTPT));
