@@ -120,7 +120,9 @@ QFT_HD int qft_pidx(int i) { return i + (i >> 4); }
 // Padded index of cell base + t*2^h (h >= 4, base's low 4 bits below 2^h):
 // pidx(base) + t * qft_pstride(h), one add per access instead of a shift and two adds.
 QFT_HD int qft_pstride(int h) { return (1 << h) + (1 << (h - 4)); }
-QFT_HD int qft_side_len(int N) { return qft_pidx(N / 2) + 1; }   // padded cells per side
+// padded cells per side of a scratch row, rounded up to even so that every
+// row and both sides start on a 16-byte boundary
+QFT_HD int qft_side_len(int N) { return (qft_pidx(N / 2) + 2) & ~1; }
 QFT_HD int cls_off(int r, int j) { return (1 << (r - 1)) - (1 << (r - 1 - j)); }
 QFT_HD int cls_bits(int r, int j) { return r - 2 - j; }
 QFT_HD unsigned invgray(unsigned g) {

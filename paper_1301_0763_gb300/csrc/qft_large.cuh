@@ -14,8 +14,9 @@ struct LargeArgs {
   qc* scrA;                   // scratch copy A: rows * 2 * side_len cells
   qc* scrB;                   // scratch copy B
   int64_t row0;               // first row (item) of this launch chunk
-  int side_len;               // padded cells per side
+  int side_len;               // padded cells per side (even: rows and sides start 16-byte aligned)
   int r;
+  int* status;                // device status word (QFT_ERR_TIMEOUT), or null
 };
 
 // The NODE and SLICE kernels do not depend on the IO of the transform; they
@@ -67,9 +68,13 @@ __global__ void __launch_bounds__(kLargeNT, 2) k_large_global(LargeArgs a, int p
   }
 }
 
+// cells of one NODE buffer: the largest group window, rounded up to an even
+// count so that a bulk copy of it is a multiple of 16 bytes
+__host__ __device__ inline int node_buf_cells(int NB) { return (qft_pidx(1 << NB) + 2) & ~1; }
+// plan | secants | two cell buffers (the current item and the prefetched next one)
 __host__ __device__ inline size_t node_smem_bytes(int NB) {
   return qft_lib::align16(sizeof(QftRowPlan)) + qft_lib::align16(sizeof(float) * (((size_t)1 << NB) + 1)) +
-         qft_lib::align16(8 * (size_t)qft_pidx(1 << NB));
+         2 * qft_lib::align16(8 * (size_t)node_buf_cells(NB));
 }
 
 #ifdef QFT_NODE_TU
@@ -100,55 +105,133 @@ __global__ void __launch_bounds__(kLargeNT, 2) k_large_slice(LargeArgs a, int ph
 // into shared memory, the sub-plan runs on them, and they are written to copy
 // `dst`.  base is a multiple of 16, so the padded layout of the window is the
 // padded layout of the scratch row shifted by qft_pidx(base).
+// Window of item `it` (= node CTA index * rows + row): sub k (advanced from
+// its previous value; the node CTA index never decreases along a CTA's items),
+// group g, the padded cell offset pb and count pn, and the source row.
+struct NodeItem {
+  int k, g, pb, pn;
+  int64_t row;
+};
+__device__ __forceinline__ void node_item(const QftLargePlan* LP, int r, int64_t it, int64_t rows, int& k,
+                                          NodeItem& w) {
+  const int cta = (int)(it / rows);
+  w.row = it - (int64_t)cta * rows;
+  while (k + 1 < LP->nsub && LP->subs[k + 1].cta_begin <= cta) ++k;
+  const QftNodeSub& S = LP->subs[k];
+  w.k = k;
+  w.g = cta - S.cta_begin;
+  const int ncell = S.group << S.nb;
+  const int base = cls_off(r, S.cls) + w.g * ncell;
+  w.pb = qft_pidx(base);
+  w.pn = qft_pidx(ncell - 1) + 1;
+}
+
 template <int L1, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_t rows) {
   // Persistent: item = node CTA index * rows + row, visited in steps of the
   // grid, so one CTA's items keep the same sub (and sub-plan) for long runs;
-  // the secants are loaded once per CTA and the sub-plan only when the sub changes.
+  // the secants are loaded once per CTA and the sub-plan only when the sub
+  // changes.  While an item is transformed, thread 0 copies the next item's
+  // cells into the other buffer with one bulk copy (completion on an mbarrier,
+  // waits bounded); windows that are not 16-byte aligned are loaded directly.
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ int s_staged[2];
   const QftLargePlan* LP = a.plan;
   QftRowPlan& Q = *reinterpret_cast<QftRowPlan*>(smem);
   const int NB = LP->NB;
   float* sec = reinterpret_cast<float*>(smem + qft_lib::align16(sizeof(QftRowPlan)));
-  for (int m = threadIdx.x; m <= (1 << NB); m += NT) sec[m] = a.gsec[m];
-  qc* cells = reinterpret_cast<qc*>(smem + qft_lib::align16(sizeof(QftRowPlan)) +
-                                    qft_lib::align16(sizeof(float) * ((1 << NB) + 1)));
+  qc* buf[2];
+  buf[0] = reinterpret_cast<qc*>(smem + qft_lib::align16(sizeof(QftRowPlan)) +
+                                 qft_lib::align16(sizeof(float) * ((1 << NB) + 1)));
+  buf[1] = buf[0] + qft_lib::align16(8 * (size_t)node_buf_cells(NB)) / 8;
   const int64_t items = (int64_t)LP->node_ctas * rows;
+  const auto src_of = [&](const NodeItem& w) {
+    return side_ptr(large_eng(a, 0, w.row), LP->subs[w.k].side) + w.pb;
+  };
+  // thread 0: bulk copy of item w's window into buffer b, if everything is 16-byte aligned
+  const auto issue = [&](const NodeItem& w, int b) {
+    const qc* src = src_of(w);
+    const uint32_t bytes = (uint32_t)(((w.pn + 1) & ~1) * 8);
+    const bool ok = ((uintptr_t)src & 15) == 0 && (bytes & 15) == 0 && (smem_u32(buf[b]) & 15) == 0;
+    s_staged[b] = ok ? 1 : 0;
+    if (ok) {
+      fence_proxy_async_smem();
+      mbar_expect_tx(smem_u32(&mbar[b]), bytes);
+      bulk_g2s(smem_u32(buf[b]), src, bytes, smem_u32(&mbar[b]));
+    }
+  };
+  for (int m = threadIdx.x; m <= (1 << NB); m += NT) sec[m] = a.gsec[m];
+  int kc = 0, kn = 0;   // sub positions of the current and of the prefetched item
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && (int64_t)blockIdx.x < items) {
+    NodeItem w;
+    node_item(LP, a.r, blockIdx.x, rows, kn, w);
+    issue(w, 0);
+  }
+  __syncthreads();
+  uint32_t parity[2] = {0, 0};
   int cur = -1;
-  int k = 0;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-    const int cta = (int)(it / rows);
-    const int64_t row = it - (int64_t)cta * rows;
-    while (k + 1 < LP->nsub && LP->subs[k + 1].cta_begin <= cta) ++k;   // cta never decreases
-    const QftNodeSub& S = LP->subs[k];
-    if (k != cur) {
+  int b = 0;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x, b ^= 1) {
+    NodeItem w;
+    node_item(LP, a.r, it, rows, kc, w);
+    const QftNodeSub& S = LP->subs[w.k];
+    qc* cells = buf[b];
+    if (s_staged[b]) {
+      const uint64_t t0 = global_ns();
+      bool ok = true;
+      while (!mbar_try_wait(smem_u32(&mbar[b]), parity[b])) {
+        if (global_ns() - t0 > kWaitLimitNs) { ok = false; break; }
+      }
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          if (a.status) atomicExch(a.status, QFT_ERR_TIMEOUT);
+          // the copy in flight writes this CTA's shared memory: a second bounded wait
+          const uint64_t t1 = global_ns();
+          while (!mbar_try_wait(smem_u32(&mbar[b]), parity[b]) && global_ns() - t1 < kWaitLimitNs) {
+          }
+        }
+        __syncthreads();
+        return;
+      }
+      parity[b] ^= 1;
+    } else {
+      const qc* srcp = src_of(w);
+      for (int i = threadIdx.x; i < w.pn; i += NT) cells[i] = srcp[i];
+    }
+    // the next item's copy goes to the other buffer, free since the last barrier
+    const int64_t next = it + gridDim.x;
+    if (threadIdx.x == 0 && next < items) {
+      NodeItem wn;
+      node_item(LP, a.r, next, rows, kn, wn);
+      issue(wn, b ^ 1);
+    }
+    if (w.k != cur) {
       const int* src = reinterpret_cast<const int*>(&S.plan);
       int* dst = reinterpret_cast<int*>(smem);
       for (int i = threadIdx.x; i < (int)(sizeof(QftRowPlan) / 4); i += NT) dst[i] = src[i];
-      cur = k;
+      cur = w.k;
     }
-    const int g = cta - S.cta_begin;
-    const int ncell = S.group << S.nb;
-    const int base = cls_off(a.r, S.cls) + g * ncell;
-    const int pb = qft_pidx(base);
-    const int pn = qft_pidx(ncell - 1) + 1;
-    const Eng ea = large_eng(a, 0, row);
-    const qc* srcp = side_ptr(ea, S.side) + pb;
-    for (int i = threadIdx.x; i < pn; i += NT) cells[i] = srcp[i];
     __syncthreads();
     Eng e;
-    e.side0 = cells - pb;     // the window maps class-level index base -> cells[0]
-    e.side1 = cells - pb;
+    e.side0 = cells - w.pb;   // the window maps class-level index base -> cells[0]
+    e.side1 = cells - w.pb;
     e.sec = sec;
     e.r = a.r;
     e.N = 1 << a.r;
     e.tabC = nullptr;
     e.tabS = nullptr;
-    run_row_phases<L1, NT>(Q, e, NoIO(), g);
-    const Eng ed = large_eng(a, S.dst, row);
-    qc* dstp = side_ptr(ed, S.side) + pb;
-    for (int i = threadIdx.x; i < pn; i += NT) dstp[i] = cells[i];
-    __syncthreads();   // the next item overwrites the cells (and maybe the sub-plan)
+    run_row_phases<L1, NT>(Q, e, NoIO(), w.g);
+    const Eng ed = large_eng(a, S.dst, w.row);
+    qc* dstp = side_ptr(ed, S.side) + w.pb;
+    for (int i = threadIdx.x; i < w.pn; i += NT) dstp[i] = cells[i];
+    __syncthreads();   // this buffer (and maybe the sub-plan) is reused two items on
   }
 }
 #endif  // QFT_NODE_TU
@@ -166,6 +249,7 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
   a.scrB = a.scrA + (size_t)p->scratch_rows * 2 * p->side_len;
   a.side_len = p->side_len;
   a.r = p->r;
+  a.status = p->d_status;
   const size_t node_smem = node_smem_bytes(H.NB);
   // node kernel: 512 threads (one CTA per SM) unless the plan asks for 256
   const int node_nt = p->node_nt == 256 ? 256 : 512;
