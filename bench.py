@@ -333,7 +333,7 @@ def run_gpu(args):
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel, from one
 # ncu capture of the named kernel at the stated size (scaled to a launch over
 # 2^28 elements); None once the kernel has changed since the capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"k_large_node": 4188667904}   # N = 2^16 capture: 523.6 MB over 2^25 elements, x 8
 
 
 def roofline(kt, peak, peak_src):
