@@ -81,6 +81,7 @@ static int plan_schedule(qft_plan p, QftTune t, int threads, int node_log2, int 
     p->smem = smem;
     p->threads = threads;
   } else {
+    if (t.LF < qft_lib::kLargeMinLF) return QFT_ERR_INVALID_N;   // the scratch holds tables for LF >= 3
     QftLargePlan* lp = (QftLargePlan*)malloc(sizeof(QftLargePlan));
     if (!lp) return QFT_ERR_CUDA;
     if (qft_build_large_plan(r, t, node_log2, node_nt, lp) != 0) { free(lp); return QFT_ERR_INVALID_N; }
@@ -138,7 +139,9 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
       if (!p->large_host) { free_resources(p); return QFT_ERR_CUDA; }
       p->side_len = qft_side_len((int)N);
       const int64_t items = kind == QFT_KIND_C2C ? batch : (batch + 1) / 2;   // real kinds: row pairs
-      const int64_t per_row = 2 * 2 * (int64_t)p->side_len * 8;
+      // two copies of the class data plus the FINAL tasks' C/S tables
+      const int64_t per_row = 2 * 2 * (int64_t)p->side_len * 8 +
+                              (int64_t)qft_lib::large_tab_cells((int)N, qft_lib::kLargeMinLF) * 8;
       int64_t rows = qft_lib::kScratchBudget / per_row;
       if (rows > items) rows = items;
       if (rows > 65535) rows = 65535;

@@ -44,6 +44,10 @@ __host__ __device__ inline size_t off_side0(int N) { return off_sec() + align16(
 __host__ __device__ inline size_t off_tab(int N) { return off_side0(N) + 2 * side_bytes(N); }
 __host__ __device__ inline size_t tab_cells(int N, int LF) { return (size_t)(N >> LF) + 2; }
 __host__ __device__ inline size_t row_smem_bytes(int N, int LF) { return off_tab(N) + align16(8 * tab_cells(N, LF)); }
+// large-row path: cells per row of the C/S tables in scratch (Mt = N / 2^LF), even;
+// the scratch is sized for LF >= kLargeMinLF
+constexpr int kLargeMinLF = 3;
+__host__ __device__ inline int large_tab_cells(int N, int LF) { return ((N >> LF) + 2 + 1) & ~1; }
 }
 
 struct qft_plan_s {

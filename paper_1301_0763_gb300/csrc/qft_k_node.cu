@@ -30,6 +30,11 @@ cudaError_t qft_large_node_launch(const LargeArgs& a, int64_t rows, int64_t item
   return cudaGetLastError();
 }
 
+cudaError_t qft_large_tab_launch(const LargeArgs& a, int64_t rows, int LF, cudaStream_t st) {
+  k_large_tab<<<(unsigned)rows, 256, 0, st>>>(a, LF);
+  return cudaGetLastError();
+}
+
 cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st) {
   k_large_slice<<<grid, kLargeNT, 0, st>>>(a, phase);
   return cudaGetLastError();

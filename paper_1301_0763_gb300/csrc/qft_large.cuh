@@ -17,7 +17,11 @@ struct LargeArgs {
   int side_len;               // padded cells per side (even: rows and sides start 16-byte aligned)
   int r;
   int* status;                // device status word (QFT_ERR_TIMEOUT), or null
+  qc* tab;                    // C_Mt / S_Mt tables of the FINAL tasks: rows * tab_stride cells, or null
+  int tab_stride;             // cells per row of the tables
+  int tabS_off;               // S_Mt starts tabS_off cells after C_Mt (Mt/2 + 1)
 };
+
 
 // The NODE and SLICE kernels do not depend on the IO of the transform; they
 // are compiled once (qft_k_node.cu) and launched through these helpers, which
@@ -26,6 +30,7 @@ cudaError_t qft_large_node_prepare(int nt, size_t smem);
 cudaError_t qft_large_node_launch(const LargeArgs& a, int64_t rows, int64_t items, int nt, size_t smem,
                                   cudaStream_t st);
 cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st);
+cudaError_t qft_large_tab_launch(const LargeArgs& a, int64_t rows, int LF, cudaStream_t st);
 
 namespace {
 
@@ -40,8 +45,8 @@ __device__ __forceinline__ Eng large_eng(const LargeArgs& a, int copy, int64_t r
   e.sec = a.gsec;
   e.r = a.r;
   e.N = 1 << a.r;
-  e.tabC = nullptr;
-  e.tabS = nullptr;
+  e.tabC = a.tab ? a.tab + row * (int64_t)a.tab_stride : nullptr;
+  e.tabS = a.tab ? e.tabC + a.tabS_off : nullptr;
   return e;
 }
 
@@ -234,6 +239,19 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_
     __syncthreads();   // this buffer (and maybe the sub-plan) is reused two items on
   }
 }
+// TAB phase: the C_Mt / S_Mt tables of one row (one CTA), level by level from
+// the dct(2) / dst(4) base cases with the class outputs in copy A (eqs qft_5C,
+// qft_5D, qft_6 and their DST forms), as the row engine builds them in shared
+// memory; a CTA barrier separates the levels.
+__global__ void __launch_bounds__(256) k_large_tab(LargeArgs a, int LF) {
+  const Eng e = large_eng(a, 0, blockIdx.x);
+  const int mt = a.r - LF;
+  for (int m = 1; m <= mt; ++m) {
+    tab_level_c(e, m, threadIdx.x, 256);
+    if (m >= 2) tab_level_s(e, m, threadIdx.x, 256);
+    __syncthreads();
+  }
+}
 #endif  // QFT_NODE_TU
 
 // One execute on the large-row path: every phase of the plan, in order, for
@@ -250,6 +268,9 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
   a.side_len = p->side_len;
   a.r = p->r;
   a.status = p->d_status;
+  a.tab = a.scrB + (size_t)p->scratch_rows * 2 * p->side_len;   // after the two copies
+  a.tab_stride = qft_lib::large_tab_cells(1 << p->r, H.LF);
+  a.tabS_off = ((1 << p->r) >> H.LF) / 2 + 1;
   const size_t node_smem = node_smem_bytes(H.NB);
   // node kernel: 512 threads (one CTA per SM) unless the plan asks for 256
   const int node_nt = p->node_nt == 256 ? 256 : 512;
@@ -261,7 +282,11 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
     a.row0 = r0;
     for (int ph = 0; ph < H.nphase; ++ph) {
       const QftLargePhase& P = H.phases[ph];
-      if (P.kind == QFT_LPH_NODE) {
+      if (P.kind == QFT_LPH_TAB) {
+        qft_time_begin(p, st, QFT_KERNEL_GLOBAL);
+        e = qft_large_tab_launch(a, rows, H.LF, st);
+        if (e != cudaSuccess) return qft_set_cuda(p, e);
+      } else if (P.kind == QFT_LPH_NODE) {
         qft_time_begin(p, st, QFT_KERNEL_NODE);
         e = qft_large_node_launch(a, rows, (int64_t)H.node_ctas * rows, node_nt, node_smem, st);
         if (e != cudaSuccess) return qft_set_cuda(p, e);

@@ -74,7 +74,8 @@ struct QftRowPlan {
 #define QFT_LP_MAX_SEGS 160
 #define QFT_LP_MAX_SUB 48
 
-enum QftLargePhaseKind { QFT_LPH_GLOBAL = 0, QFT_LPH_SLICE = 1, QFT_LPH_NODE = 2 };
+// TAB: the C_Mt / S_Mt tables of the FINAL tasks, one CTA per row
+enum QftLargePhaseKind { QFT_LPH_GLOBAL = 0, QFT_LPH_SLICE = 1, QFT_LPH_NODE = 2, QFT_LPH_TAB = 3 };
 
 struct QftLargePhase {
   int32_t kind;     // QftLargePhaseKind

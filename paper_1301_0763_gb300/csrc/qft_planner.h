@@ -373,6 +373,13 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
   }
   for (int j = 0; j < ncls; ++j)
     if (big[j] && cur[j] != 0) return -1;   // every class output must end in copy A
+  // ---- C_Mt / S_Mt tables of the FINAL tasks (Mt = N / 2^LF)
+  if (P->nphase >= QFT_LP_MAX_PHASES) return -1;
+  P->phases[P->nphase].kind = QFT_LPH_TAB;
+  P->phases[P->nphase].seg0 = P->nseg;
+  P->phases[P->nphase].nseg = 0;
+  P->phases[P->nphase].ntasks = 0;
+  P->nphase++;
   // ---- FINAL
   if (P->nphase >= QFT_LP_MAX_PHASES) return -1;
   begin_phase(QFT_LPH_GLOBAL);

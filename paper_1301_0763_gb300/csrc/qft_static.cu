@@ -11,9 +11,10 @@
 // routine that allocates, neither here nor through torch.
 //
 // Storage (file-scope device arrays, reserved when the module loads):
-//   g_static_scratch  64 MiB: scratch copies A and B of as many rows as fit
-//                     (2 copies x 2 sides x side_len cells of 8 bytes per row);
-//                     rows beyond that are done in successive chunks.
+//   g_static_scratch  64 MiB: scratch copies A and B and the FINAL tasks' C/S
+//                     tables of as many rows as fit (2 copies x 2 sides x
+//                     side_len cells plus N/8 + 4 table cells, 8 bytes each, per
+//                     row); rows beyond that are done in successive chunks.
 //   g_static_sec      Gray-ordered FP32 secants of Sec. 6.1 for N = 2^20; the
 //                     table for a shorter N is its prefix of N/4 entries.
 //   g_static_plans    the launch schedules for N = 2^15 ... 2^20.
@@ -134,7 +135,8 @@ extern "C" int qft_execute_static_scratch(int64_t n, int64_t batch, int op, cons
   p.d_large = d.plans + idx;
   p.scratch = d.scratch;
   p.side_len = qft_side_len((int)n);
-  const int64_t per_row = 2 * 2 * (int64_t)p.side_len * (int64_t)sizeof(qc_storage);
+  const int64_t per_row = 2 * 2 * (int64_t)p.side_len * (int64_t)sizeof(qc_storage) +
+                          (int64_t)qft_lib::large_tab_cells((int)n, qft_lib::kLargeMinLF) * (int64_t)sizeof(qc_storage);
   int64_t rows = (int64_t)kStaticScratchBytes / per_row;
   if (rows > batch) rows = batch;
   if (rows > 65535) rows = 65535;

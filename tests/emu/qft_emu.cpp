@@ -198,16 +198,23 @@ static QftLargePlan g_lp;
 template <class IO>
 static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vector<qc>& B, int side_len,
                           const float* gsec, const IO& io) {
+  std::vector<qc> tab(((1 << LP.r) >> LP.LF) + 4, mkc(NAN, NAN));
   auto eng = [&](int copy) {
     Eng e;
     qc* base = copy ? B.data() : A.data();
     e.side0 = base; e.side1 = base + side_len; e.sec = gsec; e.r = LP.r; e.N = 1 << LP.r;
-    e.tabC = nullptr; e.tabS = nullptr;
+    e.tabC = tab.data(); e.tabS = tab.data() + ((1 << LP.r) >> LP.LF) / 2 + 1;
     return e;
   };
   for (int ph = 0; ph < LP.nphase; ++ph) {
     const QftLargePhase& P = LP.phases[ph];
-    if (P.kind == QFT_LPH_GLOBAL) {
+    if (P.kind == QFT_LPH_TAB) {
+      const Eng e = eng(0);
+      for (int m = 1; m <= LP.r - LP.LF; ++m) {
+        tab_level_c(e, m, 0, 1);
+        if (m >= 2) tab_level_s(e, m, 0, 1);
+      }
+    } else if (P.kind == QFT_LPH_GLOBAL) {
       const Eng e = eng(0);
       const int NT = 256, TPT = 4;
       const int nblk = (P.ntasks + NT * TPT - 1) / (NT * TPT);
