@@ -104,6 +104,7 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
   p->d_plan = nullptr; p->d_sec = nullptr; p->last_cuda = cudaSuccess; p->last_stream = nullptr;
   p->large_host = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->scratch_rows = 0; p->side_len = 0;
   p->chunk_rows = 0;
+  p->large_tab = 0;
   p->grid = 0; p->threads = 0; p->smem = 0;
   p->nclasses = 0; p->classes = nullptr; p->d_offsets = nullptr; p->d_args = nullptr; p->h_args = nullptr;
   p->graph = nullptr; p->gexec = nullptr; p->graph_kernels = 0;
@@ -148,6 +149,7 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
       if (rows < 1) rows = 1;
       p->scratch_rows = rows;
       p->threads = 256;
+      p->large_tab = (r <= 20 && rows >= 64) ? 1 : 0;
       if (items > 0) e = cudaMalloc(&p->scratch, (size_t)(rows * per_row));
       if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); return rc; }
     }
@@ -300,6 +302,7 @@ static int autotune(qft_plan p) {
         case 4: if (!large) { vals = kLF; nv = 3; } break;
         case 5: if (!large) { vals = kStage; nv = 2; } break;
         case 6: if (large) { vals = kNode; nv = 6; } break;   // (node size, NODE threads) pairs
+
         }
         for (int v = 0; v < nv; ++v) {
           QftSched c = best;

@@ -268,7 +268,9 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
   a.side_len = p->side_len;
   a.r = p->r;
   a.status = p->d_status;
-  a.tab = a.scrB + (size_t)p->scratch_rows * 2 * p->side_len;   // after the two copies
+  // tables after the two copies; a CTA builds one row's tables, which pays off
+  // only with enough rows of moderate length (the plan's large_tab)
+  a.tab = p->large_tab ? a.scrB + (size_t)p->scratch_rows * 2 * p->side_len : nullptr;
   a.tab_stride = qft_lib::large_tab_cells(1 << p->r, H.LF);
   a.tabS_off = ((1 << p->r) >> H.LF) / 2 + 1;
   const size_t node_smem = node_smem_bytes(H.NB);
@@ -283,6 +285,7 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
     for (int ph = 0; ph < H.nphase; ++ph) {
       const QftLargePhase& P = H.phases[ph];
       if (P.kind == QFT_LPH_TAB) {
+        if (!a.tab) continue;
         qft_time_begin(p, st, QFT_KERNEL_GLOBAL);
         e = qft_large_tab_launch(a, rows, H.LF, st);
         if (e != cudaSuccess) return qft_set_cuda(p, e);
