@@ -170,29 +170,39 @@ int qft_filter_backward(qft_plan plan, const float* x, const void* W, const floa
 /*
  * qft_execute_static_scratch -- run op (QFT_OP_*) on `batch` C2C FP32 rows of
  * length n, 2^15 <= n <= 2^20, like qft_execute on a QFT_KIND_C2C /
- * QFT_DTYPE_F32 plan, but without a plan and without allocating.  The paper
- * has no counterpart: this is a service entry point for callers that cannot
- * allocate device memory at the point of use (all free memory held by another
- * allocator, or a latency-bound loop where cudaMalloc / cudaFree would
- * synchronise the device).  It calls no cudaMalloc, cudaFree or other
- * allocating routine.
+ * QFT_DTYPE_F32 plan (the same bits), but without a plan and without
+ * allocating.  The paper has no counterpart: this is a service entry point
+ * for callers that cannot allocate device memory at the point of use (all
+ * free memory held by another allocator, or a latency-bound loop where
+ * cudaMalloc / cudaFree would synchronise the device).  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
  *   in, out  device pointers, [batch][n] complex64, 8-byte aligned; in == out
  *            is allowed.  stream as in qft_execute.
- * Storage: a 64 MiB scratch array, the secant table and the schedules are
- * file-scope device arrays of the library, reserved when its module loads and
- * shared by every call.  Nothing in them has to start at zero (each call writes
- * every scratch cell before reading it).  Calls whose executions overlap (two
- * streams, or host threads without ordering) race on the scratch: serialise
- * them.  Batches larger than the rows the scratch holds (3 rows at n = 2^20,
- * 113 at 2^15) run in successive chunks.
+ * Storage: a 64 MiB scratch array, the secant table, the schedules and a
+ * status word are file-scope device arrays of the library, reserved when its
+ * module loads and shared by every call.  Nothing in the scratch has to start
+ * at zero (each call writes every scratch cell before reading it).  Calls
+ * whose executions overlap (two streams, or host threads without ordering)
+ * race on the scratch: serialise them.  Batches larger than the rows the
+ * scratch holds (3 rows at n = 2^20, 113 at 2^15) run in successive chunks.
  * Set-up: the first call on each device (with that device current) looks up the
  * arrays with cudaGetSymbolAddress and fills the tables with blocking copies;
- * make that first call before any stream capture begins.
+ * make that first call before any stream capture begins.  The set-up is not
+ * repeated after cudaDeviceReset: do not use the entry point across a reset.
  * Errors: QFT_ERR_INVALID_N for n not a power of two or outside [2^15, 2^20]
  * (the limit the static scratch sets); QFT_ERR_INVALID_BATCH, _INVALID_ARG (op,
- * device ordinal >= 64), _NULLPTR, _ALIGN, _CUDA as for qft_execute.
+ * device ordinal >= 64), _NULLPTR, _ALIGN, _CUDA as for qft_execute.  A bounded
+ * device-side wait that expired is reported by qft_static_scratch_sync_status.
  */
 int qft_execute_static_scratch(int64_t n, int64_t batch, int op, const void* in, void* out, void* stream);
+
+/* Host-blocking status read of qft_execute_static_scratch on the current
+ * device: synchronises `stream` and returns the static status word (QFT_OK, or
+ * QFT_ERR_TIMEOUT if a bounded wait of a call expired and that call's output is
+ * incomplete), then clears it.  Allocates nothing (blocking copies to and from
+ * the word); QFT_OK if no call has run on the device.  Paper counterpart: none
+ * (the status of the entry point above). */
+int qft_static_scratch_sync_status(void* stream);
 
 /* Releases every resource of the plan.  Safe on NULL.  A destroyed plan must
  * not be used again; the library detects most such uses (QFT_ERR_DESTROYED). */
@@ -201,6 +211,22 @@ int qft_plan_destroy(qft_plan plan);
 /* Host-blocking: synchronises the plan's last stream and returns the plan's
  * device status word (QFT_OK or QFT_ERR_TIMEOUT), then clears it. */
 int qft_plan_sync_status(qft_plan plan);
+
+/* Limit, in nanoseconds, of the kernels' bounded waits for the input copies they
+ * stage in shared memory (default 0 = 2 s).  When a wait expires the kernel
+ * records QFT_ERR_TIMEOUT in the plan's status word (qft_plan_sync_status),
+ * waits once more with the 2 s limit for its copy in flight and returns; that
+ * execute's output is then incomplete.  Single-size plans only
+ * (QFT_ERR_INVALID_ARG otherwise, or for ns < 0). */
+int qft_plan_set_wait_limit(qft_plan plan, int64_t ns);
+
+/* Test of that failure path (diagnostics, single-size plans): the next execute
+ * of the plan arms each CTA's first staging barrier without issuing its copy,
+ * so that wait runs out after the wait limit with nothing in flight, the kernel
+ * returns early and the status word reads QFT_ERR_TIMEOUT.  Applies to the
+ * row kernel when it stages rows and to the NODE kernel of n > 2^14; one shot
+ * (cleared by that execute). */
+int qft_plan_withhold_next_copy(qft_plan plan);
 
 /* Last CUDA error recorded by the plan (a cudaError_t value, 0 if none). */
 int qft_plan_last_cuda_error(qft_plan plan);

@@ -60,6 +60,13 @@ def _declare(lib):
     lib.oracle_constants_used.restype = L
     lib.oracle_secant_table.argtypes = [L, dp]
     lib.oracle_brute_dft.argtypes = [L, dp, dp]
+    lib.oracle_cdft_cla.argtypes = [L, L, dp, dp, ctypes.c_int]
+    lib.oracle_function_cla.argtypes = [ctypes.c_int, L, dp, dp]
+    lib.oracle_counts_cla.argtypes = [ctypes.c_int, L, ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_longlong)]
+    lib.oracle_constants_used_cla.argtypes = [L, ctypes.POINTER(ctypes.c_ubyte), ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_constants_used_cla.restype = L
+    lib.oracle_fft_ld.argtypes = [L, dp, dp]
     lib.oracle_max_threads.restype = ctypes.c_int
     lib.oracle_is_float.restype = ctypes.c_int
     return lib
@@ -246,6 +253,61 @@ def brute_dft(z) -> np.ndarray:
     assert z.ndim == 1
     out = np.empty_like(z)
     _check(_load().oracle_brute_dft(z.shape[0], _dp(z.view(np.float64)), _dp(out.view(np.float64))))
+    return out
+
+
+# --------------------------------------------------------- classical QFT (Sec. 4)
+def cdft_cla(z, threads: int = 0, fp32: bool = False) -> np.ndarray:
+    """Forward DFT of each row by the classical QFT of Sec. 4 (cdft_cla ->
+    rdft_cla -> dct_cla / dct_to_cla / dst_cla / dst_to_cla), the paper's
+    comparison algorithm; fp32=True evaluates it in single precision."""
+    z = _c128(z)
+    N = z.shape[-1]
+    out = np.empty_like(z)
+    lib = _load32() if fp32 else _load()
+    _check(lib.oracle_cdft_cla(N, z.size // N if N else 0, _dp(z.view(np.float64)), _dp(out.view(np.float64)),
+                               threads))
+    return out
+
+
+FUNCTIONS_CLA = {"dct_cla": 0, "dct_to_cla": 1, "dst_cla": 2, "dst_to_cla": 3}
+
+
+def function_cla(name: str, N: int, s) -> np.ndarray:
+    """Run one classical function of Sec. 4 on a signal indexed by n (len N/2+1)."""
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.float64))
+    assert s.shape == (N // 2 + 1,)
+    out = np.zeros_like(s)
+    _check(_load().oracle_function_cla(FUNCTIONS_CLA[name], N, _dp(s), _dp(out)))
+    return out
+
+
+def counts_cla(kind: str, N: int):
+    """(adds, muls) the classical QFT performs for one CDFT ('cdft') or RDFT ('rdft')."""
+    a = ctypes.c_longlong()
+    m = ctypes.c_longlong()
+    _check(_load().oracle_counts_cla({"cdft": 0, "rdft": 1}[kind], N, ctypes.byref(a), ctypes.byref(m)))
+    return int(a.value), int(m.value)
+
+
+def constants_used_cla(N: int):
+    """(used[m] for m in [0, N/4], cos(pi/4) used?) for one classical CDFT of size N."""
+    used = np.zeros(N // 4 + 1, dtype=np.uint8)
+    c = ctypes.c_int()
+    cnt = _load().oracle_constants_used_cla(N, used.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                            ctypes.byref(c))
+    if cnt < 0:
+        raise ValueError("bad N")
+    return used, bool(c.value)
+
+
+def fft_ld(z) -> np.ndarray:
+    """Reference DFT of one row computed in long double (radix-2, exact-angle
+    twiddles), for error measurements; not either QFT algorithm."""
+    z = _c128(z)
+    assert z.ndim == 1
+    out = np.empty_like(z)
+    _check(_load().oracle_fft_ld(z.shape[0], _dp(z.view(np.float64)), _dp(out.view(np.float64))))
     return out
 
 

@@ -9,7 +9,10 @@
  *
  * What it computes.  The length-N = 2^r DFT (eq qft_0A) by the eight
  * recursive functions of Sec. 5 (cdft, rdft, dct, dct_ot, dct_oo, dst,
- * dst_ot, dst_oo), in FP64, in the paper's order and notation.  Every
+ * dst_ot, dst_oo), in FP64, in the paper's order and notation.  A second
+ * section holds the paper's comparison algorithm, the classical QFT of Sec. 4
+ * (cdft_cla, rdft_cla, dct_cla, dct_to_cla, dst_cla, dst_to_cla), and a
+ * long-double reference DFT for the error measure of eq qft_44.  Every
  * function works on arrays indexed by the paper's own time index n or
  * frequency index k (so s[n] is s(n) of the text; unused cells stay zero),
  * which keeps each line checkable against the equations by eye.
@@ -322,6 +325,196 @@ static void cdft(long N, const real *zre, const real *zim, real *Zre, real *Zim)
     free(Ar); free(Ai); free(Br); free(Bi);
 }
 
+/* ============================================ classical QFT (Sec. 4)
+ * The comparison algorithm of the paper: the same cdft / rdft, but dct_cla,
+ * dct_to_cla, dst_cla and dst_to_cla below the fold (Sec. 4.3-4.6), which
+ * separate even from odd HARMONICS first (eqs qft_1/qft_2, qft_9/qft_10) and
+ * convert odd harmonics into even ones by the secant (eqs qft_26/qft_28) on
+ * signals that still hold even time indices.  Arrays are indexed by the
+ * paper's n and k, as above; counters and constants are shared.
+ * Readings (the paper describes the functions in words; the printed
+ * clas_QFT columns of Tab. 3-5 and the cost formulas of Sec. 4 fix them):
+ *  - dct_to_cla: the n = 0 secant 1/(2 cos 0) = 1/2 is applied as a
+ *    multiplication by 1/2 (exact; counted, as in the cost formulas), and the
+ *    even/odd harmonic separation of s_dc_t1t runs over n in [0, N/4-1] like
+ *    the one of dct_cla, with the partner of n = 0 a stored zero (exact;
+ *    counted).
+ *  - dct_to_cla at N = 8 applies the DCT definition:
+ *    X(1) = s(0) + s(1) cos(pi/4), X(3) = s(0) - s(1) cos(pi/4).
+ *  - dst_to_cla: DST[s_ds_te](0) = DST[s_ds_te](N/2) = 0 in eq qft_28 (DST
+ *    form), so X(1) and X(N/2-1) take one term.
+ * With these readings the counted operations equal Tab. 3-5 (N = 4..2048)
+ * and the Sec. 4 formulas (N >= 8). */
+static void dct_cla(long N, const real *c, real *C);
+static void dct_to_cla(long N, const real *s, real *X);
+static void dst_cla(long N, const real *d, real *S);
+static void dst_to_cla(long N, const real *s, real *X);
+
+/* dct_cla: s_dc_tt c[n], n in [0, N/2] -> C[k], k in [0, N/2].  Separation
+ * of even from odd harmonics (eqs qft_1, qft_2), even-harmonic halving of
+ * s_dc_te (eqs qft_9, qft_10), backward eq qft_4B. */
+static void dct_cla(long N, const real *c, real *C)
+{
+    if (N == 2) {                          /* DCT-0 definition */
+        C[0] = ADD(c[0], c[1]);
+        C[1] = SUB(c[0], c[1]);
+        return;
+    }
+    real *te = zalloc(N / 4 + 1);          /* s_dc_te(n), n in [0, N/4] -> s_A_dc_tt */
+    real *to = zalloc(N / 4);              /* s_dc_to(n), n in [0, N/4-1] */
+    for (long n = 0; n < N / 4; ++n) {
+        te[n] = ADD(c[n], c[N / 2 - n]);   /* eq qft_1 */
+        to[n] = SUB(c[n], c[N / 2 - n]);   /* eq qft_2 */
+    }
+    te[N / 4] = c[N / 4];                  /* eq qft_1, n = N/4 */
+    real *CA = zalloc(N / 4 + 1);          /* DCT[s_A_dc_tt](kA), kA in [0, N/4] */
+    real *Xo = zalloc(N / 2);              /* DCT[s_dc_to](k), odd k */
+    dct_cla(N / 2, te, CA);
+    dct_to_cla(N, to, Xo);
+    for (long kA = 0; kA <= N / 4; ++kA) C[2 * kA] = CA[kA];   /* eqs qft_10, qft_4B */
+    for (long k = 1; k < N / 2; k += 2) C[k] = Xo[k];         /* eq qft_4B */
+    free(te); free(to); free(CA); free(Xo);
+}
+
+/* dct_to_cla: s_dc_to s[n], n in [0, N/4-1] -> X[k], odd k in [1, N/2-1].
+ * Secant conversion into s_dc_t1e (eq qft_26, backward eq qft_28), even
+ * harmonic halving into s_A_dc_t1t of periodization N/2, then that signal is
+ * split like s_dc_tt in dct_cla into s_B_dc_tt (periodization N/4) and
+ * s_A_dc_to (periodization N/2). */
+static void dct_to_cla(long N, const real *s, real *X)
+{
+    if (N == 4) {                          /* DCT definition: n = 0, k = 1 */
+        X[1] = s[0];
+        return;
+    }
+    if (N == 8) {                          /* DCT definition: n in {0, 1}, k in {1, 3} */
+        const real p = MUL(s[1], cos_pi_4());
+        X[1] = ADD(s[0], p);
+        X[3] = SUB(s[0], p);
+        return;
+    }
+    const long NA = N / 2;
+    real *t = zalloc(NA / 2 + 1);          /* s_dc_t1e(n) = s_A_dc_t1t(n), n in [0, N/4-1]; t[N/4] = 0 */
+    t[0] = MUL(s[0], (real)0.5);           /* eq qft_26, n = 0: 1/(2 cos 0) */
+    for (long n = 1; n < N / 4; ++n)
+        t[n] = MUL(s[n], secant(N, n));    /* eq qft_26 */
+    real *B = zalloc(NA / 4 + 1);          /* s_B_dc_tt(n), n in [0, NA/4] (periodization N/4) */
+    real *Ao = zalloc(NA / 4);             /* s_A_dc_to(n), n in [0, NA/4-1] (periodization N/2) */
+    for (long n = 0; n < NA / 4; ++n) {
+        B[n] = ADD(t[n], t[NA / 2 - n]);   /* eq qft_1 at periodization NA */
+        Ao[n] = SUB(t[n], t[NA / 2 - n]);  /* eq qft_2 at periodization NA */
+    }
+    B[NA / 4] = t[NA / 4];
+    real *YB = zalloc(NA / 4 + 1);         /* DCT[s_B_dc_tt](kB), kB in [0, N/8] */
+    real *YA = zalloc(NA / 2);             /* DCT[s_A_dc_to](kA), odd kA in [1, N/4-1] */
+    dct_cla(NA / 2, B, YB);
+    dct_to_cla(NA, Ao, YA);
+    real *T = zalloc(NA / 2 + 1);          /* DCT[s_A_dc_t1t](kA) = DCT[s_dc_t1e](2 kA), kA in [0, N/4] */
+    for (long kA = 0; kA <= NA / 2; ++kA) T[kA] = (kA & 1) ? YA[kA] : YB[kA / 2];   /* eq qft_4B */
+    for (long k = 1; k < N / 2; k += 2)
+        X[k] = ADD(T[(k - 1) / 2], T[(k + 1) / 2]);   /* eq qft_28 */
+    free(t); free(B); free(Ao); free(YB); free(YA); free(T);
+}
+
+/* dst_cla: s_ds_tt d[n], n in [1, N/2-1] -> S[k], k in [1, N/2-1].  DST form
+ * of the harmonic separation (the even-k child takes the difference). */
+static void dst_cla(long N, const real *d, real *S)
+{
+    if (N == 4) {                          /* DST-0 definition: n = 1, k = 1 */
+        S[1] = d[1];
+        return;
+    }
+    real *te = zalloc(N / 4);              /* s_ds_te(n), n in [1, N/4-1] -> s_A_ds_tt */
+    real *to = zalloc(N / 4 + 1);          /* s_ds_to(n), n in [1, N/4] */
+    for (long n = 1; n < N / 4; ++n) {
+        te[n] = SUB(d[n], d[N / 2 - n]);
+        to[n] = ADD(d[n], d[N / 2 - n]);
+    }
+    to[N / 4] = d[N / 4];
+    real *SA = zalloc(N / 4);              /* DST[s_A_ds_tt](kA), kA in [1, N/4-1] */
+    real *Xo = zalloc(N / 2);              /* DST[s_ds_to](k), odd k */
+    dst_cla(N / 2, te, SA);
+    dst_to_cla(N, to, Xo);
+    for (long kA = 1; kA < N / 4; ++kA) S[2 * kA] = SA[kA];
+    for (long k = 1; k < N / 2; k += 2) S[k] = Xo[k];
+    free(te); free(to); free(SA); free(Xo);
+}
+
+/* dst_to_cla: s_ds_to s[n], n in [1, N/4] -> X[k], odd k in [1, N/2-1].
+ * The index n = N/4 is split off (eqs qft_29, qft_29b) and its contribution
+ * added by the definition (eqs qft_29c, qft_29d); the rest (s_ds_t1o) is
+ * converted by the secant into s_ds_te (eqs qft_26, qft_28, DST form) and
+ * halved into s_A_ds_tt of periodization N/2. */
+static void dst_to_cla(long N, const real *s, real *X)
+{
+    if (N == 4) {                          /* DST definition: n = 1, k = 1 */
+        X[1] = s[1];
+        return;
+    }
+    real *t = zalloc(N / 4);               /* s_ds_te(n) = s_A_ds_tt(n), n in [1, N/4-1] */
+    for (long n = 1; n < N / 4; ++n)
+        t[n] = MUL(s[n], secant(N, n));    /* eq qft_26, DST context */
+    real *SA = zalloc(N / 4);              /* DST[s_A_ds_tt](kA) = DST[s_ds_te](2 kA), kA in [1, N/4-1] */
+    dst_cla(N / 2, t, SA);
+    const real e1 = s[N / 4];              /* DST[s_ds_e1o](1), eq qft_29d */
+    for (long k = 1; k < N / 2; k += 2) {
+        real v;                            /* DST[s_ds_t1o](k), eq qft_28 (DST form) */
+        if (k == 1) v = SA[1];
+        else if (k == N / 2 - 1) v = SA[N / 4 - 1];
+        else v = ADD(SA[(k - 1) / 2], SA[(k + 1) / 2]);
+        X[k] = (((k - 1) / 2) & 1) ? SUB(v, e1) : ADD(v, e1);   /* eq qft_29c */
+    }
+    free(t); free(SA);
+}
+
+static void rdft_cla(long N, const real *x, real *Xre, real *Xim)
+{
+    if (N == 2) {
+        Xre[0] = ADD(x[0], x[1]);
+        Xre[1] = SUB(x[0], x[1]);
+        Xim[0] = 0; Xim[1] = 0;
+        return;
+    }
+    real *c = zalloc(N / 2 + 1);
+    real *d = zalloc(N / 2);
+    c[0] = x[0];
+    c[N / 2] = x[N / 2];
+    for (long n = 1; n < N / 2; ++n) {
+        c[n] = ADD(x[n], x[N - n]);
+        d[n] = SUB(x[n], x[N - n]);
+    }
+    real *C = zalloc(N / 2 + 1);
+    real *S = zalloc(N / 2);
+    dct_cla(N, c, C);
+    dst_cla(N, d, S);
+    for (long k = 0; k <= N / 2; ++k) Xre[k] = C[k];
+    Xim[0] = 0; Xim[N / 2] = 0;
+    for (long k = 1; k < N / 2; ++k) Xim[k] = -S[k];
+    free(c); free(d); free(C); free(S);
+}
+
+static void cdft_cla(long N, const real *zre, const real *zim, real *Zre, real *Zim)
+{
+    if (N == 2) {
+        Zre[0] = ADD(zre[0], zre[1]); Zim[0] = ADD(zim[0], zim[1]);
+        Zre[1] = SUB(zre[0], zre[1]); Zim[1] = SUB(zim[0], zim[1]);
+        return;
+    }
+    real *Ar = zalloc(N / 2 + 1), *Ai = zalloc(N / 2 + 1);
+    real *Br = zalloc(N / 2 + 1), *Bi = zalloc(N / 2 + 1);
+    rdft_cla(N, zre, Ar, Ai);
+    rdft_cla(N, zim, Br, Bi);
+    for (long k = 1; k < N / 2; ++k) {
+        Zre[k]     = SUB(Ar[k], Bi[k]);
+        Zre[N - k] = ADD(Ar[k], Bi[k]);
+        Zim[k]     = ADD(Ai[k], Br[k]);
+        Zim[N - k] = SUB(Br[k], Ai[k]);
+    }
+    Zre[0] = Ar[0];         Zim[0] = Br[0];
+    Zre[N / 2] = Ar[N / 2]; Zim[N / 2] = Br[N / 2];
+    free(Ar); free(Ai); free(Br); free(Bi);
+}
+
 /* ------------------------------------------------------------- helpers */
 static int is_pow2(long n) { return n >= 2 && (n & (n - 1)) == 0; }
 
@@ -612,5 +805,127 @@ int oracle_brute_dft(long N, const double *z, double *Z)
         Z[2 * k + 1] = (double)ai;
     }
     free(cs); free(sn);
+    return 0;
+}
+
+/* ------------------------------------------------ classical QFT public API */
+/* Forward CDFT (eq qft_0A) of each row by the classical QFT of Sec. 4. */
+int oracle_cdft_cla(long N, long batch, const double *z, double *Z, int threads)
+{
+    if (!is_pow2(N) || batch < 0) return -1;
+    set_threads(threads);
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (long b = 0; b < batch; ++b) {
+        consts_t *c = consts_make(N < 8 ? 8 : N);
+        t_c = c;
+        real *zr = zalloc(N), *zi = zalloc(N), *Zr = zalloc(N), *Zi = zalloc(N);
+        for (long n = 0; n < N; ++n) { zr[n] = (real)z[(b * N + n) * 2]; zi[n] = (real)z[(b * N + n) * 2 + 1]; }
+        cdft_cla(N, zr, zi, Zr, Zi);
+        for (long k = 0; k < N; ++k) { Z[(b * N + k) * 2] = (double)Zr[k]; Z[(b * N + k) * 2 + 1] = (double)Zi[k]; }
+        free(zr); free(zi); free(Zr); free(Zi);
+        t_c = NULL;
+        consts_free(c);
+    }
+    return 0;
+}
+
+/* One classical function on its own signal type (Tab. 1): which 0 dct_cla,
+ * 1 dct_to_cla, 2 dst_cla, 3 dst_to_cla; in[] indexed by n, out[] by k
+ * (length N/2+1 each, cells outside sto_k left 0). */
+int oracle_function_cla(int which, long N, const double *in, double *out)
+{
+    long L = N / 2 + 1;
+    if (!is_pow2(N)) return -1;
+    consts_t *k = consts_make(N < 8 ? 8 : N);
+    t_c = k;
+    real *s = zalloc(L), *X = zalloc(L);
+    for (long i = 0; i < L; ++i) s[i] = (real)in[i];
+    int rc = 0;
+    switch (which) {
+    case 0: if (N < 2) rc = -1; else dct_cla(N, s, X); break;
+    case 1: if (N < 4) rc = -1; else dct_to_cla(N, s, X); break;
+    case 2: if (N < 4) rc = -1; else dst_cla(N, s, X); break;
+    case 3: if (N < 4) rc = -1; else dst_to_cla(N, s, X); break;
+    default: rc = -1;
+    }
+    for (long i = 0; i < L; ++i) out[i] = (double)X[i];
+    free(s); free(X);
+    t_c = NULL;
+    consts_free(k);
+    return rc;
+}
+
+/* Operation counts of one classical transform (kind 0 CDFT, 1 RDFT). */
+int oracle_counts_cla(int kind, long N, long long *adds, long long *muls)
+{
+    if (!is_pow2(N)) return -1;
+    consts_t *k = consts_make(N < 8 ? 8 : N);
+    t_c = k;
+    t_adds = 0; t_muls = 0;
+    real *a = zalloc(N), *b = zalloc(N), *c = zalloc(N), *d = zalloc(N);
+    int rc = 0;
+    switch (kind) {
+    case 0: cdft_cla(N, a, b, c, d); break;
+    case 1: rdft_cla(N, a, c, d); break;
+    default: rc = -1;
+    }
+    *adds = t_adds; *muls = t_muls;
+    free(a); free(b); free(c); free(d);
+    t_c = NULL;
+    consts_free(k);
+    return rc;
+}
+
+/* Constants a classical CDFT of size N uses (as oracle_constants_used). */
+long oracle_constants_used_cla(long N, unsigned char *used, int *cos_pi_4_used)
+{
+    if (!is_pow2(N) || N < 8) return -1;
+    consts_t *k = consts_make(N);
+    t_c = k;
+    real *a = zalloc(N), *b = zalloc(N), *c = zalloc(N), *d = zalloc(N);
+    cdft_cla(N, a, b, c, d);
+    long cnt = 0;
+    for (long m = 0; m <= N / 4; ++m) { used[m] = k->used[m]; cnt += k->used[m]; }
+    *cos_pi_4_used = k->cos_pi_4_used;
+    free(a); free(b); free(c); free(d);
+    t_c = NULL;
+    consts_free(k);
+    return cnt;
+}
+
+/* Reference DFT for error measurements (eq qft_44 needs a result more exact
+ * than FP64): iterative radix-2 decimation in time, every value and every
+ * twiddle factor e^{-2 pi i j / len} in long double (cosl/sinl of the exact
+ * angle).  Not part of either QFT algorithm.  One row, N a power of two. */
+int oracle_fft_ld(long N, const double *z, double *Z)
+{
+    if (!is_pow2(N) && N != 1) return -1;
+    long double *re = (long double *)malloc(sizeof(long double) * (size_t)N);
+    long double *im = (long double *)malloc(sizeof(long double) * (size_t)N);
+    for (long n = 0; n < N; ++n) { re[n] = z[2 * n]; im[n] = z[2 * n + 1]; }
+    for (long i = 1, j = 0; i < N; ++i) {      /* bit-reversal permutation */
+        long bit = N >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            long double t = re[i]; re[i] = re[j]; re[j] = t;
+            t = im[i]; im[i] = im[j]; im[j] = t;
+        }
+    }
+    for (long len = 2; len <= N; len <<= 1) {
+        for (long j = 0; j < len / 2; ++j) {
+            const long double a = -2.0L * PI_L * (long double)j / (long double)len;
+            const long double wr = cosl(a), wi = sinl(a);
+            for (long i = 0; i < N; i += len) {
+                long double *ur = &re[i + j], *ui = &im[i + j];
+                long double *vr = &re[i + j + len / 2], *vi = &im[i + j + len / 2];
+                const long double tr = *vr * wr - *vi * wi, ti = *vr * wi + *vi * wr;
+                *vr = *ur - tr; *vi = *ui - ti;
+                *ur = *ur + tr; *ui = *ui + ti;
+            }
+        }
+    }
+    for (long k = 0; k < N; ++k) { Z[2 * k] = (double)re[k]; Z[2 * k + 1] = (double)im[k]; }
+    free(re); free(im);
     return 0;
 }

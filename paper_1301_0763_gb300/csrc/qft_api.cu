@@ -109,6 +109,8 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
   p->nclasses = 0; p->classes = nullptr; p->d_offsets = nullptr; p->d_args = nullptr; p->h_args = nullptr;
   p->graph = nullptr; p->gexec = nullptr; p->graph_kernels = 0;
   p->d_status = nullptr;
+  p->wait_ns = 0;
+  p->withhold_copy = 0;
   p->channels = 0;
   p->timing = 0; p->tev_n = 0; p->tev_cap = 0; p->tev = nullptr; p->tev_kind = nullptr;
   cudaError_t e = cudaGetDevice(&p->device);
@@ -594,7 +596,9 @@ extern "C" int qft_execute(qft_plan p, int op, const void* in, void* out, void* 
   if (cur != p->device) return QFT_ERR_INVALID_ARG;
   if (p->kind == kKindFilter) return QFT_ERR_INVALID_ARG;
   if (p->classes) return exec_ragged(p, op, in, out, st);
-  return launch_plain(p, op, in, out, st);
+  rc = launch_plain(p, op, in, out, st);
+  p->withhold_copy = 0;   // the test of the timeout path is one-shot
+  return rc;
 }
 
 extern "C" int qft_execute_forward(qft_plan p, const void* in, void* out, void* stream) {
@@ -625,6 +629,22 @@ extern "C" int qft_plan_sync_status(qft_plan p) {
     }
   }
   return st;
+}
+
+extern "C" int qft_plan_set_wait_limit(qft_plan p, int64_t ns) {
+  int rc = plan_check(p);
+  if (rc != QFT_OK) return rc;
+  if (p->classes || p->kind == kKindFilter || ns < 0) return QFT_ERR_INVALID_ARG;
+  p->wait_ns = ns;
+  return QFT_OK;
+}
+
+extern "C" int qft_plan_withhold_next_copy(qft_plan p) {
+  int rc = plan_check(p);
+  if (rc != QFT_OK) return rc;
+  if (p->classes || p->kind == kKindFilter) return QFT_ERR_INVALID_ARG;
+  p->withhold_copy = 1;
+  return QFT_OK;
 }
 
 extern "C" int qft_plan_last_cuda_error(qft_plan p) {

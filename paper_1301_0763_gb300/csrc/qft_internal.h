@@ -64,6 +64,8 @@ struct qft_plan_s {
   int no_stage;               // 1: never stage input rows in shared memory
   int node_log2, node_nt;     // large-row path: largest node group (log2 cells), NODE kernel threads
   int* d_status;              // device status word (QFT_OK or QFT_ERR_TIMEOUT)
+  int64_t wait_ns;            // limit of the kernels' waits for staged copies (ns; 0: 2 s)
+  int withhold_copy;          // one-shot test: the next execute withholds each CTA's first staged copy
   int64_t channels;           // spectral-filter plans: C (batch holds B)
   // large-row path (N > 2^kMaxRowLog2): schedule, scratch copies A and B
   QftLargePlan* large_host;

@@ -20,6 +20,8 @@ struct LargeArgs {
   qc* tab;                    // C_Mt / S_Mt tables of the FINAL tasks: rows * tab_stride cells, or null
   int tab_stride;             // cells per row of the tables
   int tabS_off;               // S_Mt starts tabS_off cells after C_Mt (Mt/2 + 1)
+  uint64_t wait_ns;           // limit of the NODE kernel's wait for a staged window
+  int withhold;               // test: each NODE CTA's first window copy is not issued (its wait runs out)
 };
 
 
@@ -174,10 +176,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_
     fence_mbar_init();
   }
   __syncthreads();
+  // a withheld copy is never issued: nothing is in flight when its wait runs out
+  bool withheld = a.withhold != 0;
   if (threadIdx.x == 0 && (int64_t)blockIdx.x < items) {
     NodeItem w;
     node_item(LP, a.r, blockIdx.x, rows, kn, w);
-    issue(w, 0);
+    if (withheld) s_staged[0] = 1;
+    else issue(w, 0);
   }
   __syncthreads();
   uint32_t parity[2] = {0, 0};
@@ -192,14 +197,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_
       const uint64_t t0 = global_ns();
       bool ok = true;
       while (!mbar_try_wait(smem_u32(&mbar[b]), parity[b])) {
-        if (global_ns() - t0 > kWaitLimitNs) { ok = false; break; }
+        if (global_ns() - t0 > a.wait_ns) { ok = false; break; }
       }
       if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
           if (a.status) atomicExch(a.status, QFT_ERR_TIMEOUT);
-          // the copy in flight writes this CTA's shared memory: a second bounded wait
+          // the copy in flight writes this CTA's shared memory: a second bounded wait (long limit)
           const uint64_t t1 = global_ns();
-          while (!mbar_try_wait(smem_u32(&mbar[b]), parity[b]) && global_ns() - t1 < kWaitLimitNs) {
+          while (!withheld && !mbar_try_wait(smem_u32(&mbar[b]), parity[b]) && global_ns() - t1 < kWaitLimitNs) {
           }
         }
         __syncthreads();
@@ -210,6 +215,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_
       const qc* srcp = src_of(w);
       for (int i = threadIdx.x; i < w.pn; i += NT) cells[i] = srcp[i];
     }
+    withheld = false;
     // the next item's copy goes to the other buffer, free since the last barrier
     const int64_t next = it + gridDim.x;
     if (threadIdx.x == 0 && next < items) {
@@ -268,6 +274,8 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
   a.side_len = p->side_len;
   a.r = p->r;
   a.status = p->d_status;
+  a.wait_ns = p->wait_ns > 0 ? (uint64_t)p->wait_ns : kWaitLimitNs;
+  a.withhold = p->withhold_copy;
   // tables after the two copies; a CTA builds one row's tables, which pays off
   // only with enough rows of moderate length (the plan's large_tab)
   a.tab = p->large_tab ? a.scrB + (size_t)p->scratch_rows * 2 * p->side_len : nullptr;

@@ -178,6 +178,15 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: a bulk copy never takes that long
 
+// Limit of the wait for an item's staged copy (the plan's, 2 s by default) and
+// the plan's one-shot test of that path: with `withhold` set, every CTA arms
+// its first item's barrier without issuing the copy, so that wait runs out and
+// the kernel reports QFT_ERR_TIMEOUT with no copy in flight.
+struct QftWait {
+  uint64_t ns;
+  int withhold;
+};
+
 // Bulk prefetch of a global range into L2 (no shared memory, no completion to
 // wait for); used for the next row when it cannot be staged in shared memory.
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
@@ -250,7 +259,7 @@ __device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e
 template <class FAC, int L1, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT)
 k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int sec_stride,
-       int64_t nitems, FAC fac, int stage_off, int* status) {
+       int64_t nitems, FAC fac, int stage_off, int* status, QftWait wait) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   QftRowPlan& P = *reinterpret_cast<QftRowPlan*>(smem);
@@ -278,7 +287,9 @@ k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int
     fence_mbar_init();
   }
   __syncthreads();
-  if (staged && threadIdx.x == 0 && (int64_t)blockIdx.x < nitems) issue(blockIdx.x);
+  // a withheld copy is never issued: nothing is in flight when its wait runs out
+  bool withheld = staged && wait.withhold != 0;
+  if (staged && threadIdx.x == 0 && (int64_t)blockIdx.x < nitems && !withheld) issue(blockIdx.x);
   const int r = P.r;
   const int N = 1 << r;
   float* sec = reinterpret_cast<float*>(smem + off_sec());
@@ -297,20 +308,21 @@ k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int
       const uint64_t t0 = global_ns();
       bool ok = true;
       while (!mbar_try_wait(mb, parity)) {
-        if (global_ns() - t0 > kWaitLimitNs) { ok = false; break; }
+        if (global_ns() - t0 > wait.ns) { ok = false; break; }
       }
       if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
           atomicExch(status, QFT_ERR_TIMEOUT);
           // the copy in flight writes this CTA's shared memory: give it a
-          // second bounded wait before the CTA leaves
+          // second bounded wait (the long limit) before the CTA leaves
           const uint64_t t1 = global_ns();
-          while (!mbar_try_wait(mb, parity) && global_ns() - t1 < kWaitLimitNs) {
+          while (!withheld && !mbar_try_wait(mb, parity) && global_ns() - t1 < kWaitLimitNs) {
           }
         }
         __syncthreads();
         return;
       }
+      withheld = false;
       parity ^= 1;
       const auto io = fac.make_staged(item, stage);
       const int64_t next = item + gridDim.x;
@@ -386,7 +398,10 @@ static inline int launch_rows_nt(qft_plan p, FAC fac, int64_t items, size_t stag
   p->smem = keep;
   if (rc != QFT_OK) return rc;
   qft_time_begin(p, st, QFT_KERNEL_ROWS);
-  kern<<<p->grid, NT, smem, st>>>(p->d_plan, p->d_sec, 1, items, fac, stage_off, p->d_status);
+  QftWait w;
+  w.ns = p->wait_ns > 0 ? (uint64_t)p->wait_ns : kWaitLimitNs;
+  w.withhold = p->withhold_copy;
+  kern<<<p->grid, NT, smem, st>>>(p->d_plan, p->d_sec, 1, items, fac, stage_off, p->d_status, w);
   qft_time_end(p, st);
   return qft_set_cuda(p, cudaGetLastError());
 }

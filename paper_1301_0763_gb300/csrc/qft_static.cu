@@ -18,15 +18,22 @@
 //   g_static_sec      Gray-ordered FP32 secants of Sec. 6.1 for N = 2^20; the
 //                     table for a shorter N is its prefix of N/4 entries.
 //   g_static_plans    the launch schedules for N = 2^15 ... 2^20.
-// Every call shares these arrays.  No cell has to start at zero: each call
-// writes every scratch cell it reads before reading it, so nothing is cleared.
-// Two calls whose executions overlap (different streams, or different host
-// threads without ordering) race on the scratch and give wrong results.
+//   g_static_status   the device status word of the NODE kernel's bounded
+//                     waits (QFT_OK or QFT_ERR_TIMEOUT), read and cleared by
+//                     qft_static_scratch_sync_status.
+// Every call shares these arrays.  No scratch cell has to start at zero: each
+// call writes every scratch cell it reads before reading it, so nothing is
+// cleared.  The status word starts at zero when the module loads and is
+// cleared by every status read.  Two calls whose executions overlap (different
+// streams, or different host threads without ordering) race on the scratch and
+// give wrong results.
 //
 // Set-up: the first call on a device looks up the arrays' device addresses
 // with cudaGetSymbolAddress (checked) and fills the secant table and the
 // schedules with blocking cudaMemcpyToSymbol copies; make that first call
-// before any stream capture begins.  Later calls only launch kernels.
+// before any stream capture begins.  Later calls only launch kernels.  The
+// set-up is not repeated after cudaDeviceReset (which discards the arrays'
+// contents): do not use the entry point across a device reset.
 #include <string.h>
 
 #include <mutex>
@@ -46,6 +53,7 @@ constexpr int kStaticMaxDevices = 64;
 static __device__ __align__(256) qc_storage g_static_scratch[kStaticScratchBytes / sizeof(qc_storage)];
 static __device__ __align__(256) float g_static_sec[kStaticSecEntries];
 static __device__ __align__(256) QftLargePlan g_static_plans[kStaticPlans];
+static __device__ __align__(256) int g_static_status;
 
 // host copies (device independent), built once
 static float g_host_sec[kStaticSecEntries];
@@ -58,6 +66,7 @@ struct StaticDev {
   qc_storage* scratch;
   float* sec;
   QftLargePlan* plans;
+  int* status;
 };
 static StaticDev g_dev[kStaticMaxDevices];
 static std::mutex g_static_mu;
@@ -87,6 +96,7 @@ static int device_setup(int dev, StaticDev* out) {
     if (cudaGetSymbolAddress((void**)&d.scratch, g_static_scratch) != cudaSuccess) return QFT_ERR_CUDA;
     if (cudaGetSymbolAddress((void**)&d.sec, g_static_sec) != cudaSuccess) return QFT_ERR_CUDA;
     if (cudaGetSymbolAddress((void**)&d.plans, g_static_plans) != cudaSuccess) return QFT_ERR_CUDA;
+    if (cudaGetSymbolAddress((void**)&d.status, g_static_status) != cudaSuccess) return QFT_ERR_CUDA;
     if (cudaMemcpyToSymbol(g_static_sec, g_host_sec, sizeof(g_host_sec)) != cudaSuccess) return QFT_ERR_CUDA;
     if (cudaMemcpyToSymbol(g_static_plans, g_host_plans, sizeof(g_host_plans)) != cudaSuccess) return QFT_ERR_CUDA;
     d.ready = true;
@@ -134,6 +144,7 @@ extern "C" int qft_execute_static_scratch(int64_t n, int64_t batch, int op, cons
   p.large_host = &g_host_plans[idx];
   p.d_large = d.plans + idx;
   p.scratch = d.scratch;
+  p.d_status = d.status;
   p.side_len = qft_side_len((int)n);
   const int64_t per_row = 2 * 2 * (int64_t)p.side_len * (int64_t)sizeof(qc_storage) +
                           (int64_t)qft_lib::large_tab_cells((int)n, qft_lib::kLargeMinLF) * (int64_t)sizeof(qc_storage);
@@ -141,17 +152,24 @@ extern "C" int qft_execute_static_scratch(int64_t n, int64_t batch, int op, cons
   if (rows > batch) rows = batch;
   if (rows > 65535) rows = 65535;
   p.scratch_rows = rows;
+  // the FINAL tasks read per-row C/S tables when a chunk holds enough rows (the
+  // same rule as a plan's); either way the result is the same bits
+  p.large_tab = rows >= 64 ? 1 : 0;
+  return exec_c2c<StC64>(&p, op, in, out, static_cast<cudaStream_t>(stream));
+}
 
-  FacC2C<StC64> f;
-  f.in = static_cast<const qc*>(in);
-  f.out = static_cast<qc*>(out);
-  f.N = (int)n;
-  f.scale = 1.f; f.scaled = 0;
-  switch (op) {
-  case QFT_OP_FORWARD: f.in_op = QFT_LANE_ID; f.out_op = QFT_LANE_ID; break;
-  case QFT_OP_INVERSE: f.in_op = QFT_LANE_SWAP; f.out_op = QFT_LANE_SWAP; f.scale = 1.f / (float)n; f.scaled = 1; break;
-  case QFT_OP_FORWARD_ADJOINT: f.in_op = QFT_LANE_CONJ; f.out_op = QFT_LANE_CONJ; break;
-  default: f.in_op = QFT_LANE_ID; f.out_op = QFT_LANE_ID; f.scale = 1.f / (float)n; f.scaled = 1; break;
+extern "C" int qft_static_scratch_sync_status(void* stream) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QFT_ERR_CUDA;
+  if (dev < 0 || dev >= kStaticMaxDevices) return QFT_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_dev[dev].ready) return QFT_OK;   // no call has run on this device
   }
-  return launch_large<FacC2C<StC64>>(&p, f, batch, static_cast<cudaStream_t>(stream));
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return QFT_ERR_CUDA;
+  int st = 0;
+  const int zero = 0;
+  if (cudaMemcpyFromSymbol(&st, g_static_status, sizeof(int)) != cudaSuccess) return QFT_ERR_CUDA;
+  if (cudaMemcpyToSymbol(g_static_status, &zero, sizeof(int)) != cudaSuccess) return QFT_ERR_CUDA;
+  return st;
 }

@@ -68,6 +68,9 @@ def load_library(path: str | None = None):
         lib.qft_filter_forward.argtypes = [vp, vp, vp, vp, vp]
         lib.qft_filter_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.qft_execute_static_scratch.argtypes = [i64, i64, ci, vp, vp, vp]
+        lib.qft_static_scratch_sync_status.argtypes = [vp]
+        lib.qft_plan_set_wait_limit.argtypes = [vp, i64]
+        lib.qft_plan_withhold_next_copy.argtypes = [vp]
         lib.qft_plan_schedule.argtypes = [vp, ctypes.POINTER(ci)]
         lib.qft_plan_set_schedule.argtypes = [vp, ctypes.POINTER(ci)]
         lib.qft_plan_time_launches.argtypes = [vp, ci]
@@ -145,6 +148,15 @@ class Plan:
 
     def sync_status(self) -> int:
         return int(self.lib.qft_plan_sync_status(self.handle))
+
+    def set_wait_limit(self, ns: int):
+        """Limit of the kernels' bounded waits for staged copies (0: the default 2 s)."""
+        _check(self.lib.qft_plan_set_wait_limit(self.handle, int(ns)), "qft_plan_set_wait_limit")
+
+    def withhold_next_copy(self):
+        """Test of the timeout path: the next execute withholds each CTA's first
+        staged copy, so its bounded wait runs out (see qft_plan_withhold_next_copy)."""
+        _check(self.lib.qft_plan_withhold_next_copy(self.handle), "qft_plan_withhold_next_copy")
 
     def destroy(self):
         if self.handle and self.handle.value:

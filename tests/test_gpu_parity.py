@@ -138,12 +138,21 @@ def _bf16_round(x32):
     return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
 
 
-@pytest.mark.parametrize("lg", [4, 10, 13])
+@pytest.mark.parametrize("lg", [4, 10, 13, 15, 16])
 @pytest.mark.parametrize("half", ["f16", "bf16"])
-def test_half_storage(q, lg, half):
+@pytest.mark.parametrize("dist", ["uniform", "student_t"])
+def test_half_storage(q, lg, half, dist):
+    """FP16 / BF16 storage, FP32 arithmetic: the stored result equals the FP32
+    oracle of the rounded input, rounded to the storage type, bit for bit.
+    N = 2^15 and 2^16 run the large-row path with half-precision IO; inputs are
+    uniform[-1, 1] and Student-t(3) scaled per row to max |x| = 1."""
     N = 1 << lg
-    rows = 21
-    z = inputs.uniform_complex(rows, N, seed=10).view(np.float32).reshape(rows, N, 2)
+    rows = 21 if lg <= 13 else 4
+    if dist == "uniform":
+        zc = inputs.uniform_complex(rows, N, seed=10)
+    else:
+        zc = inputs.student_t_complex(rows, N, seed=11).astype(np.complex64)
+    z = zc.view(np.float32).reshape(rows, N, 2)
     if half == "f16":
         zin = z.astype(np.float16)
         zf = zin.astype(np.float32)
@@ -163,6 +172,7 @@ def test_half_storage(q, lg, half):
     ref = orc.cdft(zc, fp32=True).astype(np.complex64).view(np.float32).reshape(rows, N, 2)
     ref_bits = ref.astype(np.float16).view(np.uint16) if half == "f16" else _bf16_round(ref)
     assert np.array_equal(ob, ref_bits)
+    p.destroy()
 
 
 # ------------------------------------------------------------- large rows
@@ -509,3 +519,138 @@ def test_fft_host_pipelined_matches_device_fft(q):
     torch.cuda.synchronize()
     ref = q.fft(gpu(z)).cpu().numpy()
     assert bits_equal(out.numpy(), ref)
+
+
+# ------------------------------------------------- bounded waits (failure path)
+@pytest.mark.parametrize("lg", [12, 16])
+def test_bounded_wait_times_out_and_recovers(q, lg):
+    """The staged input copies are waited for with a bounded wait.  The plan's
+    one-shot test withholds each CTA's first copy (a barrier that nothing
+    completes): the wait runs out after the plan's short limit, the kernel
+    returns early and the status word reads QFT_ERR_TIMEOUT, with nothing in
+    flight and no fault.  The next execute, at the same limit, gives the bits
+    of the oracle and a clear status word.  N = 2^12 tests the row kernel,
+    N = 2^16 the NODE kernel of the large-row path."""
+    import time
+    N = 1 << lg
+    rows = 64 if lg == 12 else 6
+    z = inputs.normal_complex(rows, N, seed=71)
+    p = q.Plan(N, rows)
+    x = gpu(z)
+    y = torch.zeros_like(x)
+    p.set_wait_limit(200_000)           # 0.2 ms
+    p.withhold_next_copy()
+    t0 = time.time()
+    p.execute(q.OP_FORWARD, x, y)
+    assert p.sync_status() == -7        # QFT_ERR_TIMEOUT
+    assert time.time() - t0 < 1.5       # no long drain: nothing was in flight
+    p.execute(q.OP_FORWARD, x, y)
+    assert p.sync_status() == 0
+    assert bits_equal(y.cpu().numpy(), orc.cdft(z, fp32=True).astype(np.complex64))
+    with pytest.raises(q.QFTError):
+        p.set_wait_limit(-1)
+    p.destroy()
+
+
+# ------------------------------------------------------ autograd wrappers
+@pytest.mark.parametrize("lg", [4, 10, 15])
+def test_autograd_fft_ifft(q, lg):
+    """torch.autograd through qft.fft / qft.ifft: x.grad = F^H g and (F/N) g,
+    bit for bit against the FP32 oracle adjoints, within 1e-5 of FP64."""
+    N = 1 << lg
+    rows = 5
+    z = inputs.normal_complex(rows, N, seed=81)
+    g = inputs.normal_complex(rows, N, seed=82)
+    x = gpu(z).requires_grad_(True)
+    q.fft(x).backward(gpu(g))
+    gx = x.grad.cpu().numpy()
+    assert bits_equal(gx, orc.cdft_adjoint(g, fp32=True).astype(np.complex64))
+    assert rel_rows(gx.astype(np.complex128), orc.cdft_adjoint(g)).max() < TOL
+    x2 = gpu(z).requires_grad_(True)
+    q.ifft(x2).backward(gpu(g))
+    gx2 = x2.grad.cpu().numpy()
+    assert bits_equal(gx2, (orc.cdft(g, fp32=True) / N).astype(np.complex64))
+    assert rel_rows(gx2.astype(np.complex128), orc.cdft(g) / N).max() < TOL
+
+
+@pytest.mark.parametrize("lg", [3, 10, 15])
+def test_autograd_rfft_irfft(q, lg):
+    """torch.autograd through qft.rfft / qft.irfft: the R2C and C2R adjoints,
+    bit for bit against the FP32 oracle's rdft_adjoint / irdft_adjoint."""
+    N = 1 << lg
+    H = N // 2 + 1
+    rows = 4
+    x = inputs.normal_real(rows, N, seed=83)
+    g = inputs.normal_complex(rows, H, seed=84)
+    xt = gpu(x).requires_grad_(True)
+    q.rfft(xt).backward(gpu(g))
+    gx = xt.grad.cpu().numpy()
+    assert bits_equal(gx, orc.rdft_adjoint(g, N, fp32=True).astype(np.float32))
+    ref = orc.rdft_adjoint(g, N)
+    assert np.linalg.norm(gx - ref) / np.linalg.norm(ref) < TOL
+    Y = gpu(inputs.normal_complex(rows, H, seed=85)).requires_grad_(True)
+    u = inputs.normal_real(rows, N, seed=86)
+    q.irfft(Y, N).backward(gpu(u))
+    gY = Y.grad.cpu().numpy()
+    assert bits_equal(gY, orc.irdft_adjoint(u, fp32=True).astype(np.complex64))
+
+
+def test_autograd_central_differences():
+    """The four wrappers' gradients against central differences of the loss
+    L(x) = sum Re(conj(w) * T(x)) evaluated by the GPU transform itself, N = 16.
+    L is linear in x, so a central difference with a step of 0.25 is exact up
+    to FP32 rounding of the two evaluations."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1301_0763_gb300 import qft as q
+    N, rows, eps = 16, 2, 0.25
+    cases = [
+        ("fft", lambda t: q.fft(t), inputs.normal_complex(rows, N, seed=90), inputs.normal_complex(rows, N, seed=91)),
+        ("ifft", lambda t: q.ifft(t), inputs.normal_complex(rows, N, seed=92), inputs.normal_complex(rows, N, seed=93)),
+        ("rfft", lambda t: q.rfft(t), inputs.normal_real(rows, N, seed=94),
+         inputs.normal_complex(rows, N // 2 + 1, seed=95)),
+        ("irfft", lambda t: q.irfft(t, N), inputs.normal_complex(rows, N // 2 + 1, seed=96),
+         inputs.normal_real(rows, N, seed=97)),
+    ]
+    for name, f, x0, w in cases:
+        wt = gpu(w)
+
+        def loss(t):
+            y = f(t)
+            return (torch.conj(wt) * y).real.sum() if y.is_complex() else (wt * y).sum()
+
+        xt = gpu(x0).requires_grad_(True)
+        loss(xt).backward()
+        grad = xt.grad.detach()
+        flat = gpu(x0).reshape(-1)
+        real_view = torch.view_as_real(flat).reshape(-1) if flat.is_complex() else flat
+        gview = (torch.view_as_real(grad.reshape(-1)).reshape(-1) if grad.is_complex() else grad.reshape(-1))
+        with torch.no_grad():
+            for j in range(real_view.numel()):
+                old = real_view[j].item()
+                real_view[j] = old + eps
+                lp = loss(flat.reshape(x0.shape)).item()
+                real_view[j] = old - eps
+                lm = loss(flat.reshape(x0.shape)).item()
+                real_view[j] = old
+                fd = (lp - lm) / (2 * eps)
+                assert abs(fd - gview[j].item()) <= 1e-4 * (1 + abs(fd)), (name, j, fd, gview[j].item())
+
+
+def test_autograd_fft_complex32_storage(q):
+    """qft.fft on complex32 (FP16 pairs) storage: the backward pass runs the
+    FP16-storage adjoint; x.grad equals the FP32 oracle adjoint of the FP16 g,
+    rounded to FP16, bit for bit."""
+    N, rows = 1024, 3
+    z = inputs.uniform_complex(rows, N, seed=87).view(np.float32).reshape(rows, N, 2).astype(np.float16)
+    g = inputs.uniform_complex(rows, N, seed=88).view(np.float32).reshape(rows, N, 2).astype(np.float16)
+    x = torch.from_numpy(z).cuda().view(torch.complex32).reshape(rows, N).requires_grad_(True)
+    gt = torch.from_numpy(g).cuda().view(torch.complex32).reshape(rows, N)
+    X = q.fft(x)
+    assert X.dtype == torch.complex32
+    X.backward(gt)
+    gx = x.grad.detach().cpu().view(torch.int16).numpy().view(np.uint16).reshape(rows, N, 2)
+    gf = g.astype(np.float32)
+    gc = gf[..., 0].astype(np.float64) + 1j * gf[..., 1]
+    ref = orc.cdft_adjoint(gc, fp32=True).astype(np.complex64).view(np.float32).reshape(rows, N, 2)
+    assert np.array_equal(gx, ref.astype(np.float16).view(np.uint16))

@@ -182,23 +182,6 @@ def test_function_equals_pruned_definition(name, N):
     assert (len(sto_n), len(sto_k)) == ln_lk[name]
 
 
-def test_ln_lk_conservation():
-    """eqs qft_42/43 and 'similar relations hold for any other function' (Sec. 6.1):
-    each improved function's children carry exactly its ln and lk."""
-    for N in [2 ** r for r in range(4, 14)]:
-        ln = {"dc_tt": N // 2 + 1, "dc_ot": N // 4, "dc_oo": N // 8,
-              "ds_tt": N // 2 - 1, "ds_ot": N // 4, "ds_oo": N // 8}
-        # dct(N) -> dct(N/2) + dct_ot(N)
-        assert ln["dc_tt"] == (N // 4 + 1) + N // 4
-        # dct_ot(N) -> dct_ot(N/2) + dct_oo(N)
-        assert ln["dc_ot"] == N // 8 + ln["dc_oo"]
-        # dct_oo(N) -> dct_ot(N/2) [-> dct_ot(N/4) + dct_oo(N/2)]
-        assert ln["dc_oo"] == N // 16 + N // 16
-        # dst(N) -> dst(N/2) + dst_ot(N)
-        assert ln["ds_tt"] == (N // 4 - 1) + N // 4
-        assert ln["ds_ot"] == N // 8 + ln["ds_oo"]
-
-
 # ------------------------------------------------------------ op-count pins
 def _golden_costs():
     rows = []
