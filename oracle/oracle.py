@@ -22,9 +22,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qft_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_qft_oracle.so")
 _LIB32_PATH = os.path.join(_HERE, "_qft_oracle_f32.so")
+_LIB32C_PATH = os.path.join(_HERE, "_qft_oracle_f32c.so")
+FLAGS32 = ("-DORACLE_REAL=float", "-ffp-contract=off")
+FLAGS32C = ("-DORACLE_REAL=float", "-DORACLE_COMPENSATED", "-ffp-contract=off")
 _lock = threading.Lock()
 _lib = None
 _lib32 = None
+_lib32c = None
 
 
 def build(force: bool = False, out: str | None = None, extra_flags=()) -> str:
@@ -69,6 +73,7 @@ def _declare(lib):
     lib.oracle_fft_ld.argtypes = [L, dp, dp]
     lib.oracle_max_threads.restype = ctypes.c_int
     lib.oracle_is_float.restype = ctypes.c_int
+    lib.oracle_is_compensated.restype = ctypes.c_int
     return lib
 
 
@@ -80,15 +85,21 @@ def _load():
         return _lib
 
 
-def _load32():
+def _load32(comp: bool = True):
     """The same oracle source built with every arithmetic value in FP32
     (-DORACLE_REAL=float): the recursion of Sec. 5 evaluated in single
-    precision, operation by operation, with constants rounded once to FP32."""
-    global _lib32
+    precision, operation by operation, with constants rounded once to FP32.
+    comp=True (the default) adds -DORACLE_COMPENSATED: the class trees of the
+    largest periodizations (N >= 2^16 only) run on compensated pairs, as the
+    library does by default; comp=False is the plain FP32 evaluation."""
+    global _lib32, _lib32c
     with _lock:
+        if comp:
+            if _lib32c is None:
+                _lib32c = _declare(ctypes.CDLL(build(out=_LIB32C_PATH, extra_flags=FLAGS32C)))
+            return _lib32c
         if _lib32 is None:
-            path = build(out=_LIB32_PATH, extra_flags=("-DORACLE_REAL=float", "-ffp-contract=off"))
-            _lib32 = _declare(ctypes.CDLL(path))
+            _lib32 = _declare(ctypes.CDLL(build(out=_LIB32_PATH, extra_flags=FLAGS32)))
         return _lib32
 
 
@@ -110,69 +121,69 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
-def cdft(z, threads: int = 0, fp32: bool = False) -> np.ndarray:
+def cdft(z, threads: int = 0, fp32: bool = False, comp: bool = True) -> np.ndarray:
     """Forward DFT (eq qft_0A) of each row of z [..., N] by the improved QFT.
     fp32=True evaluates the same recursion in single precision."""
     z = _c128(z)
     N = z.shape[-1]
     batch = z.size // N if N else 0
     out = np.empty_like(z)
-    lib = _load32() if fp32 else _load()
+    lib = _load32(comp) if fp32 else _load()
     _check(lib.oracle_cdft(N, batch, _dp(z.view(np.float64)), _dp(out.view(np.float64)), threads))
     return out
 
 
-def icdft(X, threads: int = 0, fp32: bool = False) -> np.ndarray:
+def icdft(X, threads: int = 0, fp32: bool = False, comp: bool = True) -> np.ndarray:
     """Inverse DFT, 1/N scaled: swap(cdft(swap(X)))/N."""
     X = _c128(X)
     N = X.shape[-1]
     out = np.empty_like(X)
-    lib = _load32() if fp32 else _load()
+    lib = _load32(comp) if fp32 else _load()
     _check(lib.oracle_icdft(N, X.size // N, _dp(X.view(np.float64)), _dp(out.view(np.float64)), threads))
     return out
 
 
-def rdft(x, threads: int = 0, fp32: bool = False) -> np.ndarray:
+def rdft(x, threads: int = 0, fp32: bool = False, comp: bool = True) -> np.ndarray:
     """Forward real DFT [..., N] -> [..., N/2+1] (rdft_cla of Sec. 4.2)."""
     x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
     N = x.shape[-1]
     out = np.empty(x.shape[:-1] + (N // 2 + 1,), dtype=np.complex128)
-    lib = _load32() if fp32 else _load()
+    lib = _load32(comp) if fp32 else _load()
     _check(lib.oracle_rdft(N, x.size // N, _dp(x), _dp(out.view(np.float64)), threads))
     return out
 
 
-def irdft(Y, N: int, threads: int = 0, fp32: bool = False) -> np.ndarray:
+def irdft(Y, N: int, threads: int = 0, fp32: bool = False, comp: bool = True) -> np.ndarray:
     """Inverse real DFT [..., N/2+1] -> [..., N] (1/N scaled) through DCT-0/DST-0."""
     Y = _c128(Y)
     assert Y.shape[-1] == N // 2 + 1
     out = np.empty(Y.shape[:-1] + (N,), dtype=np.float64)
-    lib = _load32() if fp32 else _load()
+    lib = _load32(comp) if fp32 else _load()
     _check(lib.oracle_irdft(N, Y.size // (N // 2 + 1), _dp(Y.view(np.float64)), _dp(out), threads))
     return out
 
 
-def rdft_adjoint(G, N: int, threads: int = 0, fp32: bool = False) -> np.ndarray:
+def rdft_adjoint(G, N: int, threads: int = 0, fp32: bool = False, comp: bool = True) -> np.ndarray:
     """Adjoint of ``rdft`` for the real inner product on (Re, Im) pairs."""
     G = _c128(G)
     out = np.empty(G.shape[:-1] + (N,), dtype=np.float64)
-    lib = _load32() if fp32 else _load()
+    lib = _load32(comp) if fp32 else _load()
     _check(lib.oracle_rdft_adjoint(N, G.size // (N // 2 + 1), _dp(G.view(np.float64)), _dp(out), threads))
     return out
 
 
-def cdft_adjoint(g, threads: int = 0, fp32: bool = False) -> np.ndarray:
+def cdft_adjoint(g, threads: int = 0, fp32: bool = False, comp: bool = True) -> np.ndarray:
     """Adjoint of the forward CDFT: F^H g = conj(F conj(g))."""
-    return np.conj(cdft(np.conj(_c128(g)), threads, fp32=fp32))
+    return np.conj(cdft(np.conj(_c128(g)), threads, fp32=fp32, comp=comp))
 
 
-def irdft_adjoint(g, threads: int = 0, fp32: bool = False) -> np.ndarray:
+def irdft_adjoint(g, threads: int = 0, fp32: bool = False, comp: bool = True) -> np.ndarray:
     """Adjoint of ``irdft`` (1/N scaled C2R): (w_k/N) rdft(g), w = 1 at k=0,N/2, 2 elsewhere;
     the imaginary parts at k = 0 and N/2 do not reach the output, so their gradient is 0.
     With fp32=True the spectrum and the (power-of-two) weights are applied in FP32."""
     g = np.asarray(g, dtype=np.float64)
     N = g.shape[-1]
-    Y = rdft(g, threads, fp32=fp32)
+    Y = rdft(g, threads, fp32=fp32, comp=comp)
     w = np.full(N // 2 + 1, 2.0 / N)
     w[0] = w[-1] = 1.0 / N
     Y = Y * w
@@ -181,27 +192,27 @@ def irdft_adjoint(g, threads: int = 0, fp32: bool = False) -> np.ndarray:
     return Y
 
 
-def dct0(c, fp32: bool = False) -> np.ndarray:
+def dct0(c, fp32: bool = False, comp: bool = True) -> np.ndarray:
     """DCT-0 of periodization N = 2 (len - 1) of each row of c [..., N/2+1]
     (eq qft_0B, the dct recursion of Sec. 5); fp32=True evaluates it in FP32."""
     c = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
     N = 2 * (c.shape[-1] - 1)
     out = np.empty_like(c)
-    lib = _load32() if fp32 else _load()
+    lib = _load32(comp) if fp32 else _load()
     rows_in, rows_out = c.reshape(-1, N // 2 + 1), out.reshape(-1, N // 2 + 1)
     for i in range(rows_in.shape[0]):
         _check(lib.oracle_dct0(N, _dp(rows_in[i]), _dp(rows_out[i])))
     return out
 
 
-def dst0(d, N: int, fp32: bool = False) -> np.ndarray:
+def dst0(d, N: int, fp32: bool = False, comp: bool = True) -> np.ndarray:
     """DST-0 of periodization N (eq qft_0C, the dst recursion of Sec. 5) of each
     row of d [..., N/2+1] indexed by n (the ends n = 0, N/2 are ignored; the
     output is 0 there); fp32=True evaluates it in FP32."""
     d = np.ascontiguousarray(np.asarray(d, dtype=np.float64))
     assert d.shape[-1] == N // 2 + 1
     out = np.empty_like(d)
-    lib = _load32() if fp32 else _load()
+    lib = _load32(comp) if fp32 else _load()
     rows_in, rows_out = d.reshape(-1, N // 2 + 1), out.reshape(-1, N // 2 + 1)
     for i in range(rows_in.shape[0]):
         _check(lib.oracle_dst0(N, _dp(rows_in[i]), _dp(rows_out[i])))
@@ -264,7 +275,7 @@ def cdft_cla(z, threads: int = 0, fp32: bool = False) -> np.ndarray:
     z = _c128(z)
     N = z.shape[-1]
     out = np.empty_like(z)
-    lib = _load32() if fp32 else _load()
+    lib = _load32(False) if fp32 else _load()
     _check(lib.oracle_cdft_cla(N, z.size // N if N else 0, _dp(z.view(np.float64)), _dp(out.view(np.float64)),
                                threads))
     return out

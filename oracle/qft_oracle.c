@@ -131,6 +131,11 @@ static void dct_oo(long N, const real *s, real *X);
 static void dst(long N, const real *d, real *S);
 static void dst_ot(long N, const real *s, real *X);
 static void dst_oo(long N, const real *s, real *X);
+#ifdef ORACLE_COMPENSATED
+static int class_compensated(long M);
+static void dct_ot_comp(long N, const real *s, real *X);
+static void dst_ot_comp(long N, const real *s, real *X);
+#endif
 
 /* dct: input s_dc_tt, c[n] for n in [0, N/2]; output C[k], k in [0, N/2].
  * Sec. 5.2.1: even/odd time separation (Sec. 3.1, eqs qft_5A/5B), then the
@@ -151,6 +156,9 @@ static void dct(long N, const real *c, real *C)
     real *E = zalloc(N / 4 + 1);           /* DCT[s_A_dc_tt](k), k in [0,N/4]   */
     real *O = zalloc(N / 4);               /* DCT[s_dc_ot](k),   k in [0,N/4-1] */
     dct(N / 2, e, E);
+#ifdef ORACLE_COMPENSATED
+    if (class_compensated(N)) dct_ot_comp(N, so, O); else
+#endif
     dct_ot(N, so, O);
     for (long k = 0; k < N / 4; ++k) {
         C[k] = ADD(E[k], O[k]);            /* eq qft_5C */
@@ -222,6 +230,9 @@ static void dst(long N, const real *d, real *S)
     real *E = zalloc(N / 4);               /* DST[s_A_ds_tt](k), k in [1,N/4-1] */
     real *O = zalloc(N / 4 + 1);           /* DST[s_ds_ot](k),   k in [1,N/4]   */
     dst(N / 2, e, E);
+#ifdef ORACLE_COMPENSATED
+    if (class_compensated(N)) dst_ot_comp(N, so, O); else
+#endif
     dst_ot(N, so, O);
     for (long k = 1; k < N / 4; ++k) {
         S[k] = ADD(E[k], O[k]);            /* eq qft_5C, DST form */
@@ -271,6 +282,143 @@ static void dst_oo(long N, const real *s, real *X)
         X[2 * j + 1] = ADD(Z[j], Z[j + 1]);/* eq qft_38C, DST context */
     free(t); free(Z);
 }
+
+/* ====================================== compensated FP32 evaluation
+ * With -DORACLE_COMPENSATED (and ORACLE_REAL=float) this oracle evaluates the
+ * class trees whose periodization is large the way the library does by
+ * default.  The FP32 error of the improved QFT comes from the secant
+ * conversion (eq qft_38A): near n = N/4 the factor 1/(2 cos(2 pi n/N)) grows
+ * like N/(4 pi), every value below it in the tree is that much larger, and
+ * the neighbour adds of eqs qft_38B/C cancel the excess, leaving the rounding
+ * errors.  So the dct_ot (dst_ot) tree of each of the J largest classes --
+ * the odd-time child of dct(M) (dst(M)) for M >= Nroot / 2^(J-1), with
+ * J = max(0, floor((log2 Nroot - 14) / 2)) -- runs on unevaluated pairs
+ * v = h + l of FP32 numbers, h being exactly the plain FP32 value:
+ *   add:  s = ah + bh; z = s - ah; e = (ah - (s - z)) + (bh - z)   (TwoSum,
+ *         Knuth, TAOCP vol. 2: s + e = ah + bh exactly); l = (al + bl) + e
+ *   sub:  add of (-bh, -bl)
+ *   mul by a constant c:  p = ah c; e = fma(ah, c, -p) (the exact product
+ *         error, Ogita, Rump and Oishi 2005); l = fma(al, c, e)
+ * and each class output is rounded once, h + l, before the combines of
+ * eqs qft_5C-6.  The constants are the plain FP32 ones; the operations and
+ * their order are the recursion's, so the counters are unchanged. */
+#ifdef ORACLE_COMPENSATED
+typedef struct { real h, l; } pair;
+
+static inline real fma_r(real a, real b, real c)
+{
+    return sizeof(real) == sizeof(float) ? (real)fmaf((float)a, (float)b, (float)c) : (real)fma(a, b, c);
+}
+static inline pair PADD(pair a, pair b)
+{
+    t_adds++;
+    const real s = a.h + b.h;
+    const real z = s - a.h;
+    const real e = (a.h - (s - z)) + (b.h - z);
+    pair r = {s, (a.l + b.l) + e};
+    return r;
+}
+static inline pair PSUB(pair a, pair b)
+{
+    pair nb = {-b.h, -b.l};
+    return PADD(a, nb);
+}
+static inline pair PMUL(pair a, real c)
+{
+    t_muls++;
+    const real p = a.h * c;
+    const real e = fma_r(a.h, c, -p);
+    pair r = {p, fma_r(a.l, c, e)};
+    return r;
+}
+static pair *palloc(long n) { return (pair *)calloc((size_t)(n > 0 ? n : 1), sizeof(pair)); }
+
+/* number of compensated classes of a root transform of length Nroot */
+static int comp_classes(long Nroot)
+{
+    int r = 0;
+    while ((1L << r) < Nroot) ++r;
+    return r >= 16 ? (r - 14) / 2 : 0;
+}
+static int class_compensated(long M)
+{
+    const int J = comp_classes(t_c->Nroot);
+    return J > 0 && M >= (t_c->Nroot >> (J - 1));
+}
+
+static void dct_ot_p(long N, const pair *s, pair *X);
+static void dct_oo_p(long N, const pair *s, pair *X);
+static void dst_ot_p(long N, const pair *s, pair *X);
+static void dst_oo_p(long N, const pair *s, pair *X);
+
+/* dct_ot / dct_oo / dst_ot / dst_oo of Sec. 5 on pairs (same steps) */
+static void dct_ot_p(long N, const pair *s, pair *X)
+{
+    if (N == 4) { X[0] = s[1]; return; }
+    pair *e = palloc(N / 4), *o = palloc(N / 4), *Xe = palloc(N / 8), *Xo = palloc(N / 4);
+    for (long n = 1; n < N / 4; n += 2) {
+        e[n] = PADD(s[n], s[N / 2 - n]);   /* eq qft_1 */
+        o[n] = PSUB(s[n], s[N / 2 - n]);   /* eq qft_2 */
+    }
+    dct_ot_p(N / 2, e, Xe);
+    dct_oo_p(N, o, Xo);
+    for (long j = 0; j < N / 8; ++j) X[2 * j] = Xe[j];
+    for (long k = 1; k < N / 4; k += 2) X[k] = Xo[k];
+    free(e); free(o); free(Xe); free(Xo);
+}
+static void dct_oo_p(long N, const pair *s, pair *X)
+{
+    if (N == 8) { X[1] = PMUL(s[1], cos_pi_4()); return; }
+    pair *t = palloc(N / 4), *Y = palloc(N / 8);
+    for (long n = 1; n < N / 4; n += 2) t[n] = PMUL(s[n], secant(N, n));   /* eq qft_38A */
+    dct_ot_p(N / 2, t, Y);
+    for (long j = 0; j + 1 < N / 8; ++j) X[2 * j + 1] = PADD(Y[j], Y[j + 1]);   /* eq qft_38C */
+    X[N / 4 - 1] = Y[N / 8 - 1];                                               /* eq qft_38B */
+    free(t); free(Y);
+}
+static void dst_ot_p(long N, const pair *s, pair *X)
+{
+    if (N == 4) { X[1] = s[1]; return; }
+    pair *e = palloc(N / 4), *o = palloc(N / 4), *Xe = palloc(N / 8 + 1), *Xo = palloc(N / 4);
+    for (long n = 1; n < N / 4; n += 2) {
+        e[n] = PSUB(s[n], s[N / 2 - n]);
+        o[n] = PADD(s[n], s[N / 2 - n]);
+    }
+    dst_ot_p(N / 2, e, Xe);
+    dst_oo_p(N, o, Xo);
+    for (long j = 1; j <= N / 8; ++j) X[2 * j] = Xe[j];
+    for (long k = 1; k < N / 4; k += 2) X[k] = Xo[k];
+    free(e); free(o); free(Xe); free(Xo);
+}
+static void dst_oo_p(long N, const pair *s, pair *X)
+{
+    if (N == 8) { X[1] = PMUL(s[1], cos_pi_4()); return; }
+    pair *t = palloc(N / 4), *Z = palloc(N / 8 + 1);
+    for (long n = 1; n < N / 4; n += 2) t[n] = PMUL(s[n], secant(N, n));
+    dst_ot_p(N / 2, t, Z);
+    X[1] = Z[1];
+    for (long j = 1; j < N / 8; ++j) X[2 * j + 1] = PADD(Z[j], Z[j + 1]);
+    free(t); free(Z);
+}
+
+/* a class tree on pairs: plain input (l = 0), each output rounded once */
+static void dct_ot_comp(long N, const real *s, real *X)
+{
+    pair *sp = palloc(N / 2), *Xp = palloc(N / 4);
+    for (long n = 1; n < N / 2; n += 2) sp[n].h = s[n];
+    dct_ot_p(N, sp, Xp);
+    for (long k = 0; k < N / 4; ++k) X[k] = Xp[k].h + Xp[k].l;
+    free(sp); free(Xp);
+}
+static void dst_ot_comp(long N, const real *s, real *X)
+{
+    pair *sp = palloc(N / 2), *Xp = palloc(N / 4 + 1);
+    for (long n = 1; n < N / 2; n += 2) sp[n].h = s[n];
+    dst_ot_p(N, sp, Xp);
+    for (long k = 1; k <= N / 4; ++k) X[k] = Xp[k].h + Xp[k].l;
+    free(sp); free(Xp);
+}
+#endif
 
 /* rdft (= rdft_cla, Sec. 4.2): input s_re_tt x[n], n in [0, N-1]; output
  * X[k], k in [0, N/2] as real and imaginary parts. */
@@ -532,6 +680,15 @@ static void set_threads(int threads)
  * (re, im) as doubles.  Return 0 on success, -1 on a bad argument. */
 
 int oracle_is_float(void) { return sizeof(real) == sizeof(float); }
+
+int oracle_is_compensated(void)
+{
+#ifdef ORACLE_COMPENSATED
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 int oracle_max_threads(void)
 {
