@@ -266,6 +266,15 @@ def run_gpu(args):
     peak, peak_src = measured_peaks()
     roof, kernel_share = roofline(kt, peak, peak_src)
     launches = sum(n for lg in logs for (_, n) in kt[lg].values())
+    # the path's own fraction: the method's 16 N bytes per transform over the step
+    roof["path_achieved"] = round(value, 1)
+    roof["path_frac"] = round(value / peak, 4)
+    # HBM passes per execute: every launch of the path reads and writes each
+    # element's 8-byte cell once (the C/S table launches of the large-row path
+    # move less and are counted as passes, so this is an upper estimate); the
+    # ncu capture of the NODE kernel measured 0.98 of its pass bytes
+    roof["traffic_ratio_est"] = {f"2^{lg}": round(sum(n for (_, n) in kt[lg].values()) / args.steps, 2)
+                                 for lg in logs}
 
     # ------------------------------------------------------- accuracy sample
     err_max, err_mean = 0.0, [float("nan")]
@@ -283,6 +292,7 @@ def run_gpu(args):
         err_max = max(err_max, float(e.max()))
         err_mean += e.tolist()
     schedules = {f"2^{lg}": plans[lg].schedule() for lg in logs}
+    comp = {f"2^{lg}": plans[lg].comp_classes() for lg in logs}
 
     # ------------------------------------------------------------- e2e
     e2e = None
@@ -315,7 +325,8 @@ def run_gpu(args):
                            ",".join(f"2^{l}" for l in logs), "elements_per_size": ELEMS,
                            "sizes_not_yet_supported": [f"2^{l}" for l in CONFIG_LOGS if l not in logs],
                            "l2": "inputs (2 GiB) larger than L2, no flush",
-                           "schedules": schedules, "autotune": tune, "autotune_s": round(tune_s, 2)},
+                           "schedules": schedules, "autotune": tune, "autotune_s": round(tune_s, 2),
+                           "compensated_classes": comp},
                 "gflops_5nlog2n": round(gflops, 1),
                 "frac_of_hbm": round(value / peak, 4),
                 "rel_err_vs_fp64": {"max": err_max, "mean": float(np.nanmean(err_mean)) if len(err_mean) > 1 else None, "rows": len(err_mean) - 1},
@@ -358,7 +369,10 @@ def roofline(kt, peak, peak_src):
     sizes = sorted(lg for lg in kt if dom in kt[lg])
     roof = {"bound": "hbm", "kernel": dom, "sizes": [f"2^{lg}" for lg in sizes],
             "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(dom),
+            "frac": round(achieved / peak, 4),
+            "frac_basis": "this kernel's own bytes per launch: 16 B per element per pass "
+                          "(row kernel: the transform's input and output; large-row kernels: scratch to scratch)",
+            "traffic": NCU_TRAFFIC.get(dom),
             "bytes_per_launch": 16 * ELEMS, "launches": n, "avg_launch_ms": round(avg, 4)}
 
     def share(steps):
@@ -471,6 +485,21 @@ def run_extras(args, dev, stream, torch, qft, orc, tune, peak):
         pr.destroy()
     ex["inverse_gbs"] = inv
     ex["real_forward_gbs"] = real
+    # the cost of the compensated classes: the same forward with every class
+    # tree in plain FP32 (QFT_PLAN_FP32_PLAIN), and its error on sampled rows
+    plain = {}
+    for lg in [l for l in CONFIG_LOGS if l >= 16]:
+        N = 1 << lg
+        a, b = zv.view(-1, N), zo.view(-1, N)
+        pl = qft.Plan(N, a.shape[0], autotune=tune, plain=True)
+        ms = _time(lambda: pl.execute(qft.OP_FORWARD, a, b), torch, stream)
+        torch.cuda.synchronize()
+        rows = [0, a.shape[0] // 2, a.shape[0] - 1]
+        e = _rel_errs(b[rows].cpu().numpy().astype(np.complex128), orc.cdft(a[rows].cpu().numpy()))
+        plain[f"2^{lg}"] = {"gbs": round(16 * (1 << 28) / (ms * 1e-3) / 1e9, 1), "rel_err_vs_fp64_max": e["max"],
+                            "comp_classes": 0}
+        pl.destroy()
+    ex["fp32_plain_forward"] = plain
     # standalone DCT-0 / DST-0 (eqs qft_0B, qft_0C): 2^28 reals in and out per size
     r2r = {}
     for lg in (12, 16, 20):

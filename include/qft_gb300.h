@@ -64,7 +64,8 @@ typedef struct qft_plan_s* qft_plan;
 #define QFT_OP_INVERSE_ADJOINT 3 /* = backward of the inverse transform */
 
 /* plan creation flags */
-#define QFT_PLAN_AUTOTUNE 1u /* time candidate schedules at creation and keep the fastest */
+#define QFT_PLAN_AUTOTUNE 1u   /* time candidate schedules at creation and keep the fastest */
+#define QFT_PLAN_FP32_PLAIN 2u /* n >= 2^16: evaluate every class tree in plain FP32 (see below)  */
 
 /* status codes */
 #define QFT_OK 0
@@ -87,13 +88,23 @@ typedef struct qft_plan_s* qft_plan;
  *          2 <= n <= 2^24 (C2C) or 4 <= n <= 2^24 (the real kinds).
  *   batch  number of rows (>= 0; 0 makes every execute a no-op).
  *   kind   QFT_KIND_C2C or QFT_KIND_R2C; dtype QFT_DTYPE_*.
- *   flags  0 or QFT_PLAN_AUTOTUNE.  With QFT_PLAN_AUTOTUNE the plan times the
+ *   flags  0, QFT_PLAN_AUTOTUNE and/or QFT_PLAN_FP32_PLAIN.  With
+ *          QFT_PLAN_AUTOTUNE the plan times the
  *          forward transform under candidate schedules (tile sizes of the
  *          phases, threads per CTA, input staging, node size and node threads
  *          for n > 2^14) on up to ~256 MB of its own rows, on a private stream,
  *          and keeps the fastest.  The schedule never changes the result: every
  *          schedule performs the same FP32 operations on the same operands.
  *          Results are cached per (n, kind, dtype, rows, device) in the process.
+ *   Precision: the FP32 error of the improved QFT grows like ~3.5e-8 sqrt(n)
+ *          (relative L2; it comes from the secant conversion of eq qft_38A,
+ *          whose factors reach n/(4 pi)).  For n >= 2^16 the plan therefore
+ *          evaluates the dct_ot / dst_ot trees of its J = floor((log2 n - 14)/2)
+ *          largest classes on compensated pairs of FP32 numbers (TwoSum adds,
+ *          exact FMA product errors, one rounding per class output), which
+ *          keeps the error near 5e-6 for every n up to 2^24 at a cost in
+ *          throughput; qft_plan_comp_classes reports J.  QFT_PLAN_FP32_PLAIN
+ *          turns this off (J = 0: the plain FP32 evaluation of the recursion).
  * The plan owns the FP32 secant table (Sec. 6.1, N/4 entries) and every
  * scratch buffer; it allocates them here, on the current CUDA device, and
  * frees them in qft_plan_destroy.  Executions must run on that device.
@@ -110,8 +121,9 @@ int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype
  *                 elements [offsets[i], offsets[i+1]) of the packed buffer;
  *                 offsets[0] == 0 and offsets[i+1]-offsets[i] == 2^log2n[i].
  *   log2n_host    count int32 entries (host memory), each in [1, 24].
- *   flags         0 or QFT_PLAN_AUTOTUNE (each length class is tuned on its own
- *                 row count before the graph is captured).
+ *   flags         0, QFT_PLAN_AUTOTUNE (each length class is tuned on its own
+ *                 row count before the graph is captured) and/or
+ *                 QFT_PLAN_FP32_PLAIN (as for qft_plan_create).
  * Data layout: one packed complex buffer for input and one for output.
  * Supported: QFT_KIND_C2C, QFT_DTYPE_F32.
  */
@@ -211,6 +223,11 @@ int qft_plan_destroy(qft_plan plan);
 /* Host-blocking: synchronises the plan's last stream and returns the plan's
  * device status word (QFT_OK or QFT_ERR_TIMEOUT), then clears it. */
 int qft_plan_sync_status(qft_plan plan);
+
+/* Number of classes (per side) whose trees the plan evaluates on compensated
+ * FP32 pairs (0 for n < 2^16 or with QFT_PLAN_FP32_PLAIN; ragged plans: the
+ * largest over their lengths), or a negative QFT_ERR_* code. */
+int qft_plan_comp_classes(qft_plan plan);
 
 /* Limit, in nanoseconds, of the kernels' bounded waits for the input copies they
  * stage in shared memory (default 0 = 2 s).  When a wait expires the kernel

@@ -333,9 +333,12 @@ static inline pair PMUL(pair a, real c)
 }
 static pair *palloc(long n) { return (pair *)calloc((size_t)(n > 0 ? n : 1), sizeof(pair)); }
 
-/* number of compensated classes of a root transform of length Nroot */
+/* number of compensated classes of a root transform of length Nroot (a test
+ * may set another count with oracle_set_comp_classes) */
+static int g_comp_override = -1;
 static int comp_classes(long Nroot)
 {
+    if (g_comp_override >= 0) return g_comp_override;
     int r = 0;
     while ((1L << r) < Nroot) ++r;
     return r >= 16 ? (r - 14) / 2 : 0;
@@ -687,6 +690,17 @@ int oracle_is_compensated(void)
     return 1;
 #else
     return 0;
+#endif
+}
+
+/* Sets the number of compensated classes for every transform (J >= 0), or
+ * restores the default rule (J < 0).  No effect without ORACLE_COMPENSATED. */
+void oracle_set_comp_classes(int J)
+{
+#ifdef ORACLE_COMPENSATED
+    g_comp_override = J;
+#else
+    (void)J;
 #endif
 }
 

@@ -84,7 +84,7 @@ static int plan_schedule(qft_plan p, QftTune t, int threads, int node_log2, int 
     if (t.LF < qft_lib::kLargeMinLF) return QFT_ERR_INVALID_N;   // the scratch holds tables for LF >= 3
     QftLargePlan* lp = (QftLargePlan*)malloc(sizeof(QftLargePlan));
     if (!lp) return QFT_ERR_CUDA;
-    if (qft_build_large_plan(r, t, node_log2, node_nt, lp) != 0) { free(lp); return QFT_ERR_INVALID_N; }
+    if (qft_build_large_plan(r, t, node_log2, node_nt, lp, p->comp_j) != 0) { free(lp); return QFT_ERR_INVALID_N; }
     if (!p->d_large) e = cudaMalloc(&p->d_large, sizeof(QftLargePlan));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_large, lp, sizeof(QftLargePlan), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { free(lp); return qft_set_cuda(p, e); }
@@ -99,12 +99,13 @@ static int plan_schedule(qft_plan p, QftTune t, int threads, int node_log2, int 
 
 // Fills a freshly allocated plan for `batch` rows of length 2^r: schedule,
 // constant table and scratch.  On failure everything it allocated is freed.
-static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
+static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype, int plain = 0) {
   p->magic = kMagic; p->kind = kind; p->dtype = dtype; p->n = int64_t(1) << r; p->batch = batch; p->r = r;
   p->d_plan = nullptr; p->d_sec = nullptr; p->last_cuda = cudaSuccess; p->last_stream = nullptr;
   p->large_host = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->scratch_rows = 0; p->side_len = 0;
   p->chunk_rows = 0;
   p->large_tab = 0;
+  p->comp_j = 0;
   p->grid = 0; p->threads = 0; p->smem = 0;
   p->nclasses = 0; p->classes = nullptr; p->d_offsets = nullptr; p->d_args = nullptr; p->h_args = nullptr;
   p->graph = nullptr; p->gexec = nullptr; p->graph_kernels = 0;
@@ -141,9 +142,13 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype) {
       p->large_host = (QftLargePlan*)malloc(sizeof(QftLargePlan));
       if (!p->large_host) { free_resources(p); return QFT_ERR_CUDA; }
       p->side_len = qft_side_len((int)N);
+      // the largest classes run on compensated pairs unless the plan asks for plain FP32
+      p->comp_j = plain ? 0 : qft_comp_classes(r);
+      if (p->comp_j > 0) p->node_log2 = qft_lib::kNodeLog2 - 1;   // four node buffers: two CTAs per SM
       const int64_t items = kind == QFT_KIND_C2C ? batch : (batch + 1) / 2;   // real kinds: row pairs
-      // two copies of the class data plus the FINAL tasks' C/S tables
-      const int64_t per_row = 2 * 2 * (int64_t)p->side_len * 8 +
+      // two copies of the class data plus the FINAL tasks' C/S tables, plus
+      // the lo parts of both copies for compensated plans
+      const int64_t per_row = (p->comp_j > 0 ? 4 : 2) * 2 * (int64_t)p->side_len * 8 +
                               (int64_t)qft_lib::large_tab_cells((int)N, qft_lib::kLargeMinLF) * 8;
       int64_t rows = qft_lib::kScratchBudget / per_row;
       if (rows > items) rows = items;
@@ -194,10 +199,10 @@ struct QftSched {
 
 static std::mutex g_tune_mu;
 struct TuneKey {
-  int r, kind, dtype, dev;
+  int r, kind, dtype, dev, comp;
   int64_t rows;
   bool operator==(const TuneKey& o) const {
-    return r == o.r && kind == o.kind && dtype == o.dtype && dev == o.dev && rows == o.rows;
+    return r == o.r && kind == o.kind && dtype == o.dtype && dev == o.dev && comp == o.comp && rows == o.rows;
   }
 };
 static TuneKey g_tune_keys[256];
@@ -259,7 +264,7 @@ static int autotune(qft_plan p) {
   int64_t cap = ((int64_t)256 << 20) / row_bytes;
   if (cap < 1) cap = 1;
   const int64_t rows = p->batch < cap ? p->batch : cap;
-  const TuneKey key{p->r, p->kind, p->dtype, p->device, rows};
+  const TuneKey key{p->r, p->kind, p->dtype, p->device, p->comp_j, rows};
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
     for (int i = 0; i < g_tune_n; ++i)
@@ -340,7 +345,7 @@ static int autotune(qft_plan p) {
 extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
   *out = nullptr;
-  if ((flags & ~QFT_PLAN_AUTOTUNE) != 0) return QFT_ERR_INVALID_ARG;
+  if ((flags & ~(QFT_PLAN_AUTOTUNE | QFT_PLAN_FP32_PLAIN)) != 0) return QFT_ERR_INVALID_ARG;
   if (kind != QFT_KIND_C2C && kind != QFT_KIND_R2C && kind != QFT_KIND_DCT0 && kind != QFT_KIND_DST0)
     return QFT_ERR_DTYPE;
   if (dtype != QFT_DTYPE_F32 && dtype != QFT_DTYPE_F16 && dtype != QFT_DTYPE_BF16) return QFT_ERR_DTYPE;
@@ -354,7 +359,7 @@ extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind
 
   qft_plan p = new (std::nothrow) qft_plan_s();
   if (!p) return QFT_ERR_CUDA;
-  int rc = plan_init(p, r, batch, kind, dtype);
+  int rc = plan_init(p, r, batch, kind, dtype, (flags & QFT_PLAN_FP32_PLAIN) ? 1 : 0);
   if (rc != QFT_OK) { delete p; return rc; }
   if (flags & QFT_PLAN_AUTOTUNE) {
     rc = autotune(p);
@@ -396,7 +401,7 @@ extern "C" int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host
                                       int64_t count, int kind, int dtype, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
   *out = nullptr;
-  if ((flags & ~QFT_PLAN_AUTOTUNE) != 0) return QFT_ERR_INVALID_ARG;
+  if ((flags & ~(QFT_PLAN_AUTOTUNE | QFT_PLAN_FP32_PLAIN)) != 0) return QFT_ERR_INVALID_ARG;
   if (kind != QFT_KIND_C2C || dtype != QFT_DTYPE_F32) return QFT_ERR_DTYPE;
   if (count < 0 || count > (int64_t(1) << 31)) return QFT_ERR_INVALID_BATCH;
   if (count > 0 && (!offsets_host || !log2n_host)) return QFT_ERR_NULLPTR;
@@ -425,7 +430,7 @@ extern "C" int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host
     C.r = r; C.count = per_r[r]; C.d_rows = nullptr;
     C.sub = new (std::nothrow) qft_plan_s();
     if (!C.sub) { rc = QFT_ERR_CUDA; break; }
-    rc = plan_init(C.sub, r, C.count, kind, dtype);
+    rc = plan_init(C.sub, r, C.count, kind, dtype, (flags & QFT_PLAN_FP32_PLAIN) ? 1 : 0);
     if (rc != QFT_OK) { delete C.sub; C.sub = nullptr; break; }
     if (flags & QFT_PLAN_AUTOTUNE) {
       rc = autotune(C.sub);
@@ -629,6 +634,17 @@ extern "C" int qft_plan_sync_status(qft_plan p) {
     }
   }
   return st;
+}
+
+extern "C" int qft_plan_comp_classes(qft_plan p) {
+  int rc = plan_check(p);
+  if (rc != QFT_OK) return rc;
+  if (p->classes) {   // ragged: the largest of its length classes
+    int j = 0;
+    for (int c = 0; c < p->nclasses; ++c) j = p->classes[c].sub->comp_j > j ? p->classes[c].sub->comp_j : j;
+    return j;
+  }
+  return p->comp_j;
 }
 
 extern "C" int qft_plan_set_wait_limit(qft_plan p, int64_t ns) {

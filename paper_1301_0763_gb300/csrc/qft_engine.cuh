@@ -61,6 +61,7 @@
 typedef float2 qc;
 #else
 #include <string.h>
+#include <math.h>
 #define QFT_HD inline
 #define QFT_RARE inline
 struct qc { float x, y; };
@@ -97,6 +98,7 @@ QFT_HD qc cmul(qc a, float s) { return mkc(__fmul_rn(a.x, s), __fmul_rn(a.y, s))
 QFT_HD float fmul(float a, float b) { return __fmul_rn(a, b); }
 QFT_HD float fadd(float a, float b) { return __fadd_rn(a, b); }
 QFT_HD float fsub(float a, float b) { return __fsub_rn(a, b); }
+QFT_HD float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 #elif defined(__CUDA_ARCH__)
 // scalar round-to-nearest intrinsics (never contracted), one per lane
 QFT_HD qc cadd(qc a, qc b) { return mkc(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
@@ -105,6 +107,7 @@ QFT_HD qc cmul(qc a, float s) { return mkc(__fmul_rn(a.x, s), __fmul_rn(a.y, s))
 QFT_HD float fmul(float a, float b) { return __fmul_rn(a, b); }
 QFT_HD float fadd(float a, float b) { return __fadd_rn(a, b); }
 QFT_HD float fsub(float a, float b) { return __fsub_rn(a, b); }
+QFT_HD float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 #else
 // host emulation: plain IEEE single precision (built with -ffp-contract=off)
 QFT_HD qc cadd(qc a, qc b) { return mkc(a.x + b.x, a.y + b.y); }
@@ -113,7 +116,39 @@ QFT_HD qc cmul(qc a, float s) { return mkc(a.x * s, a.y * s); }
 QFT_HD float fmul(float a, float b) { return a * b; }
 QFT_HD float fadd(float a, float b) { return a + b; }
 QFT_HD float fsub(float a, float b) { return a - b; }
+QFT_HD float ffma(float a, float b, float c) { return fmaf(a, b, c); }
 #endif
+
+// ------------------------------------------------ compensated arithmetic
+// In the compensated class trees every value is an unevaluated pair h + l of
+// FP32 numbers: h is exactly the plain FP32 value, l carries the rounding
+// errors (the FP32 error of the improved QFT comes from the secant conversion
+// of eq qft_38A, whose large factors make every value below them large).
+//   add: s = ah + bh, z = s - ah, e = (ah - (s - z)) + (bh - z)  (TwoSum,
+//        Knuth: s + e = ah + bh exactly), l = (al + bl) + e
+//   sub: the add of (-bh, -bl), written out without the negations
+//   mul by a constant c: p = ah c, e = fma(ah, c, -p) (exact), l = fma(al, c, e)
+// Each class output is rounded once, h + l.  e is exact, so the results do not
+// depend on operand order.
+QFT_HD void p_add(qc ah, qc al, qc bh, qc bl, qc& sh, qc& sl) {
+  const qc s = cadd(ah, bh);
+  const qc z = csub(s, ah);
+  const qc e = cadd(csub(ah, csub(s, z)), csub(bh, z));
+  sl = cadd(cadd(al, bl), e);
+  sh = s;
+}
+QFT_HD void p_sub(qc ah, qc al, qc bh, qc bl, qc& sh, qc& sl) {
+  const qc s = csub(ah, bh);
+  const qc z = csub(s, ah);
+  const qc e = csub(csub(ah, csub(s, z)), cadd(bh, z));   // (ah - (s - z)) + (-bh - z)
+  sl = cadd(csub(al, bl), e);
+  sh = s;
+}
+QFT_HD void p_mul(qc ah, qc al, float c, qc& ph, qc& pl) {
+  ph = cmul(ah, c);
+  const float ex = ffma(ah.x, c, -ph.x), ey = ffma(ah.y, c, -ph.y);
+  pl = mkc(ffma(al.x, c, ex), ffma(al.y, c, ey));
+}
 
 // ------------------------------------------------------------ geometry
 QFT_HD int qft_pidx(int i) { return i + (i >> 4); }
@@ -145,9 +180,12 @@ struct Eng {
   int N;
   qc* tabC;           // C_Mt(k), k in [0, Mt/2]   (Mt = N >> LF), or null
   qc* tabS;           // S_Mt(k), k in [1, Mt/2-1], or null
+  qc* lo0;            // lo parts of the DCT side's compensated cells (same indexing), or null
+  qc* lo1;            // lo parts of the DST side
 };
 
 QFT_HD qc* side_ptr(const Eng& e, int s) { return s ? e.side1 : e.side0; }
+QFT_HD qc* lo_ptr(const Eng& e, int s) { return s ? e.lo1 : e.lo0; }
 
 // ------------------------------------------------- forward mirror levels
 // L levels of the forward phase on registers v[t], t in [0, 2^L).  Register t
@@ -172,6 +210,28 @@ QFT_HD void dif_regs(qc (&v)[1 << L], int nb, int lo, const float* sec) {
       const qc a = v[t], b = v[t | half];
       if (SIDE == 0) { v[t] = cadd(a, b); v[t | half] = cmul(csub(a, b), s); }
       else           { v[t] = csub(a, b); v[t | half] = cmul(cadd(a, b), s); }
+    }
+  }
+}
+
+// The same levels on compensated pairs (v = h parts, w = l parts).
+template <int L, int SIDE>
+QFT_HD void dif_regs_c(qc (&v)[1 << L], qc (&w)[1 << L], int nb, int lo, const float* sec) {
+  const int h = nb - L;
+  const float* sl = sec + lo;
+#pragma unroll
+  for (int l = 1; l <= L; ++l) {
+    const int half = 1 << (L - l);
+    const float* sb = sl + (1 << (nb - l));
+#pragma unroll
+    for (int t = 0; t < (1 << L); ++t) {
+      if (t & half) continue;
+      const float s = sb[(t & (half - 1)) << h];
+      const qc a = v[t], al = w[t], b = v[t | half], bl = w[t | half];
+      qc dh, dl;
+      if (SIDE == 0) { p_add(a, al, b, bl, v[t], w[t]); p_sub(a, al, b, bl, dh, dl); }
+      else           { p_sub(a, al, b, bl, v[t], w[t]); p_add(a, al, b, bl, dh, dl); }
+      p_mul(dh, dl, s, v[t | half], w[t | half]);
     }
   }
 }
@@ -215,6 +275,37 @@ QFT_HD void bwd_chunk(qc (&w)[1 << L], const qc* h, bool hv) {
   }
 }
 
+// The same backward levels on compensated pairs.
+template <int L, int SIDE>
+QFT_HD void bwd_chunk_c(qc (&w)[1 << L], qc (&wl)[1 << L], const qc* h, const qc* hl, bool hv) {
+#pragma unroll
+  for (int s = 2; s <= (1 << L); s <<= 1) {
+    const int hs = s >> 1;
+#pragma unroll
+    for (int base = 0; base < (1 << L); base += s) {
+      qc tmp[1 << L], tml[1 << L];
+#pragma unroll
+      for (int i = 0; i < hs; ++i) {
+        const qc E = w[base + i], El = wl[base + i];
+        const qc Y = w[base + hs + i], Yl = wl[base + hs + i];
+        if (SIDE == 0) {
+          tmp[2 * i] = E; tml[2 * i] = El;
+          if (i + 1 < hs) p_add(Y, Yl, w[base + hs + i + 1], wl[base + hs + i + 1], tmp[2 * i + 1], tml[2 * i + 1]);
+          else if (hv) p_add(Y, Yl, h[base + hs], hl[base + hs], tmp[2 * i + 1], tml[2 * i + 1]);
+          else { tmp[2 * i + 1] = Y; tml[2 * i + 1] = Yl; }
+        } else {
+          tmp[2 * i + 1] = E; tml[2 * i + 1] = El;
+          if (i >= 1) p_add(w[base + hs + i - 1], wl[base + hs + i - 1], Y, Yl, tmp[2 * i], tml[2 * i]);
+          else if (hv) p_add(h[base + hs], hl[base + hs], Y, Yl, tmp[2 * i], tml[2 * i]);
+          else { tmp[2 * i] = Y; tml[2 * i] = Yl; }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < s; ++i) { w[base + i] = tmp[i]; wl[base + i] = tml[i]; }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ F1
 // Large class j: one task = the 2^L1 Gray slots t*H + lo (H = 2^(b-L1),
 // lo = gray(ilo)) of both sides.  The cells are loaded straight from the row:
@@ -249,6 +340,38 @@ QFT_HD void task_f1_big(const Eng& e, const IO& io, int j, int ilo) {
       e.side0[qft_pidx(off + t * H + lo)] = vc[t];
       e.side1[qft_pidx(off + t * H + lo)] = vs[t];
     }
+  }
+}
+
+// The same task for a compensated class: the folded cells enter the class tree
+// as pairs (l = 0); h and l parts are stored.
+template <int L1, class IO>
+QFT_HD void task_f1_big_c(const Eng& e, const IO& io, int j, int ilo) {
+  const int b = cls_bits(e.r, j);
+  const int h = b - L1;
+  const int H = 1 << h;
+  const int lo = ilo ^ (ilo >> 1);
+  qc vc[1 << L1], vs[1 << L1], wc[1 << L1], ws[1 << L1];
+#pragma unroll
+  for (int t = 0; t < (1 << L1); ++t) {
+    const int ig = ig_c(t);
+    const int c = (ig << h) | ((ig & 1) ? (H - 1 - ilo) : ilo);
+    io.get_cd((2 * c + 1) << j, vc[t], vs[t]);
+    wc[t] = mkc(0.f, 0.f);
+    ws[t] = wc[t];
+  }
+  dif_regs_c<L1, 0>(vc, wc, b, lo, e.sec);
+  dif_regs_c<L1, 1>(vs, ws, b, lo, e.sec);
+  const int off = cls_off(e.r, j);
+  const bool lin = h >= 4;   // off is a multiple of 16 then
+  const int p0 = qft_pidx(off + lo), ps = lin ? qft_pstride(h) : 0;
+#pragma unroll
+  for (int t = 0; t < (1 << L1); ++t) {
+    const int pi = lin ? p0 + t * ps : qft_pidx(off + t * H + lo);
+    e.side0[pi] = vc[t];
+    e.side1[pi] = vs[t];
+    e.lo0[pi] = wc[t];
+    e.lo1[pi] = ws[t];
   }
 }
 
@@ -326,6 +449,48 @@ QFT_HD void task_leaf(const Eng& e, int j, int q) {
   for (int t = 0; t < (1 << L); ++t) A[p0 + t] = v[t];
 }
 
+template <int L, int SIDE>
+QFT_HD void task_dif_c(const Eng& e, int j, int D, int tau) {
+  const int nb = cls_bits(e.r, j) - D;
+  const int h = nb - L;
+  const int q = tau >> h;
+  const int lo = tau & ((1 << h) - 1);
+  qc* A = side_ptr(e, SIDE);
+  qc* Al = lo_ptr(e, SIDE);
+  const int base = cls_off(e.r, j) + (q << nb) + lo;
+  qc v[1 << L], w[1 << L];
+  const bool lin = h >= 4;
+  const int p0 = qft_pidx(base), ps = lin ? qft_pstride(h) : 0;
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) {
+    const int pi = lin ? p0 + t * ps : qft_pidx(base + (t << h));
+    v[t] = A[pi];
+    w[t] = Al[pi];
+  }
+  dif_regs_c<L, SIDE>(v, w, nb, lo, e.sec);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) {
+    const int pi = lin ? p0 + t * ps : qft_pidx(base + (t << h));
+    A[pi] = v[t];
+    Al[pi] = w[t];
+  }
+}
+
+template <int L, int SIDE>
+QFT_HD void task_leaf_c(const Eng& e, int j, int q) {
+  qc* A = side_ptr(e, SIDE);
+  qc* Al = lo_ptr(e, SIDE);
+  const int base = cls_off(e.r, j) + (q << L);
+  const int p0 = qft_pidx(base);
+  qc v[1 << L], w[1 << L];
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) { v[t] = A[p0 + t]; w[t] = Al[p0 + t]; }
+  dif_regs_c<L, SIDE>(v, w, L, 0, e.sec);
+  bwd_chunk_c<L, SIDE>(v, w, v, w, false);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) { A[p0 + t] = v[t]; Al[p0 + t] = w[t]; }
+}
+
 // --------------------------------------------------------------- SLICE
 // Node at depth D-L (2^nb cells) whose depth-D descendants (2^(b-D) cells
 // each, natural frequency order, descendant t at offset t*S) are known.  Task
@@ -341,6 +506,14 @@ struct SliceRegs {
   qc h[1 << QFT_MAX_LB];
   int base;   // node base + r_ * 2^L  (write position)
   bool hv;
+};
+// compensated SLICE tasks: the l parts as well; `root` marks the tasks that
+// produce the class outputs (node at depth 0), which are rounded once, h + l
+struct SliceRegsC {
+  SliceRegs p;    // h parts, halo flag and write position
+  qc wl[1 << QFT_MAX_LB];
+  qc hl[1 << QFT_MAX_LB];
+  bool root;
 };
 
 template <int L, int SIDE>
@@ -387,6 +560,60 @@ QFT_HD void task_slice_write(const Eng& e, SliceRegs& s) {
   const int p0 = qft_pidx(s.base);   // s.base is a multiple of 2^L <= 16
 #pragma unroll
   for (int t = 0; t < (1 << L); ++t) A[p0 + t] = w[t];
+}
+
+template <int L, int SIDE>
+QFT_HD void task_slice_read_c(const Eng& e, int j, int D, int tau, SliceRegsC& s) {
+  const int b = cls_bits(e.r, j);
+  const int sb = b - D;
+  const int S = 1 << sb;
+  const int nb = b - (D - L);
+  const int q = tau >> sb;
+  const int rr = tau & (S - 1);
+  const qc* A = side_ptr(e, SIDE);
+  const qc* Al = lo_ptr(e, SIDE);
+  const int nbase = cls_off(e.r, j) + (q << nb);
+  const bool hv = SIDE == 0 ? (rr + 1 < S) : (rr >= 1);
+  const int hoff = SIDE == 0 ? rr + 1 : rr - 1;
+  const bool lin = sb >= 4;
+  const int ps = lin ? qft_pstride(sb) : 0;
+  const int pw = qft_pidx(nbase + rr);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) {
+    const int pi = lin ? pw + t * ps : qft_pidx(nbase + t * S + rr);
+    s.p.w[t] = A[pi];
+    s.wl[t] = Al[pi];
+  }
+  if (hv) {
+    const int ph = qft_pidx(nbase + hoff);
+#pragma unroll
+    for (int t = 1; t < (1 << L); ++t) {
+      const int pi = lin ? ph + t * ps : qft_pidx(nbase + t * S + hoff);
+      s.p.h[t] = A[pi];
+      s.hl[t] = Al[pi];
+    }
+  }
+  s.p.hv = hv;
+  s.root = D == L;
+  s.p.base = nbase + (rr << L);
+}
+
+template <int L, int SIDE>
+QFT_HD void task_slice_write_c(const Eng& e, SliceRegsC& s) {
+  qc w[1 << L], wl[1 << L];
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) { w[t] = s.p.w[t]; wl[t] = s.wl[t]; }
+  bwd_chunk_c<L, SIDE>(w, wl, s.p.h, s.hl, s.p.hv);
+  qc* A = side_ptr(e, SIDE);
+  qc* Al = lo_ptr(e, SIDE);
+  const int p0 = qft_pidx(s.p.base);
+  if (s.root) {
+#pragma unroll
+    for (int t = 0; t < (1 << L); ++t) A[p0 + t] = cadd(w[t], wl[t]);   // class output, rounded once
+  } else {
+#pragma unroll
+    for (int t = 0; t < (1 << L); ++t) { A[p0 + t] = w[t]; Al[p0 + t] = wl[t]; }
+  }
 }
 
 // --------------------------------------------------------------- FINAL
@@ -560,8 +787,25 @@ QFT_HD const QftSeg& find_seg(const QftRowPlan& P, int p, int tau) {
   return P.segs[s];
 }
 
-template <int L1, class IO>
+// COMP kernels (large-row path) also run the compensated variants of the
+// segments flagged in pad[2] (classes whose trees run on pairs); their register
+// tiles hold at most 8 cells (the planner caps L at 3 for those segments).
+template <int L1, class IO, bool COMP = false>
 QFT_HD void run_plain_task(int LF, const QftSeg& sg, const Eng& e, const IO& io, int loc) {
+  if (COMP && sg.pad[2]) {
+    switch (sg.type) {
+    case QFT_SEG_F1_BIG: task_f1_big_c<L1>(e, io, sg.cls, loc); return;
+    case QFT_SEG_DIF:
+#define QFT_DIFC_CASE(LL) case LL: if (sg.side) task_dif_c<LL, 1>(e, sg.cls, sg.D, loc); else task_dif_c<LL, 0>(e, sg.cls, sg.D, loc); return;
+      switch (sg.L) { QFT_DIFC_CASE(1) QFT_DIFC_CASE(2) QFT_DIFC_CASE(3) default: return; }
+#undef QFT_DIFC_CASE
+    case QFT_SEG_LEAF:
+#define QFT_LEAFC_CASE(LL) case LL: if (sg.side) task_leaf_c<LL, 1>(e, sg.cls, loc); else task_leaf_c<LL, 0>(e, sg.cls, loc); return;
+      switch (sg.L) { QFT_LEAFC_CASE(1) QFT_LEAFC_CASE(2) QFT_LEAFC_CASE(3) default: return; }
+#undef QFT_LEAFC_CASE
+    default: break;
+    }
+  }
   switch (sg.type) {
   case QFT_SEG_F1_BIG: task_f1_big<L1>(e, io, sg.cls, loc); break;
   case QFT_SEG_F1_SMALL:
@@ -603,11 +847,25 @@ QFT_HD void run_plain_task(int LF, const QftSeg& sg, const Eng& e, const IO& io,
 // l = first, first + step, ... < end (task index g*count + l).  The switch on
 // the task kind is taken once per segment; the loop body is specialised, so
 // the class geometry is loop-invariant.
-template <int L1, class IO>
+template <int L1, class IO, bool COMP = false>
 QFT_HD void run_plain_segment(int LF, const QftSeg& sg, const Eng& e, const IO& io, int first, int end,
                               int step, int g) {
   const int off = g * sg.count;
 #define QFT_LOOP(CALL) for (int l = first; l < end; l += step) { const int loc = off + l; (void)loc; CALL; }
+  if (COMP && sg.pad[2]) {
+    switch (sg.type) {
+    case QFT_SEG_F1_BIG: QFT_LOOP(task_f1_big_c<L1>(e, io, sg.cls, loc)) return;
+    case QFT_SEG_DIF:
+#define QFT_DIFC_CASE(LL) case LL: if (sg.side) { QFT_LOOP((task_dif_c<LL, 1>(e, sg.cls, sg.D, loc))) } else { QFT_LOOP((task_dif_c<LL, 0>(e, sg.cls, sg.D, loc))) } return;
+      switch (sg.L) { QFT_DIFC_CASE(1) QFT_DIFC_CASE(2) QFT_DIFC_CASE(3) default: return; }
+#undef QFT_DIFC_CASE
+    case QFT_SEG_LEAF:
+#define QFT_LEAFC_CASE(LL) case LL: if (sg.side) { QFT_LOOP((task_leaf_c<LL, 1>(e, sg.cls, loc))) } else { QFT_LOOP((task_leaf_c<LL, 0>(e, sg.cls, loc))) } return;
+      switch (sg.L) { QFT_LEAFC_CASE(1) QFT_LEAFC_CASE(2) QFT_LEAFC_CASE(3) default: return; }
+#undef QFT_LEAFC_CASE
+    default: break;
+    }
+  }
   switch (sg.type) {
   case QFT_SEG_F1_BIG: QFT_LOOP(task_f1_big<L1>(e, io, sg.cls, loc)) break;
   case QFT_SEG_F1_SMALL:
@@ -656,6 +914,36 @@ QFT_HD void run_slice_read(const QftSeg& sg, const Eng& e, int loc, SliceRegs& s
     default: break;
   }
 #undef QFT_SR_CASE
+}
+
+// MAXL: the largest L the caller's plans give compensated SLICE segments (the
+// NODE kernel's sub-plans use at most 2, which keeps its registers in budget).
+template <int MAXL = 3>
+QFT_HD void run_slice_read_c(const QftSeg& sg, const Eng& e, int loc, SliceRegsC& s) {
+  switch (sg.L) {
+  case 1: if (sg.side) task_slice_read_c<1, 1>(e, sg.cls, sg.D, loc, s); else task_slice_read_c<1, 0>(e, sg.cls, sg.D, loc, s); break;
+  case 2: if (sg.side) task_slice_read_c<2, 1>(e, sg.cls, sg.D, loc, s); else task_slice_read_c<2, 0>(e, sg.cls, sg.D, loc, s); break;
+  case 3:
+    if constexpr (MAXL >= 3) {
+      if (sg.side) task_slice_read_c<3, 1>(e, sg.cls, sg.D, loc, s); else task_slice_read_c<3, 0>(e, sg.cls, sg.D, loc, s);
+    }
+    break;
+  default: break;
+  }
+}
+
+template <int MAXL = 3>
+QFT_HD void run_slice_write_c(const QftSeg& sg, const Eng& e, SliceRegsC& s) {
+  switch (sg.L) {
+  case 1: if (sg.side) task_slice_write_c<1, 1>(e, s); else task_slice_write_c<1, 0>(e, s); break;
+  case 2: if (sg.side) task_slice_write_c<2, 1>(e, s); else task_slice_write_c<2, 0>(e, s); break;
+  case 3:
+    if constexpr (MAXL >= 3) {
+      if (sg.side) task_slice_write_c<3, 1>(e, s); else task_slice_write_c<3, 0>(e, s);
+    }
+    break;
+  default: break;
+  }
 }
 
 QFT_HD void run_slice_write(const QftSeg& sg, const Eng& e, SliceRegs& s) {

@@ -61,6 +61,8 @@ __device__ __forceinline__ Eng filt_setup(unsigned char* smem, const FiltArgs& a
   e.sec = sec; e.r = P.r; e.N = N;
   e.tabC = reinterpret_cast<qc*>(smem + qft_lib::off_tab(N));
   e.tabS = e.tabC + (N >> P.LF) / 2 + 1;
+  e.lo0 = nullptr;
+  e.lo1 = nullptr;
   return e;
 }
 

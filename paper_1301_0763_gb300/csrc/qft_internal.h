@@ -74,6 +74,7 @@ struct qft_plan_s {
   int64_t scratch_rows;       // rows the scratch copies hold
   int64_t chunk_rows;         // rows per launch sequence (0: scratch_rows); fewer keep a chunk's copies in L2
   int large_tab;              // 1: TAB launch + FINAL from C/S tables; 0: FINAL walks the class recursion
+  int comp_j;                 // classes (per side) whose trees run on compensated pairs (large rows only)
   int side_len;
   // ragged plans (qft_plan_create_ragged)
   int nclasses;

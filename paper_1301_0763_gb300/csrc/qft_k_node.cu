@@ -1,33 +1,43 @@
 // qft_k_node.cu -- the NODE and SLICE kernels of the large-row path (they do
-// not depend on the transform's IO), compiled once for every launcher.
+// not depend on the transform's IO), compiled once for every launcher, with
+// and without the compensated segments.
 #define QFT_NODE_TU 1
 #include "qft_large.cuh"
 
-cudaError_t qft_large_node_prepare(int nt, size_t smem) {
-  return nt == 256 ? cudaFuncSetAttribute(k_large_node<qft_lib::kL1, 256>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                   : cudaFuncSetAttribute(k_large_node<qft_lib::kL1, 512>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int NT, bool COMP>
+static cudaError_t node_attr(size_t smem) {
+  return cudaFuncSetAttribute(k_large_node<qft_lib::kL1, NT, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+cudaError_t qft_large_node_prepare(int nt, size_t smem, int comp) {
+  if (comp) return nt == 256 ? node_attr<256, true>(smem) : node_attr<512, true>(smem);
+  return nt == 256 ? node_attr<256, false>(smem) : node_attr<512, false>(smem);
 }
 
 // Persistent NODE launch: as many CTAs as fit on the GPU at once (at most one
 // per item); each loops over its items.
-cudaError_t qft_large_node_launch(const LargeArgs& a, int64_t rows, int64_t items, int nt, size_t smem,
-                                  cudaStream_t st) {
+template <int NT, bool COMP>
+static cudaError_t node_launch(const LargeArgs& a, int64_t rows, int64_t items, size_t smem, cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = nt == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_node<qft_lib::kL1, 256>, 256, smem)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_node<qft_lib::kL1, 512>, 512, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_node<qft_lib::kL1, NT, COMP>, NT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)per_sm * sms;
   if (grid > items) grid = items;
   if (grid < 1) grid = 1;
-  if (nt == 256) k_large_node<qft_lib::kL1, 256><<<(unsigned)grid, 256, smem, st>>>(a, rows);
-  else k_large_node<qft_lib::kL1, 512><<<(unsigned)grid, 512, smem, st>>>(a, rows);
+  k_large_node<qft_lib::kL1, NT, COMP><<<(unsigned)grid, NT, smem, st>>>(a, rows);
   return cudaGetLastError();
+}
+
+cudaError_t qft_large_node_launch(const LargeArgs& a, int64_t rows, int64_t items, int nt, size_t smem,
+                                  cudaStream_t st, int comp) {
+  if (comp) return nt == 256 ? node_launch<256, true>(a, rows, items, smem, st)
+                             : node_launch<512, true>(a, rows, items, smem, st);
+  return nt == 256 ? node_launch<256, false>(a, rows, items, smem, st)
+                   : node_launch<512, false>(a, rows, items, smem, st);
 }
 
 cudaError_t qft_large_tab_launch(const LargeArgs& a, int64_t rows, int LF, cudaStream_t st) {
@@ -35,7 +45,8 @@ cudaError_t qft_large_tab_launch(const LargeArgs& a, int64_t rows, int LF, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st) {
-  k_large_slice<<<grid, kLargeNT, 0, st>>>(a, phase);
+cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st, int comp) {
+  if (comp) k_large_slice<true><<<grid, kLargeNT, 0, st>>>(a, phase);
+  else k_large_slice<false><<<grid, kLargeNT, 0, st>>>(a, phase);
   return cudaGetLastError();
 }

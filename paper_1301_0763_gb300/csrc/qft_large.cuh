@@ -22,16 +22,19 @@ struct LargeArgs {
   int tabS_off;               // S_Mt starts tabS_off cells after C_Mt (Mt/2 + 1)
   uint64_t wait_ns;           // limit of the NODE kernel's wait for a staged window
   int withhold;               // test: each NODE CTA's first window copy is not issued (its wait runs out)
+  qc* loA;                    // lo parts of the compensated cells of copy A (same layout), or null
+  qc* loB;                    // lo parts of copy B
 };
 
 
 // The NODE and SLICE kernels do not depend on the IO of the transform; they
 // are compiled once (qft_k_node.cu) and launched through these helpers, which
 // return the CUDA error of the launch.
-cudaError_t qft_large_node_prepare(int nt, size_t smem);
+// comp != 0 selects the kernels that also run the compensated segments.
+cudaError_t qft_large_node_prepare(int nt, size_t smem, int comp);
 cudaError_t qft_large_node_launch(const LargeArgs& a, int64_t rows, int64_t items, int nt, size_t smem,
-                                  cudaStream_t st);
-cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st);
+                                  cudaStream_t st, int comp);
+cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st, int comp);
 cudaError_t qft_large_tab_launch(const LargeArgs& a, int64_t rows, int LF, cudaStream_t st);
 
 namespace {
@@ -49,12 +52,15 @@ __device__ __forceinline__ Eng large_eng(const LargeArgs& a, int copy, int64_t r
   e.N = 1 << a.r;
   e.tabC = a.tab ? a.tab + row * (int64_t)a.tab_stride : nullptr;
   e.tabS = a.tab ? e.tabC + a.tabS_off : nullptr;
+  qc* lb = copy ? a.loB : a.loA;
+  e.lo0 = lb ? lb + row * 2 * (int64_t)a.side_len : nullptr;
+  e.lo1 = lb ? e.lo0 + a.side_len : nullptr;
   return e;
 }
 
 // GLOBAL phase (F1, DIF, FINAL): blockIdx.y = row within the chunk, blockIdx.x
 // = block of kLargeNT * kLargeTPT consecutive tasks of that row's phase.
-template <class FAC, int L1>
+template <class FAC, int L1, bool COMP>
 __global__ void __launch_bounds__(kLargeNT, 2) k_large_global(LargeArgs a, int phase, FAC fac) {
   const QftLargePlan* P = a.plan;
   const QftLargePhase ph = P->phases[phase];
@@ -71,21 +77,23 @@ __global__ void __launch_bounds__(kLargeNT, 2) k_large_global(LargeArgs a, int p
     if (first < 0) first += ((-first + kLargeNT - 1) / kLargeNT) * kLargeNT;
     int end = T1 - sg.begin;
     if (end > sg.count) end = sg.count;
-    run_plain_segment<L1>(P->LF, sg, e, io, first, end, kLargeNT, 0);
+    run_plain_segment<L1, decltype(io), COMP>(P->LF, sg, e, io, first, end, kLargeNT, 0);
   }
 }
 
 // cells of one NODE buffer: the largest group window, rounded up to an even
 // count so that a bulk copy of it is a multiple of 16 bytes
 __host__ __device__ inline int node_buf_cells(int NB) { return (qft_pidx(1 << NB) + 2) & ~1; }
-// plan | secants | two cell buffers (the current item and the prefetched next one)
-__host__ __device__ inline size_t node_smem_bytes(int NB) {
+// plan | secants | two cell buffers (the current item and the prefetched next
+// one) | with compensation, two more buffers for their lo parts
+__host__ __device__ inline size_t node_smem_bytes(int NB, int comp = 0) {
   return qft_lib::align16(sizeof(QftRowPlan)) + qft_lib::align16(sizeof(float) * (((size_t)1 << NB) + 1)) +
-         2 * qft_lib::align16(8 * (size_t)node_buf_cells(NB));
+         (comp ? 4 : 2) * qft_lib::align16(8 * (size_t)node_buf_cells(NB));
 }
 
 #ifdef QFT_NODE_TU
 // SLICE phase above the node depth: reads copy sg.pad[0], writes copy sg.pad[1].
+template <bool COMP>
 __global__ void __launch_bounds__(kLargeNT, 2) k_large_slice(LargeArgs a, int phase) {
   const QftLargePlan* P = a.plan;
   const QftLargePhase ph = P->phases[phase];
@@ -100,9 +108,15 @@ __global__ void __launch_bounds__(kLargeNT, 2) k_large_slice(LargeArgs a, int ph
     const QftSeg sg = P->segs[sgi];
     const Eng es = large_eng(a, sg.pad[0], row);
     const Eng ed = large_eng(a, sg.pad[1], row);
-    SliceRegs s;
-    run_slice_read(sg, es, tau - sg.begin, s);
-    run_slice_write(sg, ed, s);
+    if (COMP && sg.pad[2]) {
+      SliceRegsC s;
+      run_slice_read_c(sg, es, tau - sg.begin, s);
+      run_slice_write_c(sg, ed, s);
+    } else {
+      SliceRegs s;
+      run_slice_read(sg, es, tau - sg.begin, s);
+      run_slice_write(sg, ed, s);
+    }
   }
 }
 
@@ -133,7 +147,7 @@ __device__ __forceinline__ void node_item(const QftLargePlan* LP, int r, int64_t
   w.pn = qft_pidx(ncell - 1) + 1;
 }
 
-template <int L1, int NT>
+template <int L1, int NT, bool COMP>
 __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_t rows) {
   // Persistent: item = node CTA index * rows + row, visited in steps of the
   // grid, so one CTA's items keep the same sub (and sub-plan) for long runs;
@@ -152,20 +166,30 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_
   buf[0] = reinterpret_cast<qc*>(smem + qft_lib::align16(sizeof(QftRowPlan)) +
                                  qft_lib::align16(sizeof(float) * ((1 << NB) + 1)));
   buf[1] = buf[0] + qft_lib::align16(8 * (size_t)node_buf_cells(NB)) / 8;
+  qc* lbuf[2];   // lo parts of the compensated subs' cells (COMP kernels only)
+  lbuf[0] = buf[1] + qft_lib::align16(8 * (size_t)node_buf_cells(NB)) / 8;
+  lbuf[1] = lbuf[0] + qft_lib::align16(8 * (size_t)node_buf_cells(NB)) / 8;
   const int64_t items = (int64_t)LP->node_ctas * rows;
   const auto src_of = [&](const NodeItem& w) {
     return side_ptr(large_eng(a, 0, w.row), LP->subs[w.k].side) + w.pb;
   };
-  // thread 0: bulk copy of item w's window into buffer b, if everything is 16-byte aligned
+  const auto lsrc_of = [&](const NodeItem& w) {
+    return lo_ptr(large_eng(a, 0, w.row), LP->subs[w.k].side) + w.pb;
+  };
+  // thread 0: bulk copy of item w's window (and, for a compensated sub, of its
+  // lo parts) into buffer b, if everything is 16-byte aligned
   const auto issue = [&](const NodeItem& w, int b) {
     const qc* src = src_of(w);
+    const bool comp = COMP && LP->subs[w.k].comp;
     const uint32_t bytes = (uint32_t)(((w.pn + 1) & ~1) * 8);
-    const bool ok = ((uintptr_t)src & 15) == 0 && (bytes & 15) == 0 && (smem_u32(buf[b]) & 15) == 0;
+    const bool ok = ((uintptr_t)src & 15) == 0 && (bytes & 15) == 0 && (smem_u32(buf[b]) & 15) == 0 &&
+                    (!comp || (((uintptr_t)lsrc_of(w) & 15) == 0 && (smem_u32(lbuf[b]) & 15) == 0));
     s_staged[b] = ok ? 1 : 0;
     if (ok) {
       fence_proxy_async_smem();
-      mbar_expect_tx(smem_u32(&mbar[b]), bytes);
+      mbar_expect_tx(smem_u32(&mbar[b]), comp ? 2 * bytes : bytes);
       bulk_g2s(smem_u32(buf[b]), src, bytes, smem_u32(&mbar[b]));
+      if (comp) bulk_g2s(smem_u32(lbuf[b]), lsrc_of(w), bytes, smem_u32(&mbar[b]));
     }
   };
   for (int m = threadIdx.x; m <= (1 << NB); m += NT) sec[m] = a.gsec[m];
@@ -214,6 +238,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_
     } else {
       const qc* srcp = src_of(w);
       for (int i = threadIdx.x; i < w.pn; i += NT) cells[i] = srcp[i];
+      if (COMP && S.comp) {
+        const qc* lsrc = lsrc_of(w);
+        for (int i = threadIdx.x; i < w.pn; i += NT) lbuf[b][i] = lsrc[i];
+      }
     }
     withheld = false;
     // the next item's copy goes to the other buffer, free since the last barrier
@@ -238,10 +266,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_
     e.N = 1 << a.r;
     e.tabC = nullptr;
     e.tabS = nullptr;
-    run_row_phases<L1, NT>(Q, e, NoIO(), w.g);
+    e.lo0 = lbuf[b] - w.pb;
+    e.lo1 = lbuf[b] - w.pb;
+    run_row_phases<L1, NT, NoIO, NoHook, COMP>(Q, e, NoIO(), w.g);
     const Eng ed = large_eng(a, S.dst, w.row);
     qc* dstp = side_ptr(ed, S.side) + w.pb;
     for (int i = threadIdx.x; i < w.pn; i += NT) dstp[i] = cells[i];
+    if (COMP && S.comp) {
+      qc* ldst = lo_ptr(ed, S.side) + w.pb;
+      for (int i = threadIdx.x; i < w.pn; i += NT) ldst[i] = lbuf[b][i];
+    }
     __syncthreads();   // this buffer (and maybe the sub-plan) is reused two items on
   }
 }
@@ -266,25 +300,32 @@ __global__ void __launch_bounds__(256) k_large_tab(LargeArgs a, int LF) {
 template <class FAC>
 static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t st) {
   const QftLargePlan& H = *p->large_host;
+  const int comp = H.comp_classes > 0 ? 1 : 0;
   LargeArgs a;
   a.plan = p->d_large;
   a.gsec = p->d_sec;
+  // scratch: copy A | copy B | C/S tables | (compensated plans) lo parts of A | of B
+  const size_t copy_cells = (size_t)p->scratch_rows * 2 * p->side_len;
   a.scrA = reinterpret_cast<qc*>(p->scratch);
-  a.scrB = a.scrA + (size_t)p->scratch_rows * 2 * p->side_len;
+  a.scrB = a.scrA + copy_cells;
   a.side_len = p->side_len;
   a.r = p->r;
   a.status = p->d_status;
   a.wait_ns = p->wait_ns > 0 ? (uint64_t)p->wait_ns : kWaitLimitNs;
   a.withhold = p->withhold_copy;
-  // tables after the two copies; a CTA builds one row's tables, which pays off
-  // only with enough rows of moderate length (the plan's large_tab)
-  a.tab = p->large_tab ? a.scrB + (size_t)p->scratch_rows * 2 * p->side_len : nullptr;
   a.tab_stride = qft_lib::large_tab_cells(1 << p->r, H.LF);
   a.tabS_off = ((1 << p->r) >> H.LF) / 2 + 1;
-  const size_t node_smem = node_smem_bytes(H.NB);
+  // tables after the two copies; a CTA builds one row's tables, which pays off
+  // only with enough rows of moderate length (the plan's large_tab)
+  qc* tab0 = a.scrB + copy_cells;
+  a.tab = p->large_tab ? tab0 : nullptr;
+  qc* lo0 = tab0 + (size_t)p->scratch_rows * qft_lib::large_tab_cells(1 << p->r, qft_lib::kLargeMinLF);
+  a.loA = comp ? lo0 : nullptr;
+  a.loB = comp ? lo0 + copy_cells : nullptr;
+  const size_t node_smem = node_smem_bytes(H.NB, comp);
   // node kernel: 512 threads (one CTA per SM) unless the plan asks for 256
   const int node_nt = p->node_nt == 256 ? 256 : 512;
-  cudaError_t e = qft_large_node_prepare(node_nt, node_smem);
+  cudaError_t e = qft_large_node_prepare(node_nt, node_smem, comp);
   if (e != cudaSuccess) return qft_set_cuda(p, e);
   const int64_t chunk = p->chunk_rows > 0 && p->chunk_rows < p->scratch_rows ? p->chunk_rows : p->scratch_rows;
   for (int64_t r0 = 0; r0 < items; r0 += chunk) {
@@ -299,17 +340,18 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
         if (e != cudaSuccess) return qft_set_cuda(p, e);
       } else if (P.kind == QFT_LPH_NODE) {
         qft_time_begin(p, st, QFT_KERNEL_NODE);
-        e = qft_large_node_launch(a, rows, (int64_t)H.node_ctas * rows, node_nt, node_smem, st);
+        e = qft_large_node_launch(a, rows, (int64_t)H.node_ctas * rows, node_nt, node_smem, st, comp);
         if (e != cudaSuccess) return qft_set_cuda(p, e);
       } else {
         const unsigned bx = (unsigned)((P.ntasks + kLargeNT * kLargeTPT - 1) / (kLargeNT * kLargeTPT));
         if (P.kind == QFT_LPH_SLICE) {
           qft_time_begin(p, st, QFT_KERNEL_SLICE);
-          e = qft_large_slice_launch(a, ph, dim3(bx, (unsigned)rows), st);
+          e = qft_large_slice_launch(a, ph, dim3(bx, (unsigned)rows), st, comp);
           if (e != cudaSuccess) return qft_set_cuda(p, e);
         } else {
           qft_time_begin(p, st, QFT_KERNEL_GLOBAL);
-          k_large_global<FAC, qft_lib::kL1><<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph, fac);
+          if (comp) k_large_global<FAC, qft_lib::kL1, true><<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph, fac);
+          else k_large_global<FAC, qft_lib::kL1, false><<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph, fac);
         }
       }
       qft_time_end(p, st);
@@ -328,28 +370,6 @@ static inline int launch_any(qft_plan p, FAC fac, int64_t items, cudaStream_t st
 }
 
 }  // namespace
-
-// N = 2 rows of a ragged plan
-__global__ void k_ragged_n2(FacRaggedC2C<StC64> fac, int64_t rows) {
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row >= rows) return;
-  const auto io = fac.make(row);
-  const qc a = io.ld(0), b = io.ld(1);
-  io.st(0, cadd(a, b));
-  io.st(1, csub(a, b));
-}
-
-static inline int exec_ragged_class(qft_plan sub, const QftIoArgs* d_args, const int64_t* d_offsets,
-                                    const int32_t* d_rows, cudaStream_t st) {
-  FacRaggedC2C<StC64> f;
-  f.args = d_args; f.offsets = d_offsets; f.rows = d_rows; f.N = (int)sub->n;
-  if (sub->r == 1) {
-    const int64_t blocks = (sub->batch + 127) / 128;
-    k_ragged_n2<<<(unsigned)blocks, 128, 0, st>>>(f, sub->batch);
-    return qft_set_cuda(sub, cudaGetLastError());
-  }
-  return launch_any<FacRaggedC2C<StC64>>(sub, f, sub->batch, st);
-}
 
 template <class ST>
 static inline int exec_c2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
@@ -372,28 +392,5 @@ static inline int exec_c2c(qft_plan p, int op, const void* in, void* out, cudaSt
   }
   return launch_any<FacC2C<ST>>(p, f, p->batch, st, (size_t)p->n * sizeof(typename ST::elem),
                                 ((uintptr_t)in % 16) == 0);
-}
-
-static inline int exec_r2c(qft_plan p, int op, const void* in, void* out, cudaStream_t st) {
-  const int64_t items = (p->batch + 1) / 2;
-  const int N = (int)p->n;
-  if (op == QFT_OP_FORWARD || op == QFT_OP_INVERSE_ADJOINT) {
-    FacR2C<StC64> f;
-    f.in = static_cast<const float*>(in);
-    f.out = static_cast<qc*>(out);
-    f.rows = p->batch; f.N = N;
-    f.wscale = op == QFT_OP_FORWARD ? 0.f : 1.f / (float)N;
-    return launch_any<FacR2C<StC64>>(p, f, items, st, (size_t)2 * N * sizeof(float), ((uintptr_t)in % 16) == 0);
-  }
-  if (op == QFT_OP_INVERSE || op == QFT_OP_FORWARD_ADJOINT) {
-    FacC2R<StC64> f;
-    f.in = static_cast<const qc*>(in);
-    f.out = static_cast<float*>(out);
-    f.rows = p->batch; f.N = N;
-    if (op == QFT_OP_INVERSE) { f.wmid = 2.f; f.scale = 1.f / (float)N; }
-    else { f.wmid = 1.f; f.scale = 1.f; }
-    return launch_any<FacC2R<StC64>>(p, f, items, st);
-  }
-  return QFT_ERR_INVALID_ARG;
 }
 

@@ -93,11 +93,15 @@ struct QftNodeSub {
   int32_t group;      // nodes per CTA
   int32_t dst;        // 0: results to scratch A, 1: to scratch B
   int32_t cta_begin;  // first CTA (within one row) of this sub
+  int32_t comp;       // 1: the class tree runs on compensated pairs (lo parts loaded and stored too)
+  int32_t pad_;
   QftRowPlan plan;
 };
 
+// Segments of classes whose trees run on compensated pairs carry pad[2] = 1.
 struct QftLargePlan {
   int32_t r, L1, LF, NB;
+  int32_t comp_classes;           // J: classes 0..J-1 (both sides) run on compensated pairs
   int32_t nphase;
   QftLargePhase phases[QFT_LP_MAX_PHASES];
   int32_t nseg;

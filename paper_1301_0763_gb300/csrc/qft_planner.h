@@ -216,10 +216,18 @@ static inline int qft_build_row_plan(int r, QftTune t, QftRowPlan* P, int nt = 0
   return 0;
 }
 
+// Number of classes (of each side) whose trees the library evaluates on
+// compensated pairs by default: the FP32 error of the improved QFT grows like
+// ~3.5e-8 sqrt(N) (the secant conversion of eq qft_38A); running the J largest
+// classes on pairs h + l divides it by about 2^J, so J = floor((log2 N - 14)/2)
+// from N = 2^16 keeps it near 5e-6 for every N up to 2^24.
+static inline int qft_comp_classes(int r) { return r >= 16 ? (r - 14) / 2 : 0; }
+
 // ---------------------------------------------------------------------------
 // Schedule for rows longer than one CTA's shared memory (see qft_plan.h).
 // NB: log2 of the largest node (group) a CTA transforms in shared memory.
-static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_threads, QftLargePlan* P) {
+// J: classes 0..J-1 run on compensated pairs (their segments get pad[2] = 1).
+static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_threads, QftLargePlan* P, int J = 0) {
   memset(P, 0, sizeof *P);
   if (r < 4 || r > 24 || NB < 4 || NB > 14) return -1;
   if (t.L1 < 1 || t.L1 > 4 || t.LS < 1 || t.LS > 4 || t.LL < 0 || t.LL > 4 || t.LB < 1 || t.LB > 4 ||
@@ -228,6 +236,8 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
   int LF = t.LF;
   if (LF > r - 2) LF = r - 2;
   P->r = r; P->L1 = t.L1; P->LF = LF; P->NB = NB;
+  if (J < 0 || J > r - 2) return -1;
+  P->comp_classes = J;
   const int ncls = r - 1;
   int depth[32], Dn[32], nsl[32], cur[32];
   bool big[32];
@@ -246,6 +256,7 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
     memset(&s, 0, sizeof s);
     s.type = (uint8_t)type; s.side = (uint8_t)side; s.cls = (uint8_t)cls; s.L = (uint8_t)L; s.D = (uint8_t)D;
     s.pad[0] = (uint8_t)src; s.pad[1] = (uint8_t)dst;
+    s.pad[2] = (uint8_t)((type == QFT_SEG_F1_BIG || type == QFT_SEG_DIF || type == QFT_SEG_SLICE) && cls < J ? 1 : 0);
     s.begin = ph.ntasks; s.count = count;
     ph.ntasks += count;
     ph.nseg++;
@@ -272,6 +283,7 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
       Ls[j] = 0;
       if (!big[j] || depth[j] >= Dn[j]) continue;
       Ls[j] = Dn[j] - depth[j] < t.LS ? Dn[j] - depth[j] : t.LS;
+      if (j < J && Ls[j] > 3) Ls[j] = 3;   // compensated tiles hold at most 8 cells
       any = true;
     }
     if (!any) break;
@@ -302,6 +314,7 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
       if (S.group > S.nodes) S.group = S.nodes;
       S.dst = cur[j];
       S.cta_begin = cta;
+      S.comp = j < J ? 1 : 0;
       cta += S.nodes / S.group;
       // sub-plan: the row-plan phases of class j below depth D, counts per group
       QftRowPlan& Q = S.plan;
@@ -316,6 +329,7 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
         QftSeg& s = Q.segs[Q.nseg++];
         memset(&s, 0, sizeof s);
         s.type = (uint8_t)type; s.side = (uint8_t)side; s.cls = (uint8_t)j; s.L = (uint8_t)L; s.D = (uint8_t)Dd;
+        s.pad[2] = (uint8_t)(j < J ? 1 : 0);
         s.begin = Q.phase_ntasks[Q.nphase];
         s.count = count_row >> gshift;
         Q.phase_ntasks[Q.nphase] += s.count;
@@ -323,10 +337,16 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
       };
       auto qend = [&]() { Q.nphase++; Q.phase_seg0[Q.nphase] = Q.nseg; };
       int dd = D;
-      const int LLn = qft_leaf_levels(nb, nb, t);
+      // compensated subs keep two backward levels per SLICE phase inside the
+      // node: their tasks hold h and l parts across the phase's barrier
+      QftTune tn = t;
+      if (j < J && tn.LB > 2) tn.LB = 2;
+      int LLn = qft_leaf_levels(nb, nb, tn);
+      if (j < J && LLn > 3) LLn = 3;   // compensated tiles hold at most 8 cells
       while (b - dd > LLn) {   // DIF inside the node
         int L = b - dd - LLn;
         if (L > t.LS) L = t.LS;
+        if (j < J && L > 3) L = 3;
         qbegin(0);
         if (!qadd(QFT_SEG_DIF, L, dd, 1 << (b - L))) return -1;
         qend();
@@ -336,8 +356,8 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
       if (!qadd(QFT_SEG_LEAF, b - dd, dd, 1 << dd)) return -1;
       qend();
       while (dd > D) {          // SLICE inside the node (remainder first)
-        int L = (dd - D) % t.LB;
-        if (L == 0) L = t.LB;
+        int L = (dd - D) % tn.LB;
+        if (L == 0) L = tn.LB;
         qbegin(1);
         if (!qadd(QFT_SEG_SLICE, L, dd, 1 << (b - L))) return -1;
         qend();

@@ -202,7 +202,7 @@ struct NoHook {
 // groups of the large-row path); 0 for whole rows.  Plain phases end with a
 // barrier; SLICE phases run in rounds of NT tasks, all reads of a round before
 // any of its writes (the plan guarantees a node's tasks never straddle rounds).
-template <int L1, int NT, class IO, class HOOK = NoHook>
+template <int L1, int NT, class IO, class HOOK = NoHook, bool COMP = false>
 __device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e, const IO& io, int g,
                                                const HOOK& after_f1 = HOOK()) {
   const int tid = threadIdx.x;
@@ -233,22 +233,41 @@ __device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e
       for (int tau = t0; tau < nt; tau += stride) {
         while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
         const QftSeg& sg = P.segs[sgi];
-        run_plain_task<L1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin);
+        run_plain_task<L1, IO, COMP>(P.LF, sg, e, io, g * sg.count + tau - sg.begin);
       }
       __syncthreads();
       if (p == P.in_last_phase) after_f1();
     } else {
       for (int rb = 0; rb < nt; rb += NT) {
         const int tau = rb + tid;
-        SliceRegs s;
         const bool act = tau < nt;
-        if (act) {
-          while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
-          run_slice_read(P.segs[sgi], e, g * P.segs[sgi].count + tau - P.segs[sgi].begin, s);
+        if constexpr (COMP) {
+          // compensated segments keep the l parts as well (pad[2] of the segment)
+          SliceRegsC s;
+          bool cs = false;
+          if (act) {
+            while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
+            cs = P.segs[sgi].pad[2] != 0;
+            const int loc = g * P.segs[sgi].count + tau - P.segs[sgi].begin;
+            if (cs) run_slice_read_c<2>(P.segs[sgi], e, loc, s);
+            else run_slice_read(P.segs[sgi], e, loc, s.p);
+          }
+          __syncthreads();
+          if (act) {
+            if (cs) run_slice_write_c<2>(P.segs[sgi], e, s);
+            else run_slice_write(P.segs[sgi], e, s.p);
+          }
+          __syncthreads();
+        } else {
+          SliceRegs s;
+          if (act) {
+            while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
+            run_slice_read(P.segs[sgi], e, g * P.segs[sgi].count + tau - P.segs[sgi].begin, s);
+          }
+          __syncthreads();
+          if (act) run_slice_write(P.segs[sgi], e, s);
+          __syncthreads();
         }
-        __syncthreads();
-        if (act) run_slice_write(P.segs[sgi], e, s);
-        __syncthreads();
       }
     }
   }
@@ -301,6 +320,8 @@ k_rows(const QftRowPlan* __restrict__ gplan, const float* __restrict__ gsec, int
   e.side0 = side0; e.side1 = side1; e.sec = sec; e.r = r; e.N = N;
   e.tabC = reinterpret_cast<qc*>(smem + qft_lib::off_tab(N));
   e.tabS = e.tabC + (N >> P.LF) / 2 + 1;
+  e.lo0 = nullptr;
+  e.lo1 = nullptr;
   uint32_t parity = 0;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
     if (staged) {

@@ -11,10 +11,13 @@
 // routine that allocates, neither here nor through torch.
 //
 // Storage (file-scope device arrays, reserved when the module loads):
-//   g_static_scratch  64 MiB: scratch copies A and B and the FINAL tasks' C/S
-//                     tables of as many rows as fit (2 copies x 2 sides x
-//                     side_len cells plus N/8 + 4 table cells, 8 bytes each, per
-//                     row); rows beyond that are done in successive chunks.
+//   g_static_scratch  64 MiB: scratch copies A and B, the FINAL tasks' C/S
+//                     tables and, for n >= 2^16, the lo parts of both copies
+//                     (the compensated classes, as a plan of that length
+//                     evaluates them), for as many rows as fit (2 or 4 copies
+//                     x 2 sides x side_len cells plus N/8 + 4 table cells, 8
+//                     bytes each, per row); rows beyond that are done in
+//                     successive chunks.
 //   g_static_sec      Gray-ordered FP32 secants of Sec. 6.1 for N = 2^20; the
 //                     table for a shorter N is its prefix of N/4 entries.
 //   g_static_plans    the launch schedules for N = 2^15 ... 2^20.
@@ -81,7 +84,11 @@ static int host_setup() {
     t.L1 = qft_lib::kL1;
     t.LB = qft_lib::kLB;
     g_host_tunes[i] = t;
-    if (qft_build_large_plan(r, t, qft_lib::kNodeLog2, qft_lib::kNodeThreads, &g_host_plans[i]) != 0)
+    // the same precision as a plan of this length (compensated largest classes,
+    // whose node groups hold 2^11 cells)
+    const int J = qft_comp_classes(r);
+    if (qft_build_large_plan(r, t, J > 0 ? qft_lib::kNodeLog2 - 1 : qft_lib::kNodeLog2, qft_lib::kNodeThreads,
+                             &g_host_plans[i], J) != 0)
       return QFT_ERR_INVALID_N;
   }
   g_host_ready = true;
@@ -146,7 +153,9 @@ extern "C" int qft_execute_static_scratch(int64_t n, int64_t batch, int op, cons
   p.scratch = d.scratch;
   p.d_status = d.status;
   p.side_len = qft_side_len((int)n);
-  const int64_t per_row = 2 * 2 * (int64_t)p.side_len * (int64_t)sizeof(qc_storage) +
+  p.comp_j = g_host_plans[idx].comp_classes;
+  // two scratch copies (four with the lo parts of a compensated length) and the tables
+  const int64_t per_row = (p.comp_j > 0 ? 4 : 2) * 2 * (int64_t)p.side_len * (int64_t)sizeof(qc_storage) +
                           (int64_t)qft_lib::large_tab_cells((int)n, qft_lib::kLargeMinLF) * (int64_t)sizeof(qc_storage);
   int64_t rows = (int64_t)kStaticScratchBytes / per_row;
   if (rows > batch) rows = batch;

@@ -27,6 +27,7 @@ KIND_C2C, KIND_R2C, KIND_DCT0, KIND_DST0 = 0, 1, 2, 3
 DTYPE_F32, DTYPE_F16, DTYPE_BF16 = 0, 1, 2
 OP_FORWARD, OP_INVERSE, OP_FORWARD_ADJOINT, OP_INVERSE_ADJOINT = 0, 1, 2, 3
 PLAN_AUTOTUNE = 1
+PLAN_FP32_PLAIN = 2
 SCHEDULE_KEYS = ("threads", "L1", "LS", "LL", "LB", "LF", "staging", "node_log2", "node_threads", "chunk_rows")
 
 _lib = None
@@ -70,6 +71,7 @@ def load_library(path: str | None = None):
         lib.qft_execute_static_scratch.argtypes = [i64, i64, ci, vp, vp, vp]
         lib.qft_static_scratch_sync_status.argtypes = [vp]
         lib.qft_plan_set_wait_limit.argtypes = [vp, i64]
+        lib.qft_plan_comp_classes.argtypes = [vp]
         lib.qft_plan_withhold_next_copy.argtypes = [vp]
         lib.qft_plan_schedule.argtypes = [vp, ctypes.POINTER(ci)]
         lib.qft_plan_set_schedule.argtypes = [vp, ctypes.POINTER(ci)]
@@ -99,15 +101,23 @@ class Plan:
     """A plan of `batch` transforms of length `n` (see qft_plan_create)."""
 
     def __init__(self, n: int, batch: int, kind: int = KIND_C2C, dtype: int = DTYPE_F32, device=None,
-                 autotune: bool = False):
+                 autotune: bool = False, plain: bool = False):
         self.lib = load_library()
         self.n, self.batch, self.kind, self.dtype = int(n), int(batch), int(kind), int(dtype)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         self.handle = ctypes.c_void_p()
+        flags = (PLAN_AUTOTUNE if autotune else 0) | (PLAN_FP32_PLAIN if plain else 0)
         with torch.cuda.device(self.device):
             _check(self.lib.qft_plan_create(ctypes.byref(self.handle), self.n, self.batch, self.kind,
-                                            self.dtype, PLAN_AUTOTUNE if autotune else 0), "qft_plan_create")
+                                            self.dtype, flags), "qft_plan_create")
+
+    def comp_classes(self) -> int:
+        """Classes per side evaluated on compensated FP32 pairs (qft_plan_comp_classes)."""
+        rc = int(self.lib.qft_plan_comp_classes(self.handle))
+        if rc < 0:
+            raise QFTError(rc, "qft_plan_comp_classes")
+        return rc
 
     def time_launches(self, enable: bool = True):
         _check(self.lib.qft_plan_time_launches(self.handle, 1 if enable else 0), "qft_plan_time_launches")
@@ -176,7 +186,7 @@ class RaggedPlan(Plan):
     [offsets[i], offsets[i+1]) and has length 2^log2n[i].  One execute is one
     CUDA-graph launch of every length class."""
 
-    def __init__(self, offsets, log2n, device=None, autotune: bool = False):
+    def __init__(self, offsets, log2n, device=None, autotune: bool = False, plain: bool = False):
         import numpy as np
         self.lib = load_library()
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
@@ -191,7 +201,7 @@ class RaggedPlan(Plan):
             _check(self.lib.qft_plan_create_ragged(
                 ctypes.byref(self.handle), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                 lg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.count, KIND_C2C, DTYPE_F32,
-                PLAN_AUTOTUNE if autotune else 0),
+                (PLAN_AUTOTUNE if autotune else 0) | (PLAN_FP32_PLAIN if plain else 0)),
                 "qft_plan_create_ragged")
 
 

@@ -16,7 +16,7 @@
 
 using namespace qft;
 
-template <class IO>
+template <class IO, bool COMP = false>
 static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr, int g = 0) {
   for (int p = 0; p < P.nphase; ++p) {
     const int nt = P.phase_ntasks[p];
@@ -27,11 +27,11 @@ static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr, i
       for (int tau = 0; tau < nt; ++tau) {
         const QftSeg& sg = find_seg(P, p, tau);
         switch (P.L1) {
-        case 0: run_plain_task<0>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
-        case 1: run_plain_task<1>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
-        case 2: run_plain_task<2>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
-        case 3: run_plain_task<3>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
-        default: run_plain_task<4>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+        case 0: run_plain_task<0, IO, COMP>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+        case 1: run_plain_task<1, IO, COMP>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+        case 2: run_plain_task<2, IO, COMP>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+        case 3: run_plain_task<3, IO, COMP>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
+        default: run_plain_task<4, IO, COMP>(P.LF, sg, e, io, g * sg.count + tau - sg.begin); break;
         }
       }
       continue;
@@ -43,15 +43,15 @@ static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr, i
           int first = (tid - sg.begin) % nthr;
           if (first < 0) first += nthr;
           switch (P.L1) {
-          case 0: run_plain_segment<0>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
-          case 1: run_plain_segment<1>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
-          case 2: run_plain_segment<2>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
-          case 3: run_plain_segment<3>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
-          default: run_plain_segment<4>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
+          case 0: run_plain_segment<0, IO, COMP>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
+          case 1: run_plain_segment<1, IO, COMP>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
+          case 2: run_plain_segment<2, IO, COMP>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
+          case 3: run_plain_segment<3, IO, COMP>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
+          default: run_plain_segment<4, IO, COMP>(P.LF, sg, e, io, first, sg.count, nthr, g); break;
           }
         }
     } else {
-      std::vector<SliceRegs> regs(nthr);
+      std::vector<SliceRegsC> regs(nthr);
       std::vector<int> segi(nthr);
       for (int rb = 0; rb < nt; rb += nthr) {
         for (int tid = 0; tid < nthr; ++tid) {
@@ -60,11 +60,16 @@ static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr, i
           if (tau < nt) {
             const QftSeg& sg = find_seg(P, p, tau);
             segi[tid] = (int)(&sg - P.segs);
-            run_slice_read(sg, e, g * sg.count + tau - sg.begin, regs[tid]);
+            if (COMP && sg.pad[2]) run_slice_read_c<2>(sg, e, g * sg.count + tau - sg.begin, regs[tid]);
+            else run_slice_read(sg, e, g * sg.count + tau - sg.begin, regs[tid].p);
           }
         }
         for (int tid = 0; tid < nthr; ++tid)
-          if (segi[tid] >= 0) run_slice_write(P.segs[segi[tid]], e, regs[tid]);
+          if (segi[tid] >= 0) {
+            const QftSeg& sg = P.segs[segi[tid]];
+            if (COMP && sg.pad[2]) run_slice_write_c<2>(sg, e, regs[tid]);
+            else run_slice_write(sg, e, regs[tid].p);
+          }
       }
     }
   }
@@ -90,6 +95,7 @@ struct Row {
     tab.assign((N >> P.LF) + 2, mkc(NAN, NAN));
     e.tabC = tab.data();
     e.tabS = tab.data() + (N >> P.LF) / 2 + 1;
+    e.lo0 = nullptr; e.lo1 = nullptr;
   }
 };
 
@@ -199,11 +205,14 @@ template <class IO>
 static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vector<qc>& B, int side_len,
                           const float* gsec, const IO& io) {
   std::vector<qc> tab(((1 << LP.r) >> LP.LF) + 4, mkc(NAN, NAN));
+  std::vector<qc> Alo(2 * side_len, mkc(NAN, NAN)), Blo(2 * side_len, mkc(NAN, NAN));
   auto eng = [&](int copy) {
     Eng e;
     qc* base = copy ? B.data() : A.data();
+    qc* lb = copy ? Blo.data() : Alo.data();
     e.side0 = base; e.side1 = base + side_len; e.sec = gsec; e.r = LP.r; e.N = 1 << LP.r;
     e.tabC = tab.data(); e.tabS = tab.data() + ((1 << LP.r) >> LP.LF) / 2 + 1;
+    e.lo0 = lb; e.lo1 = lb + side_len;
     return e;
   };
   for (int ph = 0; ph < LP.nphase; ++ph) {
@@ -228,7 +237,7 @@ static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vecto
             if (first < 0) first += ((-first + NT - 1) / NT) * NT;
             int end = T1 - sg.begin;
             if (end > sg.count) end = sg.count;
-            run_plain_segment<3>(LP.LF, sg, e, io, first, end, NT, 0);
+            run_plain_segment<3, IO, true>(LP.LF, sg, e, io, first, end, NT, 0);
           }
         }
     } else if (P.kind == QFT_LPH_SLICE) {
@@ -236,9 +245,15 @@ static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vecto
         int s = P.seg0;
         while (s + 1 < P.seg0 + P.nseg && LP.segs[s + 1].begin <= tau) ++s;
         const QftSeg& sg = LP.segs[s];
-        SliceRegs regs;
-        run_slice_read(sg, eng(sg.pad[0]), tau - sg.begin, regs);
-        run_slice_write(sg, eng(sg.pad[1]), regs);
+        if (sg.pad[2]) {
+          SliceRegsC regs;
+          run_slice_read_c(sg, eng(sg.pad[0]), tau - sg.begin, regs);
+          run_slice_write_c(sg, eng(sg.pad[1]), regs);
+        } else {
+          SliceRegs regs;
+          run_slice_read(sg, eng(sg.pad[0]), tau - sg.begin, regs);
+          run_slice_write(sg, eng(sg.pad[1]), regs);
+        }
       }
     } else {
       std::vector<float> secp(gsec, gsec + (1 << LP.NB) + 1);
@@ -249,17 +264,26 @@ static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vecto
           const int ncell = S.group << S.nb;
           const int base = cls_off(LP.r, S.cls) + g * ncell;
           const int pb = qft_pidx(base), pn = qft_pidx(ncell - 1) + 1;
-          std::vector<qc> win(pn);
+          std::vector<qc> win(pn), lwin(pn, mkc(NAN, NAN));
           const Eng ea = eng(0);
           const qc* src = side_ptr(ea, S.side) + pb;
           for (int i = 0; i < pn; ++i) win[i] = src[i];
+          if (S.comp) {
+            const qc* lsrc = lo_ptr(ea, S.side) + pb;
+            for (int i = 0; i < pn; ++i) lwin[i] = lsrc[i];
+          }
           Eng e;
           e.side0 = win.data() - pb; e.side1 = win.data() - pb;
           e.sec = secp.data(); e.r = LP.r; e.N = 1 << LP.r; e.tabC = nullptr; e.tabS = nullptr;
-          run_row(S.plan, e, NoIO(), 512, g);
+          e.lo0 = lwin.data() - pb; e.lo1 = lwin.data() - pb;
+          run_row<NoIO, true>(S.plan, e, NoIO(), 512, g);
           const Eng ed = eng(S.dst);
           qc* dst = side_ptr(ed, S.side) + pb;
           for (int i = 0; i < pn; ++i) dst[i] = win[i];
+          if (S.comp) {
+            qc* ldst = lo_ptr(ed, S.side) + pb;
+            for (int i = 0; i < pn; ++i) ldst[i] = lwin[i];
+          }
         }
       }
     }
@@ -267,10 +291,13 @@ static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vecto
 }
 
 // op as in emu_c2c (complex64 rows)
-extern "C" int emu_c2c_large(int N, int64_t batch, const float* in, float* out, int op) {
+// plain = 1: every class tree in plain FP32 (else the library's compensated classes)
+// plain = 1: J = 0; plain < 0: J = -plain (another count, for tests)
+extern "C" int emu_c2c_large(int N, int64_t batch, const float* in, float* out, int op, int plain, int NB) {
   int r = 0; while ((1 << r) < N) ++r;
   QftTune t = qft_default_tune(r);
-  if (qft_build_large_plan(r, t, 12, 512, &g_lp) != 0) return -2;
+  const int J = plain > 0 ? 0 : (plain < 0 ? -plain : qft_comp_classes(r));
+  if (qft_build_large_plan(r, t, NB, 512, &g_lp, J) != 0) return -2;
   std::vector<float> gsec(N / 4 + 1, 0.f);
   qft_fill_gray_secants(r, gsec.data());
   const int side_len = qft_side_len(N);
@@ -290,10 +317,11 @@ extern "C" int emu_c2c_large(int N, int64_t batch, const float* in, float* out, 
 }
 
 // R2C family on the large path (op as in emu_r2c)
-extern "C" int emu_r2c_large(int N, int64_t batch, const float* in, float* out, int op) {
+extern "C" int emu_r2c_large(int N, int64_t batch, const float* in, float* out, int op, int plain) {
   int r = 0; while ((1 << r) < N) ++r;
   QftTune t = qft_default_tune(r);
-  if (qft_build_large_plan(r, t, 12, 512, &g_lp) != 0) return -2;
+  const int J = plain ? 0 : qft_comp_classes(r);
+  if (qft_build_large_plan(r, t, J > 0 ? 11 : 12, 512, &g_lp, J) != 0) return -2;
   std::vector<float> gsec(N / 4 + 1, 0.f);
   qft_fill_gray_secants(r, gsec.data());
   const int side_len = qft_side_len(N);

@@ -129,15 +129,52 @@ def test_half_storage_bit_exact(lg, dtype):
 @pytest.mark.parametrize("lg", [15, 16, 17, 18, 20])
 def test_large_path_forward_bit_exact(lg):
     """Rows longer than one CTA (global phases + shared-memory node groups +
-    ping-pong slices) reproduce the FP32 recursion bit for bit."""
+    ping-pong slices) reproduce the FP32 recursion bit for bit -- with the
+    library's compensated classes (from N = 2^16) and in plain FP32."""
     N = 1 << lg
     z = inputs.normal_complex(1, N, seed=20 + lg)
     assert bits_equal(emu.c2c_large(z), orc.cdft(z, fp32=True).astype(np.complex64))
+    assert bits_equal(emu.c2c_large(z, plain=True), orc.cdft(z, fp32=True, comp=False).astype(np.complex64))
+
+
+@pytest.mark.parametrize("lg", [16, 18])
+@pytest.mark.parametrize("node_log2", [10, 11])
+def test_large_path_node_sizes(lg, node_log2):
+    """Node groups of 2^10 and 2^11 cells (the compensated plans' default is
+    2^11; 2^12 would put more tasks on one node than a CTA has threads): same bits."""
+    N = 1 << lg
+    z = inputs.normal_complex(1, N, seed=40 + lg)
+    assert bits_equal(emu.c2c_large(z, node_log2=node_log2), orc.cdft(z, fp32=True).astype(np.complex64))
+
+
+@pytest.mark.parametrize("lg", [7, 8, 10, 12])
+@pytest.mark.parametrize("J", [1, 2])
+def test_large_path_compensated_classes_small_n(lg, J):
+    """The compensated class trees at small N (the class count forced on both
+    sides), where every launch of the large-row path is exercised in seconds."""
+    import ctypes
+    N = 1 << lg
+    z = inputs.normal_complex(2, N, seed=60 + lg).astype(np.complex64)
+    L = emu.load()
+    fp = ctypes.POINTER(ctypes.c_float)
+    out = np.empty_like(z)
+    assert L.emu_c2c_large(N, 2, z.view(np.float32).ctypes.data_as(fp), out.view(np.float32).ctypes.data_as(fp),
+                           0, -J, 12) == 0
+    lib = orc._load32(True)
+    lib.oracle_set_comp_classes.argtypes = [ctypes.c_int]
+    lib.oracle_set_comp_classes(J)
+    try:
+        ref = orc.cdft(z, fp32=True).astype(np.complex64)
+    finally:
+        lib.oracle_set_comp_classes(-1)
+    assert bits_equal(out, ref)
+    assert not bits_equal(ref, orc.cdft(z, fp32=True, comp=False).astype(np.complex64))
 
 
 @pytest.mark.parametrize("op", [1, 2, 3])
-def test_large_path_other_ops(op):
-    N = 1 << 15
+@pytest.mark.parametrize("lg", [15, 16])
+def test_large_path_other_ops(op, lg):
+    N = 1 << lg
     z = inputs.uniform_complex(2, N, seed=op)
     ref = {1: lambda: orc.icdft(z, fp32=True), 2: lambda: orc.cdft_adjoint(z, fp32=True),
            3: lambda: orc.cdft(z, fp32=True) / N}[op]()
@@ -152,6 +189,7 @@ def test_large_path_real():
     assert bits_equal(emu.r2c_large(X, 1, N), orc.irdft(X, N, fp32=True).astype(np.float32))
     assert bits_equal(emu.r2c_large(X, 2, N), orc.rdft_adjoint(X, N, fp32=True).astype(np.float32))
     assert bits_equal(emu.r2c_large(x, 3, N), orc.irdft_adjoint(x, fp32=True).astype(np.complex64))
+    assert bits_equal(emu.r2c_large(x, 0, N, plain=True), orc.rdft(x, fp32=True, comp=False).astype(np.complex64))
 
 
 @pytest.mark.parametrize("lg", [2, 3, 4, 6, 9, 12, 14])

@@ -4,12 +4,14 @@ Every call goes through the C ABI (paper_1301_0763_gb300.qft -> _qft_gb300.so).
 Two bars:
  * bit-exact: the kernels perform exactly the operations of the recursion of
    Sec. 5 in FP32, so their output equals the oracle evaluated in FP32
-   (same source, -DORACLE_REAL=float) bit for bit;
+   (same source, -DORACLE_REAL=float) bit for bit.  From N = 2^16 on, the
+   largest classes run on compensated FP32 pairs by default; the oracle's
+   compensated build (-DORACLE_COMPENSATED, the default of fp32=True) follows
+   the same operations.  Plans created with QFT_PLAN_FP32_PLAIN are compared
+   with the plain FP32 oracle (comp=False).
  * tolerance: against the FP64 oracle, max relative L2 error per row <= 1e-5
-   (the target) for N <= 2^16.  Above that the FP32 error of the method itself
-   (measured on the CPU with the FP32 oracle, independent of any kernel) grows
-   like ~3.5e-8 sqrt(N), so the bound used is tol(N) = 6e-8 sqrt(N) (the
-   measured maxima: 1.9e-5 at 2^18, 3.6e-5 at 2^20, 8.1e-5 at 2^22).
+   at every N (the target; the compensated classes keep the FP32 error near
+   5e-6 up to 2^24).
 """
 import numpy as np
 import pytest
@@ -24,7 +26,7 @@ TOL = 1e-5
 
 
 def tol(N):
-    return max(TOL, 6e-8 * np.sqrt(N))
+    return TOL
 
 
 @pytest.fixture(scope="module")
@@ -654,3 +656,29 @@ def test_autograd_fft_complex32_storage(q):
     gc = gf[..., 0].astype(np.float64) + 1j * gf[..., 1]
     ref = orc.cdft_adjoint(gc, fp32=True).astype(np.complex64).view(np.float32).reshape(rows, N, 2)
     assert np.array_equal(gx, ref.astype(np.float16).view(np.uint16))
+
+
+# ------------------------------------------------------- precision modes
+@pytest.mark.parametrize("lg", [16, 18, 20])
+def test_compensated_default_and_plain_flag(q, lg):
+    """Default plans of N >= 2^16 run J = floor((log2 N - 14)/2) classes on
+    compensated pairs: bits of the compensated FP32 oracle, error <= 1e-5.
+    QFT_PLAN_FP32_PLAIN gives the bits of the plain FP32 oracle instead."""
+    N = 1 << lg
+    rows = 3
+    z = inputs.normal_complex(rows, N, seed=90 + lg)
+    x = gpu(z)
+    pc = q.Plan(N, rows)
+    pp = q.Plan(N, rows, plain=True)
+    assert pc.comp_classes() == (lg - 14) // 2 and pp.comp_classes() == 0
+    yc = torch.empty_like(x)
+    yp = torch.empty_like(x)
+    pc.execute(q.OP_FORWARD, x, yc)
+    pp.execute(q.OP_FORWARD, x, yp)
+    torch.cuda.synchronize()
+    assert bits_equal(yc.cpu().numpy(), orc.cdft(z, fp32=True).astype(np.complex64))
+    assert bits_equal(yp.cpu().numpy(), orc.cdft(z, fp32=True, comp=False).astype(np.complex64))
+    assert rel_rows(yc.cpu().numpy().astype(np.complex128), orc.cdft(z)).max() < TOL
+    pc.destroy()
+    pp.destroy()
+    assert q.Plan(1 << 14, 1).comp_classes() == 0

@@ -360,3 +360,30 @@ def test_dct0_dst0_batched_match_definitions(N):
     assert np.abs(orc.dst0(d, N) - S_ref).max() < 1e-13 * N
     assert np.abs(orc.dct0(c, fp32=True) - C_ref).max() < 1e-5 * N
     assert np.abs(orc.dst0(d, N, fp32=True) - S_ref).max() < 1e-5 * N
+
+
+# ------------------------------------------------- compensated FP32 evaluation
+@pytest.mark.parametrize("lg", [4, 10, 14, 15])
+def test_compensated_mode_is_plain_below_2e16(lg):
+    """J = floor((log2 N - 14)/2) compensated classes: none below N = 2^16, so
+    the compensated build gives the plain FP32 bits there."""
+    N = 1 << lg
+    z = inputs.normal_complex(3, N, seed=700 + lg)
+    assert np.array_equal(orc.cdft(z, fp32=True), orc.cdft(z, fp32=True, comp=False))
+
+
+@pytest.mark.parametrize("lg", [16, 18, 20])
+def test_compensated_mode_meets_1e5(lg):
+    """The compensated FP32 evaluation is within 1e-5 (relative L2) of the
+    long-double reference DFT at N = 2^16 .. 2^20, where the plain FP32
+    evaluation of the same recursion is not (or barely): the error of the
+    secant conversion (eq qft_38A) is what the pairs remove.  A dropped l term
+    or a wrong TwoSum sign leaves the plain error in place and fails here."""
+    N = 1 << lg
+    rows = 3 if lg < 20 else 2
+    z = inputs.normal_complex(rows, N, seed=710 + lg).astype(np.complex128)
+    exact = np.array([orc.fft_ld(r) for r in z])
+    ec = np.linalg.norm(orc.cdft(z, fp32=True) - exact, axis=1) / np.linalg.norm(exact, axis=1)
+    ep = np.linalg.norm(orc.cdft(z, fp32=True, comp=False) - exact, axis=1) / np.linalg.norm(exact, axis=1)
+    assert ec.max() < 7.5e-6
+    assert ec.max() < 0.7 * ep.min()
