@@ -273,8 +273,12 @@ def run_gpu(args):
     # element's 8-byte cell once (the C/S table launches of the large-row path
     # move less and are counted as passes, so this is an upper estimate); the
     # ncu capture of the NODE kernel measured 0.98 of its pass bytes
-    roof["traffic_ratio_est"] = {f"2^{lg}": round(sum(n for (_, n) in kt[lg].values()) / args.steps, 2)
-                                 for lg in logs}
+    def passes(lg):
+        launches = sum(n for (_, n) in kt[lg].values()) / args.steps
+        cr = plans[lg].schedule()["chunk_rows"]
+        chunks = -(-(ELEMS >> lg) // cr) if cr > 0 else 1
+        return round(launches / chunks, 2)
+    roof["traffic_ratio_est"] = {f"2^{lg}": passes(lg) for lg in logs}
 
     # ------------------------------------------------------- accuracy sample
     err_max, err_mean = 0.0, [float("nan")]

@@ -144,7 +144,6 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype, int 
       p->side_len = qft_side_len((int)N);
       // the largest classes run on compensated pairs unless the plan asks for plain FP32
       p->comp_j = plain ? 0 : qft_comp_classes(r);
-      if (p->comp_j > 0) p->node_log2 = qft_lib::kNodeLog2 - 1;   // four node buffers: two CTAs per SM
       const int64_t items = kind == QFT_KIND_C2C ? batch : (batch + 1) / 2;   // real kinds: row pairs
       // two copies of the class data plus the FINAL tasks' C/S tables, plus
       // the lo parts of both copies for compensated plans
@@ -397,6 +396,27 @@ static int ragged_launch_all(qft_plan p, cudaStream_t st) {
   return QFT_OK;
 }
 
+// The same launches on one forked stream per length class (ss[c], created by
+// the caller before the capture), joined back into `st` through the events
+// ev[0..n] (used while capturing the graph): the classes share nothing but the
+// argument block, which they only read, so their launches may overlap, and
+// the small classes fill the SMs the large ones leave idle at their tails.
+static int ragged_launch_forked(qft_plan p, cudaStream_t st, cudaStream_t* ss, cudaEvent_t* ev) {
+  const int n = p->nclasses;
+  cudaError_t e = cudaEventRecord(ev[n], st);
+  int rc = QFT_OK;
+  for (int c = 0; c < n && e == cudaSuccess && rc == QFT_OK; ++c) {
+    e = cudaStreamWaitEvent(ss[c], ev[n], 0);
+    if (e != cudaSuccess) break;
+    rc = qft_launch_ragged_class(p->classes[c].sub, p->d_args, p->d_offsets, p->classes[c].d_rows, ss[c]);
+    if (rc != QFT_OK) { p->last_cuda = p->classes[c].sub->last_cuda; break; }
+    e = cudaEventRecord(ev[c], ss[c]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[c], 0);
+  }
+  if (rc == QFT_OK && e != cudaSuccess) rc = qft_set_cuda(p, e);
+  return rc;
+}
+
 extern "C" int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host, const int32_t* log2n_host,
                                       int64_t count, int kind, int dtype, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
@@ -455,10 +475,15 @@ extern "C" int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host
   if (rc == QFT_OK && p->nclasses > 0) {
     // capture every class launch once; executes replay the graph
     cudaStream_t cs = nullptr;
-    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    const int nc = p->nclasses;
+    cudaStream_t* fs = (cudaStream_t*)calloc((size_t)nc, sizeof(cudaStream_t));
+    cudaEvent_t* fe = (cudaEvent_t*)calloc((size_t)nc + 1, sizeof(cudaEvent_t));
+    e = (fs && fe) ? cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) : cudaErrorMemoryAllocation;
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) e = cudaStreamCreateWithFlags(&fs[c], cudaStreamNonBlocking);
+    for (int c = 0; c <= nc && e == cudaSuccess; ++c) e = cudaEventCreateWithFlags(&fe[c], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      const int lrc = ragged_launch_all(p, cs);
+      const int lrc = ragged_launch_forked(p, cs, fs, fe);
       cudaGraph_t g = nullptr;
       const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
       if (lrc == QFT_OK && e2 == cudaSuccess) {
@@ -473,6 +498,10 @@ extern "C" int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host
       }
     }
     if (cs) cudaStreamDestroy(cs);
+    for (int c = 0; fs && c < nc; ++c) if (fs[c]) cudaStreamDestroy(fs[c]);
+    for (int c = 0; fe && c <= nc; ++c) if (fe[c]) cudaEventDestroy(fe[c]);
+    free(fs);
+    free(fe);
     if (e != cudaSuccess) {   // no graph: executes launch the classes directly
       if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
       p->gexec = nullptr;

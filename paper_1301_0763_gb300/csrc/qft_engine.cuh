@@ -75,10 +75,11 @@ QFT_HD qc mkc(float x, float y) { qc r; r.x = x; r.y = y; return r; }
 // Complex adds and subtracts use the packed two-lane FP32 instructions
 // (add/sub.rn.f32x2, one instruction per complex value); multiplies by a
 // secant or a scale use the scalar round-to-nearest intrinsic per lane.  With
-// both packed multiplies and packed adds in one kernel, sm_103a builds did not
-// reproduce the FP32 evaluation of the recursion bit for bit (each of the
-// three packed forms alone does, in isolation and in the whole engine), so
-// the packed multiply is not used.  QFT_SCALAR_ARITH selects scalar adds too.
+// both packed multiplies (mul/fma.rn.f32x2) and packed adds in one kernel,
+// sm_103a builds did not reproduce the FP32 evaluation of the recursion bit
+// for bit (checked again with the compensated products: N = 16 already
+// differs), so the packed multiply is not used.  QFT_SCALAR_ARITH selects
+// scalar adds too.
 #if defined(__CUDA_ARCH__) && !defined(QFT_SCALAR_ARITH)
 QFT_HD qc cadd(qc a, qc b) {
   qc r;
@@ -548,18 +549,22 @@ QFT_HD void task_slice_read(const Eng& e, int j, int D, int tau, SliceRegs& s) {
   }
   s.hv = hv;
   s.base = nbase + (rr << L);
+  // the backward levels run here, so that only the 2^L outputs stay live until
+  // the write (across the SLICE round's barrier in the row kernel)
+  qc w[1 << L];
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) w[t] = s.w[t];
+  bwd_chunk<L, SIDE>(w, s.h, hv);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) s.w[t] = w[t];
 }
 
 template <int L, int SIDE>
 QFT_HD void task_slice_write(const Eng& e, SliceRegs& s) {
-  qc w[1 << L];
-#pragma unroll
-  for (int t = 0; t < (1 << L); ++t) w[t] = s.w[t];
-  bwd_chunk<L, SIDE>(w, s.h, s.hv);
   qc* A = side_ptr(e, SIDE);
   const int p0 = qft_pidx(s.base);   // s.base is a multiple of 2^L <= 16
 #pragma unroll
-  for (int t = 0; t < (1 << L); ++t) A[p0 + t] = w[t];
+  for (int t = 0; t < (1 << L); ++t) A[p0 + t] = s.w[t];
 }
 
 template <int L, int SIDE>
@@ -596,23 +601,26 @@ QFT_HD void task_slice_read_c(const Eng& e, int j, int D, int tau, SliceRegsC& s
   s.p.hv = hv;
   s.root = D == L;
   s.p.base = nbase + (rr << L);
+  // backward levels now: only the outputs stay live until the write
+  qc w[1 << L], wl[1 << L];
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) { w[t] = s.p.w[t]; wl[t] = s.wl[t]; }
+  bwd_chunk_c<L, SIDE>(w, wl, s.p.h, s.hl, hv);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) { s.p.w[t] = w[t]; s.wl[t] = wl[t]; }
 }
 
 template <int L, int SIDE>
 QFT_HD void task_slice_write_c(const Eng& e, SliceRegsC& s) {
-  qc w[1 << L], wl[1 << L];
-#pragma unroll
-  for (int t = 0; t < (1 << L); ++t) { w[t] = s.p.w[t]; wl[t] = s.wl[t]; }
-  bwd_chunk_c<L, SIDE>(w, wl, s.p.h, s.hl, s.p.hv);
   qc* A = side_ptr(e, SIDE);
   qc* Al = lo_ptr(e, SIDE);
   const int p0 = qft_pidx(s.p.base);
   if (s.root) {
 #pragma unroll
-    for (int t = 0; t < (1 << L); ++t) A[p0 + t] = cadd(w[t], wl[t]);   // class output, rounded once
+    for (int t = 0; t < (1 << L); ++t) A[p0 + t] = cadd(s.p.w[t], s.wl[t]);   // class output, rounded once
   } else {
 #pragma unroll
-    for (int t = 0; t < (1 << L); ++t) { A[p0 + t] = w[t]; Al[p0 + t] = wl[t]; }
+    for (int t = 0; t < (1 << L); ++t) { A[p0 + t] = s.p.w[t]; Al[p0 + t] = s.wl[t]; }
   }
 }
 

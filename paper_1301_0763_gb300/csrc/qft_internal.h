@@ -32,7 +32,7 @@ constexpr int kMaxRowLog2 = 14;   // largest row one CTA transforms in shared me
 constexpr int kMaxLog2 = 24;      // largest transform length
 constexpr int kNodeLog2 = 12;     // largest node group of the large-row path (cells)
 constexpr int kNodeThreads = 512;
-constexpr int64_t kScratchBudget = (int64_t)8 << 30;   // bytes of scratch per plan
+constexpr int64_t kScratchBudget = (int64_t)16 << 30;  // bytes of scratch per plan
 constexpr int kL1 = 3;            // mirror levels per F1 task (register tile 2^kL1 per side)
 constexpr int kLB = 3;            // backward levels per SLICE task (QFT_MAX_LB)
 

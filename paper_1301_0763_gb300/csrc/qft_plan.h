@@ -71,6 +71,11 @@ struct QftRowPlan {
 //   SLICE   the backward levels above the node depth, reading one scratch copy
 //           and writing the other (no in-place hazard between CTAs).
 #define QFT_LP_MAX_PHASES 16
+// most backward levels one SLICE task of a compensated class does inside a
+// NODE group (its pairs stay in registers across the SLICE round's barrier)
+#ifndef QFT_COMP_NODE_LB
+#define QFT_COMP_NODE_LB 3
+#endif
 #define QFT_LP_MAX_SEGS 160
 #define QFT_LP_MAX_SUB 48
 

@@ -337,10 +337,11 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
       };
       auto qend = [&]() { Q.nphase++; Q.phase_seg0[Q.nphase] = Q.nseg; };
       int dd = D;
-      // compensated subs keep two backward levels per SLICE phase inside the
-      // node: their tasks hold h and l parts across the phase's barrier
+      // compensated subs keep at most QFT_COMP_NODE_LB backward levels per
+      // SLICE phase inside the node: their tasks hold h and l parts across
+      // the phase's barrier
       QftTune tn = t;
-      if (j < J && tn.LB > 2) tn.LB = 2;
+      if (j < J && tn.LB > QFT_COMP_NODE_LB) tn.LB = QFT_COMP_NODE_LB;
       int LLn = qft_leaf_levels(nb, nb, tn);
       if (j < J && LLn > 3) LLn = 3;   // compensated tiles hold at most 8 cells
       while (b - dd > LLn) {   // DIF inside the node

@@ -249,12 +249,12 @@ __device__ __forceinline__ void run_row_phases(const QftRowPlan& P, const Eng& e
             while (sgi + 1 < sge && P.segs[sgi + 1].begin <= tau) ++sgi;
             cs = P.segs[sgi].pad[2] != 0;
             const int loc = g * P.segs[sgi].count + tau - P.segs[sgi].begin;
-            if (cs) run_slice_read_c<2>(P.segs[sgi], e, loc, s);
+            if (cs) run_slice_read_c<QFT_COMP_NODE_LB>(P.segs[sgi], e, loc, s);
             else run_slice_read(P.segs[sgi], e, loc, s.p);
           }
           __syncthreads();
           if (act) {
-            if (cs) run_slice_write_c<2>(P.segs[sgi], e, s);
+            if (cs) run_slice_write_c<QFT_COMP_NODE_LB>(P.segs[sgi], e, s);
             else run_slice_write(P.segs[sgi], e, s.p);
           }
           __syncthreads();

@@ -84,11 +84,9 @@ static int host_setup() {
     t.L1 = qft_lib::kL1;
     t.LB = qft_lib::kLB;
     g_host_tunes[i] = t;
-    // the same precision as a plan of this length (compensated largest classes,
-    // whose node groups hold 2^11 cells)
-    const int J = qft_comp_classes(r);
-    if (qft_build_large_plan(r, t, J > 0 ? qft_lib::kNodeLog2 - 1 : qft_lib::kNodeLog2, qft_lib::kNodeThreads,
-                             &g_host_plans[i], J) != 0)
+    // the same precision as a plan of this length (compensated largest classes)
+    if (qft_build_large_plan(r, t, qft_lib::kNodeLog2, qft_lib::kNodeThreads, &g_host_plans[i],
+                             qft_comp_classes(r)) != 0)
       return QFT_ERR_INVALID_N;
   }
   g_host_ready = true;

@@ -94,13 +94,12 @@ def plan_info(N, tune=None):
 
 def c2c_large(z, op=0, plain=False, node_log2=None):
     """The large-row launch sequence on the host; plain=True runs every class
-    tree in plain FP32 instead of the library's compensated classes.  The node
-    size defaults to the library's: 2^11 cells with compensated classes
-    (N >= 2^16), else 2^12."""
+    tree in plain FP32 instead of the library's compensated classes (node
+    groups of 2^node_log2 cells, the library's default 2^12)."""
     z = np.ascontiguousarray(z, dtype=np.complex64)
     N = z.shape[-1]
     if node_log2 is None:
-        node_log2 = 12 if plain or N < (1 << 16) else 11
+        node_log2 = 12
     out = np.empty_like(z)
     rc = load().emu_c2c_large(N, z.size // N, _fp(z.view(np.float32)), _fp(out.view(np.float32)), op,
                               1 if plain else 0, node_log2)

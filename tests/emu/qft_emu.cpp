@@ -60,14 +60,14 @@ static void run_row(const QftRowPlan& P, const Eng& e, const IO& io, int nthr, i
           if (tau < nt) {
             const QftSeg& sg = find_seg(P, p, tau);
             segi[tid] = (int)(&sg - P.segs);
-            if (COMP && sg.pad[2]) run_slice_read_c<2>(sg, e, g * sg.count + tau - sg.begin, regs[tid]);
+            if (COMP && sg.pad[2]) run_slice_read_c<QFT_COMP_NODE_LB>(sg, e, g * sg.count + tau - sg.begin, regs[tid]);
             else run_slice_read(sg, e, g * sg.count + tau - sg.begin, regs[tid].p);
           }
         }
         for (int tid = 0; tid < nthr; ++tid)
           if (segi[tid] >= 0) {
             const QftSeg& sg = P.segs[segi[tid]];
-            if (COMP && sg.pad[2]) run_slice_write_c<2>(sg, e, regs[tid]);
+            if (COMP && sg.pad[2]) run_slice_write_c<QFT_COMP_NODE_LB>(sg, e, regs[tid]);
             else run_slice_write(sg, e, regs[tid].p);
           }
       }
@@ -321,7 +321,7 @@ extern "C" int emu_r2c_large(int N, int64_t batch, const float* in, float* out, 
   int r = 0; while ((1 << r) < N) ++r;
   QftTune t = qft_default_tune(r);
   const int J = plain ? 0 : qft_comp_classes(r);
-  if (qft_build_large_plan(r, t, J > 0 ? 11 : 12, 512, &g_lp, J) != 0) return -2;
+  if (qft_build_large_plan(r, t, 12, 512, &g_lp, J) != 0) return -2;
   std::vector<float> gsec(N / 4 + 1, 0.f);
   qft_fill_gray_secants(r, gsec.data());
   const int side_len = qft_side_len(N);

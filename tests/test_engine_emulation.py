@@ -140,8 +140,7 @@ def test_large_path_forward_bit_exact(lg):
 @pytest.mark.parametrize("lg", [16, 18])
 @pytest.mark.parametrize("node_log2", [10, 11])
 def test_large_path_node_sizes(lg, node_log2):
-    """Node groups of 2^10 and 2^11 cells (the compensated plans' default is
-    2^11; 2^12 would put more tasks on one node than a CTA has threads): same bits."""
+    """Node groups of 2^10 and 2^11 cells (the default is 2^12): same bits."""
     N = 1 << lg
     z = inputs.normal_complex(1, N, seed=40 + lg)
     assert bits_equal(emu.c2c_large(z, node_log2=node_log2), orc.cdft(z, fp32=True).astype(np.complex64))
