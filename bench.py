@@ -264,7 +264,8 @@ def run_gpu(args):
         times = [e[0].elapsed_time(e[1]) for e in evs[lg]]
         per_size[lg] = sum(times) / len(times)
     peak, peak_src = measured_peaks()
-    roof, kernel_share = roofline(kt, peak, peak_src)
+    comp_j = {lg: plans[lg].comp_classes() for lg in logs}
+    roof, kernel_share = roofline(kt, peak, peak_src, comp_j)
     launches = sum(n for lg in logs for (_, n) in kt[lg].values())
     # the path's own fraction: the method's 16 N bytes per transform over the step
     roof["path_achieved"] = round(value, 1)
@@ -296,7 +297,7 @@ def run_gpu(args):
         err_max = max(err_max, float(e.max()))
         err_mean += e.tolist()
     schedules = {f"2^{lg}": plans[lg].schedule() for lg in logs}
-    comp = {f"2^{lg}": plans[lg].comp_classes() for lg in logs}
+    comp = {f"2^{lg}": comp_j[lg] for lg in logs}
 
     # ------------------------------------------------------------- e2e
     e2e = None
@@ -347,37 +348,56 @@ def run_gpu(args):
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel, from one
 # ncu capture of the named kernel at the stated size (scaled to a launch over
-# 2^28 elements); None once the kernel has changed since the capture.
-NCU_TRAFFIC = {"k_large_node": 4188667904}   # N = 2^16 capture: 523.6 MB over 2^25 elements, x 8
+# 2^28 elements by the rows, since the traffic grows in proportion to them);
+# None once the kernel has changed since the capture.
+NCU_TRAFFIC = {("k_large_node", 18): 465741824 * 16}   # N = 2^18 capture: 465.7 MB over 2^24 elements, x 16
+ROOF_SIZE = {"k_large_node": 18}                         # the size the roofline line reports for that kernel
 
 
-def roofline(kt, peak, peak_src):
+def comp_factor(J):
+    """Bytes per element per pass of the large-row kernels over the 16 B of the
+    plain cells: the compensated classes (the share 1 - 2^-J of the cells) also
+    move their lo parts."""
+    return 2.0 - 2.0 ** (-J) if J > 0 else 1.0
+
+
+def roofline(kt, peak, peak_src, comp=None):
     """Roofline of the kernel with the largest summed time over the timed
     region.  Every launch of every kernel of the path reads and writes each of
     the 2^28 elements' 8-byte cells once (row kernel: the transform's 8N in +
-    8N out; large-row kernels: 8N of class data in and 8N out per pass), so its
-    algorithmic bytes per launch are 16 * 2^28 (one scratch chunk per size at
-    this workload)."""
+    8N out; large-row kernels: 8N of class data in and 8N out per pass), plus
+    the lo parts of the compensated classes' cells, so its algorithmic bytes
+    per launch are 16 * 2^28 * comp_factor(J) (one launch per size at this
+    workload).  `achieved` is for the size in ROOF_SIZE (the ncu capture's),
+    `per_size` for every size the kernel ran at."""
+    comp = comp or {}
     tot = {}
-    per = {}
     for lg, d in kt.items():
         for k, (ms, n) in d.items():
             tot[k] = tot.get(k, 0.0) + ms
-            a = per.setdefault(k, [0.0, 0])
-            a[0] += ms
-            a[1] += n
     dom = max(tot, key=tot.get)
-    ms, n = per[dom]
-    avg = ms / n
-    achieved = 16 * ELEMS / (avg * 1e-3) / 1e9
     sizes = sorted(lg for lg in kt if dom in kt[lg])
-    roof = {"bound": "hbm", "kernel": dom, "sizes": [f"2^{lg}" for lg in sizes],
+    per_size = {}
+    for lg in sizes:
+        ms, n = kt[lg][dom]
+        bpl = 16 * ELEMS * comp_factor(comp.get(lg, 0))
+        per_size[f"2^{lg}"] = {"gbs": round(bpl / (ms / n * 1e-3) / 1e9, 1), "avg_launch_ms": round(ms / n, 4),
+                               "launches": n, "bytes_per_launch": int(bpl), "compensated_classes": comp.get(lg, 0)}
+    lg0 = ROOF_SIZE.get(dom, sizes[-1])
+    if lg0 not in sizes:
+        lg0 = sizes[-1]
+    ms, n = kt[lg0][dom]
+    bpl = 16 * ELEMS * comp_factor(comp.get(lg0, 0))
+    avg = ms / n
+    achieved = bpl / (avg * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "size": f"2^{lg0}",
             "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "frac_basis": "this kernel's own bytes per launch: 16 B per element per pass "
-                          "(row kernel: the transform's input and output; large-row kernels: scratch to scratch)",
-            "traffic": NCU_TRAFFIC.get(dom),
-            "bytes_per_launch": 16 * ELEMS, "launches": n, "avg_launch_ms": round(avg, 4)}
+            "frac_basis": "this kernel's own bytes per launch at this size: 16 B per element per pass, x (2 - 2^-J) "
+                          "with J compensated classes (row kernel: the transform's input and output; large-row "
+                          "kernels: scratch to scratch)",
+            "traffic": NCU_TRAFFIC.get((dom, lg0)),
+            "bytes_per_launch": int(bpl), "launches": n, "avg_launch_ms": round(avg, 4), "per_size": per_size}
 
     def share(steps):
         return {k: round(v / steps, 3) for k, v in sorted(tot.items(), key=lambda x: -x[1])}
