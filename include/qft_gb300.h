@@ -196,7 +196,8 @@ int qft_filter_backward(qft_plan plan, const float* x, const void* W, const floa
  * at zero (each call writes every scratch cell before reading it).  Calls
  * whose executions overlap (two streams, or host threads without ordering)
  * race on the scratch: serialise them.  Batches larger than the rows the
- * scratch holds (3 rows at n = 2^20, 113 at 2^15) run in successive chunks.
+ * scratch holds (113 rows at n = 2^15, 29 at 2^16, 7 at 2^18, 1 at 2^20, where the
+ * compensated classes also keep their lo parts) run in successive chunks.
  * Set-up: the first call on each device (with that device current) looks up the
  * arrays with cudaGetSymbolAddress and fills the tables with blocking copies;
  * make that first call before any stream capture begins.  The set-up is not
