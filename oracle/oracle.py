@@ -23,21 +23,25 @@ _SRC = os.path.join(_HERE, "qft_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_qft_oracle.so")
 _LIB32_PATH = os.path.join(_HERE, "_qft_oracle_f32.so")
 _LIB32C_PATH = os.path.join(_HERE, "_qft_oracle_f32c.so")
+_SRC_FX = os.path.join(_HERE, "qft_oracle_fx.c")
+_LIBFX_PATH = os.path.join(_HERE, "_qft_oracle_fx.so")
 FLAGS32 = ("-DORACLE_REAL=float", "-ffp-contract=off")
 FLAGS32C = ("-DORACLE_REAL=float", "-DORACLE_COMPENSATED", "-ffp-contract=off")
 _lock = threading.Lock()
 _lib = None
 _lib32 = None
 _lib32c = None
+_libfx = None
 
 
-def build(force: bool = False, out: str | None = None, extra_flags=()) -> str:
-    """Compile qft_oracle.c into a shared library (gcc, OpenMP if available)."""
+def build(force: bool = False, out: str | None = None, extra_flags=(), src: str | None = None) -> str:
+    """Compile qft_oracle.c (or `src`) into a shared library (gcc, OpenMP if available)."""
     out = out or _LIB_PATH
+    src = src or _SRC
     if (not force and os.path.exists(out)
-            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(out) >= os.path.getmtime(src)):
         return out
-    base = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", _SRC, "-o", out, "-lm", *extra_flags]
+    base = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", src, "-o", out, "-lm", *extra_flags]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        stdout=subprocess.PIPE, stderr=subprocess.PIPE)
@@ -101,6 +105,27 @@ def _load32(comp: bool = True):
         if _lib32 is None:
             _lib32 = _declare(ctypes.CDLL(build(out=_LIB32_PATH, extra_flags=FLAGS32)))
         return _lib32
+
+
+def build_fx(force: bool = False) -> str:
+    """Compile the fixed-point oracle (qft_oracle_fx.c) into its own library."""
+    return build(force=force, out=_LIBFX_PATH, src=_SRC_FX)
+
+
+def _load_fx():
+    global _libfx
+    with _lock:
+        if _libfx is None:
+            lib = ctypes.CDLL(build_fx())
+            i16 = ctypes.POINTER(ctypes.c_int16)
+            i32 = ctypes.POINTER(ctypes.c_int32)
+            L = ctypes.c_long
+            lib.oracle_cdft_fx.argtypes = [L, L, i16, i32, i32, ctypes.c_int]
+            lib.oracle_fx_const.argtypes = [L, L, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
+            lib.oracle_fx_rs.argtypes = [ctypes.c_int64, ctypes.c_int]
+            lib.oracle_fx_rs.restype = ctypes.c_int64
+            _libfx = lib
+        return _libfx
 
 
 def _dp(a: np.ndarray):
@@ -320,6 +345,44 @@ def fft_ld(z) -> np.ndarray:
     out = np.empty_like(z)
     _check(_load().oracle_fft_ld(z.shape[0], _dp(z.view(np.float64)), _dp(out.view(np.float64))))
     return out
+
+
+# ------------------------------------------------------- fixed-point variant
+def cdft_fx(z, threads: int = 0):
+    """Fixed-point forward DFT of each row (block floating point, see
+    qft_oracle_fx.c): z int16 [..., N, 2] (Q15 re, im) -> (mantissas int32
+    [..., N, 2], exponents int32 [...]); the value of X(k) is m(k) 2^E."""
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.int16))
+    assert z.ndim >= 2 and z.shape[-1] == 2
+    N = z.shape[-2]
+    batch = z.size // (2 * N) if N else 0
+    X = np.empty(z.shape, dtype=np.int32)
+    E = np.empty(z.shape[:-2], dtype=np.int32)
+    _check(_load_fx().oracle_cdft_fx(N, batch, z.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)),
+                                     X.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     E.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), threads))
+    return X, E
+
+
+def fx_value(X, E) -> np.ndarray:
+    """complex128 values m 2^E of fixed-point outputs (exact for |m| < 2^53)."""
+    X = np.asarray(X)
+    E = np.asarray(E)
+    return np.ldexp(X[..., 0].astype(np.float64), E[..., None]) + 1j * np.ldexp(
+        X[..., 1].astype(np.float64), E[..., None])
+
+
+def fx_const(N: int, n: int):
+    """(c, x): the fixed-point secant 1/(2 cos(2 pi n/N)) = c 2^x, c in [2^30, 2^31)."""
+    c = ctypes.c_int64()
+    x = ctypes.c_int()
+    _check(_load_fx().oracle_fx_const(N, n, ctypes.byref(c), ctypes.byref(x)))
+    return int(c.value), int(x.value)
+
+
+def fx_rs(v: int, s: int) -> int:
+    """The oracle's rounding shift v 2^-s (half up; s <= 0 exact)."""
+    return int(_load_fx().oracle_fx_rs(v, s))
 
 
 if __name__ == "__main__":  # pragma: no cover - manual build helper

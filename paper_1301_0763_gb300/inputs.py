@@ -44,6 +44,13 @@ def normal_real(rows: int, n: int, seed: int = 1, dtype=np.float32) -> np.ndarra
     return rng(seed).standard_normal(size=(rows, n)).astype(dtype)
 
 
+def q15_complex(rows: int, n: int, seed: int = 5) -> np.ndarray:
+    """Complex Q15 samples for the fixed-point variant: int16 [rows, n, 2]
+    (re, im), each round(32767 u) with u ~ U[-1, 1] drawn in float64."""
+    u = rng(seed).uniform(-1.0, 1.0, size=(rows, n, 2))
+    return np.round(u * 32767.0).astype(np.int16)
+
+
 def student_t_complex(rows: int, n: int, seed: int = 3, dof: float = 3.0) -> np.ndarray:
     """Student-t(3) re and im, each row scaled so that max(|re|, |im|) = 1 (float64)."""
     g = rng(seed)
