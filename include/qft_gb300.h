@@ -56,6 +56,8 @@ typedef struct qft_plan_s* qft_plan;
 #define QFT_DTYPE_F32 0  /* complex64 (C2C) / float32 real + complex64 spectrum (R2C) */
 #define QFT_DTYPE_F16 1  /* complex stored as two IEEE half values (C2C only)          */
 #define QFT_DTYPE_BF16 2 /* complex stored as two bfloat16 values (C2C only)           */
+#define QFT_DTYPE_I16 3  /* fixed-point variant (C2C forward only, qft_execute_fixed):
+                            complex int16 Q15 in, int32 block-floating-point out       */
 
 /* operations for qft_execute */
 #define QFT_OP_FORWARD 0
@@ -154,6 +156,33 @@ int qft_execute(qft_plan plan, int op, const void* in, void* out, void* stream);
 int qft_execute_forward(qft_plan plan, const void* in, void* out, void* stream);
 int qft_execute_inverse(qft_plan plan, const void* in, void* out, void* stream);
 int qft_execute_backward(qft_plan plan, const void* grad_out, void* grad_in, void* stream);
+
+/*
+ * qft_execute_fixed -- forward DFT (eq qft_0A) of every row of a
+ * QFT_DTYPE_I16 plan by the fixed-point variant of the improved QFT: the
+ * recursion of Sec. 5 (fold, class split, mirror butterflies, secant
+ * conversion eq qft_38A, neighbour adds eqs qft_38B/C, combines eqs
+ * qft_5C-6, the CDFT combine of Sec. 4.1) with every value an int32 mantissa
+ * of a block floating-point block.  The paper names fixed point as its target
+ * (Sec. 1, 7) without a scaling rule; the library's rule: each block
+ * (fold output per class, each child of a mirror butterfly, each node and
+ * chain output, the output row) is normalized so that its largest mantissa
+ * has 29 significant bits, right shifts rounded half up; adds are exact;
+ * secants are 31-bit mantissas with their own exponents and the 64-bit
+ * products are normalized once per node.
+ *   plan       created with kind QFT_KIND_C2C, dtype QFT_DTYPE_I16, flags 0,
+ *              2 <= n <= 2^13 (QFT_ERR_INVALID_N otherwise).
+ *   in         device, [batch][n] complex int16 pairs (re, im): value q 2^-15;
+ *              4-byte aligned.
+ *   out        device, [batch][n] complex int32 mantissa pairs; 8-byte aligned.
+ *   exponents  device, [batch] int32: X(k) = out(k) * 2^exponents[row]
+ *              (0 for a row of zeros); 4-byte aligned.
+ *   Outputs are normalized: the largest |mantissa| of a nonzero row lies in
+ *   [2^28, 2^29].  The buffers may not overlap (QFT_ERR_INPLACE).  The result
+ *   depends on nothing but the input: it is the same bits on every run.
+ * Stream-ordered; qft_execute on such a plan returns QFT_ERR_DTYPE.
+ */
+int qft_execute_fixed(qft_plan plan, const void* in, void* out, int32_t* exponents, void* stream);
 
 /*
  * Spectral-filter layer y = irfft(W (.) rfft(x)) on real rows: rfft is the

@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "_qft_gb300.so")
 SOURCES = ["qft_api.cu", "qft_k_c2c_f32.cu", "qft_k_c2c_f16.cu", "qft_k_c2c_bf16.cu", "qft_k_real.cu", "qft_filter.cu",
            "qft_k_node.cu", "qft_k_ragged.cu", "qft_filter_bwd.cu", "qft_k_r2r.cu",
-           "qft_static.cu"]
+           "qft_static.cu", "qft_k_fixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: the transform never needs a fused multiply-add, and ptxas must not
 # contract the packed f32x2 multiplies and adds (that would change the rounding).

@@ -58,6 +58,8 @@ static void free_resources(qft_plan p) {
   cudaFree(p->d_sec);
   cudaFree(p->d_large);
   cudaFree(p->scratch);
+  cudaFree(p->d_fx);
+  p->d_fx = nullptr;
   free(p->large_host);
   p->d_plan = nullptr; p->d_sec = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->large_host = nullptr;
 }
@@ -113,6 +115,7 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype, int 
   p->wait_ns = 0;
   p->withhold_copy = 0;
   p->channels = 0;
+  p->d_fx = nullptr;
   p->timing = 0; p->tev_n = 0; p->tev_cap = 0; p->tev = nullptr; p->tev_kind = nullptr;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -341,12 +344,35 @@ static int autotune(qft_plan p) {
   return rc;
 }
 
+// Fixed-point plans (QFT_DTYPE_I16, C2C forward only): the constant table and
+// the kernel configuration; no schedule, no scratch.
+static int plan_create_fixed(qft_plan* out, int64_t n, int64_t batch, int kind, unsigned flags) {
+  if (kind != QFT_KIND_C2C) return QFT_ERR_DTYPE;
+  if (flags != 0) return QFT_ERR_INVALID_ARG;
+  if (n < 2 || (n & (n - 1)) != 0 || n > ((int64_t)1 << qft_lib::kFixedMaxLog2)) return QFT_ERR_INVALID_N;
+  if (batch < 0 || batch > (int64_t(1) << 40)) return QFT_ERR_INVALID_BATCH;
+  int r = 0;
+  while ((int64_t(1) << r) < n) ++r;
+  qft_plan p = new (std::nothrow) qft_plan_s();
+  if (!p) return QFT_ERR_CUDA;
+  int rc = plan_init(p, 1, batch, kind, QFT_DTYPE_I16);   // common fields and the status word only
+  if (rc != QFT_OK) { delete p; return rc; }
+  p->n = n;
+  p->r = r;
+  rc = qft_fixed_prepare(p);
+  if (rc != QFT_OK) { free_resources(p); delete p; return rc; }
+  register_plan(p);
+  *out = p;
+  return QFT_OK;
+}
+
 extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
   *out = nullptr;
   if ((flags & ~(QFT_PLAN_AUTOTUNE | QFT_PLAN_FP32_PLAIN)) != 0) return QFT_ERR_INVALID_ARG;
   if (kind != QFT_KIND_C2C && kind != QFT_KIND_R2C && kind != QFT_KIND_DCT0 && kind != QFT_KIND_DST0)
     return QFT_ERR_DTYPE;
+  if (dtype == QFT_DTYPE_I16) return plan_create_fixed(out, n, batch, kind, flags);
   if (dtype != QFT_DTYPE_F32 && dtype != QFT_DTYPE_F16 && dtype != QFT_DTYPE_BF16) return QFT_ERR_DTYPE;
   if (kind != QFT_KIND_C2C && dtype != QFT_DTYPE_F32) return QFT_ERR_DTYPE;
   if (n < 2 || (n & (n - 1)) != 0) return QFT_ERR_INVALID_N;
@@ -608,6 +634,7 @@ extern "C" int qft_execute(qft_plan p, int op, const void* in, void* out, void* 
   int rc = plan_check(p);
   if (rc != QFT_OK) return rc;
   if (op < QFT_OP_FORWARD || op > QFT_OP_INVERSE_ADJOINT) return QFT_ERR_INVALID_ARG;
+  if (p->dtype == QFT_DTYPE_I16) return QFT_ERR_DTYPE;   // qft_execute_fixed
   if (p->batch == 0) return QFT_OK;
   if (!in || !out) return QFT_ERR_NULLPTR;
   const size_t al_c = p->dtype == QFT_DTYPE_F32 ? 8 : 4;
@@ -633,6 +660,23 @@ extern "C" int qft_execute(qft_plan p, int op, const void* in, void* out, void* 
   rc = launch_plain(p, op, in, out, st);
   p->withhold_copy = 0;   // the test of the timeout path is one-shot
   return rc;
+}
+
+extern "C" int qft_execute_fixed(qft_plan p, const void* in, void* out, int32_t* exponents, void* stream) {
+  int rc = plan_check(p);
+  if (rc != QFT_OK) return rc;
+  if (p->dtype != QFT_DTYPE_I16) return QFT_ERR_DTYPE;
+  if (p->batch == 0) return QFT_OK;
+  if (!in || !out || !exponents) return QFT_ERR_NULLPTR;
+  if (((uintptr_t)in % 4) || ((uintptr_t)out % 8) || ((uintptr_t)exponents % 4)) return QFT_ERR_ALIGN;
+  if (in == out || (const void*)exponents == in || (void*)exponents == out) return QFT_ERR_INPLACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  p->last_stream = st;
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return qft_set_cuda(p, e);
+  if (cur != p->device) return QFT_ERR_INVALID_ARG;
+  return qft_launch_fixed(p, in, out, exponents, st);
 }
 
 extern "C" int qft_execute_forward(qft_plan p, const void* in, void* out, void* stream) {
@@ -679,7 +723,7 @@ extern "C" int qft_plan_comp_classes(qft_plan p) {
 extern "C" int qft_plan_set_wait_limit(qft_plan p, int64_t ns) {
   int rc = plan_check(p);
   if (rc != QFT_OK) return rc;
-  if (p->classes || p->kind == kKindFilter || ns < 0) return QFT_ERR_INVALID_ARG;
+  if (p->classes || p->kind == kKindFilter || p->dtype == QFT_DTYPE_I16 || ns < 0) return QFT_ERR_INVALID_ARG;
   p->wait_ns = ns;
   return QFT_OK;
 }
@@ -687,7 +731,7 @@ extern "C" int qft_plan_set_wait_limit(qft_plan p, int64_t ns) {
 extern "C" int qft_plan_withhold_next_copy(qft_plan p) {
   int rc = plan_check(p);
   if (rc != QFT_OK) return rc;
-  if (p->classes || p->kind == kKindFilter) return QFT_ERR_INVALID_ARG;
+  if (p->classes || p->kind == kKindFilter || p->dtype == QFT_DTYPE_I16) return QFT_ERR_INVALID_ARG;
   p->withhold_copy = 1;
   return QFT_OK;
 }
@@ -753,7 +797,7 @@ extern "C" int qft_plan_set_schedule(qft_plan p, const int* v) {
   int rc = plan_check(p);
   if (rc != QFT_OK) return rc;
   if (!v) return QFT_ERR_NULLPTR;
-  if (p->classes || p->kind == kKindFilter || p->r < 2) return QFT_ERR_INVALID_ARG;
+  if (p->classes || p->kind == kKindFilter || p->r < 2 || p->dtype == QFT_DTYPE_I16) return QFT_ERR_INVALID_ARG;
   QftSched c = sched_of(p);
   c.threads = p->large_host ? p->threads : v[0];
   if (!p->large_host && c.threads != 256 && c.threads != 512) return QFT_ERR_INVALID_ARG;

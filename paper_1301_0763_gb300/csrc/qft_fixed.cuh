@@ -1,0 +1,429 @@
+// qft_fixed.cuh -- the fixed-point variant of the improved QFT: complex int16
+// (Q15) input, int32 block-floating-point arithmetic, int32 mantissas and one
+// exponent per row out.  Written once for the sm_103a kernel and, with
+// QFT_HOST_EMULATION, for a host build used only by the test-suite.
+//
+// Arithmetic (the paper names fixed point as its target, Sec. 1 and 7, and
+// gives no scaling rule; this is the library's rule).  The values of one block
+// share one exponent E (value = mantissa * 2^E).  NORM shifts a block so that
+// its largest mantissa has 29 significant bits (left shifts exact, right
+// shifts rounded half up: floor((m + 2^(s-1)) / 2^s)); an all-zero block gets
+// the exponent kEZero, which never wins an alignment.  Adds and subtracts are
+// exact on mantissas of one exponent; two blocks are aligned to the larger
+// exponent first.  The secant of eq qft_38A is a 31-bit mantissa c in
+// [2^30, 2^31) with its own exponent x; o * c is exact in 64 bits, and the
+// products of one node form one block.  Blocks: the fold outputs (per class),
+// the even-harmonic child of every mirror butterfly, the secant products of
+// every odd-harmonic child, every node output (after the neighbour adds of
+// eqs qft_38B/C and the interleave of eq qft_4B), every dct / dst output of the
+// class chain (eqs qft_5C-6) and the CDFT output row (Sec. 4.1).  Every value
+// is a function of block operands and block maxima only, so the order in which
+// threads run does not change a bit.
+//
+// Shared-memory layout of one row (N = 2^r, 4 <= N <= 2^kMaxLog2), per side s
+// (0: DCT network on c(n) = z(n) + z(N-n), 1: DST network on d(n) = z(n) -
+// z(N-n)): cells V[s][0 .. N/2].  The class of 2-adic valuation j (a dct_ot /
+// dst_ot of periodization M = N/2^j with P = N/2^(j+2) points; lp = log2 P)
+// holds slots [off, off + P), off = N/2 - 2P, its time index n = 2^j (2i+1)
+// at slot off + i.  The DCT chain's base pair c(0), c(N/2) sits at N/2 - 1,
+// N/2; the DST chain's base d(N/4) is the DST class lp = 0.
+//  - A node of a class tree with m cells (periodization 4m) keeps its input
+//    s(n), odd n, at slot (n-1)/2; the mirror butterfly writes the
+//    even-harmonic child to the first half and the secant products (the
+//    odd-harmonic child, converted by eq qft_38A) to the second half, so a
+//    tree is a perfect binary tree of nodes laid out in place.
+//  - A node's output keeps natural frequency order: DCT X(k) at slot k, DST
+//    X(k) at slot k - 1.
+//  - The output of dct(4P) / dst(4P) of the class chain occupies the slots of
+//    the class and of every smaller class (and the base), natural order.
+// Block exponents: one int16 per tree node (heap order, class heap at 2 off),
+// and one per chain output (ch[s][lp + 1]; ch[0][0] is dct(2)).
+#pragma once
+#include <stdint.h>
+#include <math.h>
+
+#if defined(__CUDACC__) && !defined(QFT_HOST_EMULATION)
+#define QFX_HD __host__ __device__ __forceinline__
+#else
+#define QFX_HD inline
+#endif
+
+namespace qfx {
+
+constexpr int kBits = 29;          // significant bits of a normalized block's largest mantissa
+constexpr int kEZero = -16384;     // exponent of an all-zero block
+constexpr int kKeyOff = 64;        // offset that keeps product keys positive
+constexpr int kMaxLog2 = 13;       // largest row one CTA transforms
+constexpr int kInExp = -15;        // exponent of the Q15 input
+
+struct Cell { int32_t x, y; };
+struct Sec { int32_t c, x; };      // secant = c * 2^x
+
+QFX_HD int blen64(uint64_t v) {
+#if defined(__CUDA_ARCH__)
+  return 64 - __clzll((long long)v);
+#else
+  return v ? 64 - __builtin_clzll(v) : 0;
+#endif
+}
+QFX_HD uint64_t mag64(int64_t v) { return v < 0 ? (uint64_t)(-v) : (uint64_t)v; }
+QFX_HD int imax(int a, int b) { return a > b ? a : b; }
+// bit length of the larger magnitude of a cell (0 for a zero cell)
+QFX_HD int key(Cell a) {
+  const uint64_t mx = mag64(a.x), my = mag64(a.y);
+  return blen64(mx > my ? mx : my);
+}
+// v 2^-s rounded half up (floor((v + 2^(s-1)) / 2^s)); s <= 0: exact left shift
+QFX_HD int64_t rs(int64_t v, int s) {
+  if (s <= 0) return v * ((int64_t)1 << (-s));
+  if (s >= 63) return 0;   // |v| < 2^61
+  return (v + ((int64_t)1 << (s - 1))) >> s;
+}
+QFX_HD Cell rsc(Cell a, int s) {
+  Cell r;
+  r.x = (int32_t)rs(a.x, s);
+  r.y = (int32_t)rs(a.y, s);
+  return r;
+}
+QFX_HD Cell add(Cell a, Cell b) { Cell r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+QFX_HD Cell sub(Cell a, Cell b) { Cell r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+QFX_HD Cell zero() { Cell r; r.x = 0; r.y = 0; return r; }
+// exponent after a NORM of a block whose largest mantissa has bl bits
+QFX_HD int norm_exp(int bl, int E) { return bl ? E + bl - kBits : kEZero; }
+
+// The constants of a row of length N: entry m/2 - 1 + i holds the secant
+// 1/(2 cos(2 pi (2i+1) / (4m))) of slot i of a node of m cells (m = 2 ..
+// N/4); the node of 2 cells (periodization 8) uses cos(pi/4), the base case
+// of dct_oo / dst_oo (the same value).  Long double, the complementary-angle
+// sine near the pole, rounded once to a 31-bit mantissa.  N/4 - 1 entries.
+inline void fill_consts(int N, Sec* tab) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int m = 2; m <= N / 4; m *= 2) {
+    const long M = 4L * m;
+    for (int i = 0; i < m / 2; ++i) {
+      const long n = 2L * i + 1;
+      long double v;
+      if (M == 8) v = cosl(pi / 4);
+      else if (8 * n <= M) v = 1.0L / (2.0L * cosl(2 * pi * (long double)n / (long double)M));
+      else v = 1.0L / (2.0L * sinl(2 * pi * (long double)(M / 4 - n) / (long double)M));
+      int e;
+      const long double f = frexpl(v, &e);
+      long long c = (long long)floorl(f * 2147483648.0L + 0.5L);
+      if (c == (1LL << 31)) { c >>= 1; ++e; }
+      tab[m / 2 - 1 + i].c = (int32_t)c;
+      tab[m / 2 - 1 + i].x = e - 31;
+    }
+  }
+}
+
+// shared-memory bytes of one row of length N
+QFX_HD int slot_count(int N) { return N >= 64 ? N / 32 : 2; }
+QFX_HD size_t smem_bytes(int N) {
+  return sizeof(Cell) * 2 * (size_t)(N / 2 + 2) + sizeof(int16_t) * 2 * (size_t)N +
+         sizeof(int) * 4 * (size_t)slot_count(N) + sizeof(int) * 32;
+}
+
+struct Row {
+  Cell* V0;            // DCT side, N/2 + 2 cells
+  Cell* V1;            // DST side
+  int16_t* X0;         // tree-node exponents of the DCT side, N (class heap at 2 off)
+  int16_t* X1;         // of the DST side
+  int* ch;             // chain exponents: ch[16 s + lp + 1]
+  const Sec* sec;      // fill_consts table
+  int r, N;
+};
+// side selects (no indexed member arrays: they would put the row in local memory)
+QFX_HD Cell* side(const Row& R, int s) { return s ? R.V1 : R.V0; }
+QFX_HD int16_t* exps(const Row& R, int s) { return s ? R.X1 : R.X0; }
+
+// One item of a step: up to two output cells and two block keys.
+struct Item {
+  Cell a, b;
+  int k1, k2;
+  int seg;             // items of the item's block (a power of two); 0: no work
+};
+QFX_HD void item_none(Item& it) { it.k1 = 0; it.k2 = 0; it.seg = 0; it.a = zero(); it.b = zero(); }
+
+QFX_HD Cell load_z(const uint32_t* z, int n) {
+  const uint32_t w = z[n];
+  Cell c;
+  c.x = (int32_t)(int16_t)(uint16_t)(w & 0xffffu);
+  c.y = (int32_t)(int16_t)(uint16_t)(w >> 16);
+  return c;
+}
+
+// ---------------------------------------------------------------- fold step
+// Items w in [0, N): side s = w / (N/2), slot w1 = w mod (N/2) < N/2 - 1: the
+// fold value c(n) or d(n) of that slot, one block per class (a NORM of the
+// fold output followed by the lossless NORMs of the even/odd separations of
+// Sec. 3.1 is one NORM per class).
+struct FoldDec { int s, w1, lp, P, off, i; };
+QFX_HD bool fold_dec(const Row& R, int w, FoldDec& d) {
+  const int H = R.N / 2;
+  d.s = w >= H;
+  d.w1 = w - d.s * H;
+  if (d.w1 >= H - 1) return false;
+  d.lp = blen64((uint64_t)(H - 1 - d.w1)) - 1;
+  d.P = 1 << d.lp;
+  d.off = H - 2 * d.P;
+  d.i = d.w1 - d.off;
+  return true;
+}
+QFX_HD void fold_compute(const Row& R, const uint32_t* z, int w, Item& it) {
+  item_none(it);
+  FoldDec d;
+  if (!fold_dec(R, w, d)) return;
+  const int n = (2 * d.i + 1) << (R.r - 2 - d.lp);
+  const Cell a = load_z(z, n), b = load_z(z, R.N - n);
+  it.a = d.s ? sub(a, b) : add(a, b);
+  it.k1 = key(it.a);
+  it.seg = d.P;
+}
+QFX_HD void fold_write(const Row& R, int w, const Item& it, int bl) {
+  FoldDec d;
+  fold_dec(R, w, d);
+  side(R, d.s)[d.w1] = rsc(it.a, bl - kBits);
+  if (d.i == 0) {
+    const int E = norm_exp(bl, kInExp);
+    exps(R, d.s)[2 * d.off] = (int16_t)E;
+    if (d.s == 1 && d.lp == 0) R.ch[16 + 1] = E;   // dst(4) of the chain: its input d(N/4)
+  }
+}
+// The DCT chain's base: c(0), c(N/2) normalized, then dct(2) (eq qft_0B).
+QFX_HD void fold_base(const Row& R, const uint32_t* z) {
+  const int H = R.N / 2;
+  Cell b0 = load_z(z, 0), b1 = load_z(z, H);
+  const int bl = imax(key(b0), key(b1));
+  const int E = norm_exp(bl, kInExp);
+  b0 = rsc(b0, bl - kBits);
+  b1 = rsc(b1, bl - kBits);
+  const Cell c0 = add(b0, b1), c1 = sub(b0, b1);
+  const int bl2 = imax(key(c0), key(c1));
+  R.V0[H - 1] = rsc(c0, bl2 - kBits);
+  R.V0[H] = rsc(c1, bl2 - kBits);
+  R.ch[0] = bl ? norm_exp(bl2, E) : kEZero;
+}
+
+// ------------------------------------------------------- forward step (depth d)
+// Items w in [0, N/2): side s = w / (N/4); per class (lp >= d + 1) the mirror
+// butterflies of its 2^d nodes of m = P / 2^d cells, one pair (i, m-1-i) per
+// item, i < m/2 (eqs qft_1, qft_2; DST roles swapped, Sec. 3.2), and the
+// secant products of the odd-harmonic half (eq qft_38A).  Keys: k1 for the
+// even-harmonic child, k2 for the product block (x + bits + kKeyOff).
+struct FwdDec { int s, lp, off, q, i, m, base; };
+QFX_HD bool fwd_dec(const Row& R, int dep, int w, FwdDec& d) {
+  const int Q4 = R.N / 4;
+  d.s = w >= Q4;
+  const int w1 = w - d.s * Q4;
+  d.lp = blen64((uint64_t)(Q4 - 1 - w1));
+  if (d.lp < dep + 1) return false;
+  const int P = 1 << d.lp;
+  d.off = R.N / 2 - 2 * P;
+  const int w2 = w1 - (Q4 - P);
+  const int hb = d.lp - dep - 1;
+  d.q = w2 >> hb;
+  d.i = w2 & ((1 << hb) - 1);
+  d.m = 2 << hb;
+  d.base = d.off + d.q * d.m;
+  return true;
+}
+QFX_HD void fwd_compute(const Row& R, int dep, int w, Item& it) {
+  item_none(it);
+  FwdDec d;
+  if (!fwd_dec(R, dep, w, d)) return;
+  const Cell* V = side(R, d.s);
+  const Cell a = V[d.base + d.i], b = V[d.base + d.m - 1 - d.i];
+  it.a = d.s ? sub(a, b) : add(a, b);   // even-harmonic child
+  it.b = d.s ? add(a, b) : sub(a, b);   // odd-harmonic child (before the secant)
+  it.k1 = key(it.a);
+  const Sec c = R.sec[(d.m >> 1) - 1 + d.i];
+  const int64_t px = (int64_t)it.b.x * c.c, py = (int64_t)it.b.y * c.c;
+  const uint64_t mx = mag64(px), my = mag64(py);
+  const int bl = blen64(mx > my ? mx : my);
+  it.k2 = bl ? c.x + bl + kKeyOff : 0;
+  it.seg = d.m >> 1;
+}
+QFX_HD void fwd_write(const Row& R, int dep, int w, const Item& it, int k1, int k2) {
+  FwdDec d;
+  fwd_dec(R, dep, w, d);
+  Cell* V = side(R, d.s);
+  int16_t* X = exps(R, d.s);
+  const int Ein = X[2 * d.off + (1 << dep) - 1 + d.q];
+  V[d.base + d.i] = rsc(it.a, k1 - kBits);
+  const Sec c = R.sec[(d.m >> 1) - 1 + d.i];
+  const int top = k2 - kKeyOff - kBits;   // product block exponent - Ein
+  Cell t = zero();
+  if (k2) {
+    t.x = (int32_t)rs((int64_t)it.b.x * c.c, top - c.x);
+    t.y = (int32_t)rs((int64_t)it.b.y * c.c, top - c.x);
+  }
+  V[d.base + (d.m >> 1) + d.i] = t;
+  if (d.i == 0) {
+    const int hc = 2 * d.off + (2 << dep) - 1 + 2 * d.q;
+    X[hc] = (int16_t)norm_exp(k1, Ein);
+    X[hc + 1] = (int16_t)(k2 ? Ein + top : kEZero);
+  }
+}
+
+// ----------------------------------------------------- backward step (height h)
+// Items w in [0, N): side s, slot w1 < N/2 - 1 of class lp.
+//  - lp >= h: output cell k of a tree node of m = 2^h cells at depth lp - h,
+//    from its children (eqs qft_4B, qft_38B, qft_38C; DST forms of Sec. 5).
+//  - lp == h - 1: item t of the class chain's combine dct(4P) (or dst(4P),
+//    lp >= 1): outputs t and 2P - t (eqs qft_5C, qft_5D; DCT item 0 also
+//    the middle output, eq qft_6).
+struct BwdDec { int s, lp, P, off, w2; };
+QFX_HD int bwd_dec(const Row& R, int h, int w, BwdDec& d) {
+  const int H = R.N / 2;
+  d.s = w >= H;
+  const int w1 = w - d.s * H;
+  if (w1 >= H - 1) return 0;
+  d.lp = blen64((uint64_t)(H - 1 - w1)) - 1;
+  d.P = 1 << d.lp;
+  d.off = H - 2 * d.P;
+  d.w2 = w1 - d.off;
+  if (d.lp >= h) return 1;                                   // tree item
+  if (d.lp == h - 1 && (d.s == 0 || d.lp >= 1)) return 2;    // chain item
+  return 0;
+}
+QFX_HD int tree_ex(const Row& R, const BwdDec& d, int h, int& Ee, int& Ey) {
+  const int dep = d.lp - h, q = d.w2 >> h;
+  const int hc = 2 * d.off + (2 << dep) - 1 + 2 * q;
+  Ee = exps(R, d.s)[hc];
+  Ey = exps(R, d.s)[hc + 1];
+  return imax(Ee, Ey);
+}
+QFX_HD int chain_ex(const Row& R, const BwdDec& d, int& EE, int& EO) {
+  EO = exps(R, d.s)[2 * d.off];
+  EE = R.ch[16 * d.s + d.lp];
+  return imax(EE, EO);
+}
+QFX_HD void bwd_compute(const Row& R, int h, int w, Item& it) {
+  item_none(it);
+  BwdDec d;
+  const int kind = bwd_dec(R, h, w, d);
+  if (!kind) return;
+  const Cell* V = side(R, d.s);
+  if (kind == 1) {
+    int Ee, Ey;
+    const int Ex = tree_ex(R, d, h, Ee, Ey);
+    const int m = 1 << h, k = d.w2 & (m - 1);
+    const int base = d.off + (d.w2 >> h) * m, half = base + (m >> 1);
+    Cell v;
+    if (d.s == 0) {            // DCT: X(2j) = E(j); X(2j+1) = Y(j) + Y(j+1); X(m-1) = Y(m/2-1)
+      if (!(k & 1)) v = rsc(V[base + (k >> 1)], Ex - Ee);
+      else if (k < m - 1) v = rsc(add(V[half + (k >> 1)], V[half + (k >> 1) + 1]), Ex - Ey);
+      else v = rsc(V[half + (m >> 1) - 1], Ex - Ey);
+    } else {                   // DST, slot k holds X(k+1): X(2j) = E(j); X(1) = Z(1); X(2j+1) = Z(j) + Z(j+1)
+      const int kk = k + 1;
+      if (!(kk & 1)) v = rsc(V[base + (kk >> 1) - 1], Ex - Ee);
+      else if (kk == 1) v = rsc(V[half], Ex - Ey);
+      else v = rsc(add(V[half + (kk >> 1) - 1], V[half + (kk >> 1)]), Ex - Ey);
+    }
+    it.a = v;
+    it.k1 = key(v);
+    it.seg = m;
+    return;
+  }
+  int EE, EO;
+  const int Ex = chain_ex(R, d, EE, EO);
+  const int t = d.w2, P = d.P, off = d.off;
+  if (d.s == 0) {              // C(t) = E(t) + O(t), C(2P-t) = E(t) - O(t), C(P) = E(P)
+    const Cell e = rsc(V[off + P + t], Ex - EE), o = rsc(V[off + t], Ex - EO);
+    it.a = add(e, o);
+    it.b = sub(e, o);
+    it.k1 = imax(key(it.a), key(it.b));
+    if (t == 0) it.k1 = imax(it.k1, key(rsc(V[off + 2 * P], Ex - EE)));
+  } else if (t == 0) {         // S(P) = O(P)
+    it.a = rsc(V[off + P - 1], Ex - EO);
+    it.k1 = key(it.a);
+  } else {                     // S(t) = E(t) + O(t), S(2P-t) = O(t) - E(t)
+    const Cell e = rsc(V[off + P + t - 1], Ex - EE), o = rsc(V[off + t - 1], Ex - EO);
+    it.a = add(e, o);
+    it.b = sub(o, e);
+    it.k1 = imax(key(it.a), key(it.b));
+  }
+  it.seg = P;
+}
+QFX_HD void bwd_write(const Row& R, int h, int w, const Item& it, int bl) {
+  BwdDec d;
+  const int kind = bwd_dec(R, h, w, d);
+  Cell* V = side(R, d.s);
+  const int sh = bl - kBits;
+  if (kind == 1) {
+    int Ee, Ey;
+    const int Ex = tree_ex(R, d, h, Ee, Ey);
+    const int m = 1 << h, k = d.w2 & (m - 1), q = d.w2 >> h;
+    V[d.off + q * m + k] = rsc(it.a, sh);
+    if (k == 0) exps(R, d.s)[2 * d.off + (1 << (d.lp - h)) - 1 + q] = (int16_t)norm_exp(bl, Ex);
+    return;
+  }
+  int EE, EO;
+  const int Ex = chain_ex(R, d, EE, EO);
+  const int t = d.w2, P = d.P, off = d.off;
+  if (d.s == 0) {
+    if (t == 0) {
+      const Cell mid = rsc(V[off + 2 * P], Ex - EE);   // E(P), read before C(2P) replaces it
+      V[off + P] = rsc(mid, sh);
+      R.ch[d.lp + 1] = norm_exp(bl, Ex);
+    }
+    V[off + t] = rsc(it.a, sh);
+    V[off + 2 * P - t] = rsc(it.b, sh);
+  } else if (t == 0) {
+    V[off + P - 1] = rsc(it.a, sh);
+    R.ch[16 + d.lp + 1] = norm_exp(bl, Ex);
+  } else {
+    V[off + t - 1] = rsc(it.a, sh);
+    V[off + 2 * P - t - 1] = rsc(it.b, sh);
+  }
+}
+
+// ------------------------------------------------------------- final step
+// Items k in [0, N/2): X(k) = C(k) - i S(k), X(N-k) = C(k) + i S(k) (Sec.
+// 4.1 on complex data), item 0: X(0) = C(0), X(N/2) = C(N/2); one block.
+QFX_HD int fin_ex(const Row& R, int& EC, int& ES) {
+  EC = R.ch[R.r - 1];
+  ES = R.ch[16 + R.r - 1];
+  return imax(EC, ES);
+}
+QFX_HD void fin_values(const Row& R, int k, Cell& lo, Cell& hi) {
+  int EC, ES;
+  const int Ex = fin_ex(R, EC, ES);
+  if (k == 0) {
+    lo = rsc(R.V0[0], Ex - EC);
+    hi = rsc(R.V0[R.N / 2], Ex - EC);
+    return;
+  }
+  const Cell a = rsc(R.V0[k], Ex - EC), b = rsc(R.V1[k - 1], Ex - ES);
+  lo.x = a.x + b.y; lo.y = a.y - b.x;
+  hi.x = a.x - b.y; hi.y = a.y + b.x;
+}
+QFX_HD void fin_compute(const Row& R, int k, Item& it) {
+  fin_values(R, k, it.a, it.b);
+  it.k1 = imax(key(it.a), key(it.b));
+  it.k2 = 0;
+  it.seg = R.N / 2;
+}
+// out: the row's N cells; *E the row exponent (0 for a row of zeros)
+QFX_HD void fin_write(const Row& R, int k, int bl, Cell* out, int* E) {
+  Cell lo, hi;
+  fin_values(R, k, lo, hi);
+  out[k] = rsc(lo, bl - kBits);
+  out[k == 0 ? R.N / 2 : R.N - k] = rsc(hi, bl - kBits);
+  if (k == 0) {
+    int EC, ES;
+    *E = bl ? fin_ex(R, EC, ES) + bl - kBits : 0;
+  }
+}
+
+// N = 2: X(0) = z(0) + z(1), X(1) = z(0) - z(1), one block.
+QFX_HD void row_n2(const uint32_t* z, Cell* out, int* E) {
+  const Cell a = load_z(z, 0), b = load_z(z, 1);
+  const Cell s = add(a, b), t = sub(a, b);
+  const int bl = imax(key(s), key(t));
+  out[0] = rsc(s, bl - kBits);
+  out[1] = rsc(t, bl - kBits);
+  *E = bl ? kInExp + bl - kBits : 0;
+}
+
+}  // namespace qfx

@@ -30,6 +30,7 @@ struct __align__(8) qc_storage { float x, y; };
 namespace qft_lib {
 constexpr int kMaxRowLog2 = 14;   // largest row one CTA transforms in shared memory
 constexpr int kMaxLog2 = 24;      // largest transform length
+constexpr int kFixedMaxLog2 = 13; // largest row of the fixed-point variant (one CTA, shared memory)
 constexpr int kNodeLog2 = 12;     // largest node group of the large-row path (cells)
 constexpr int kNodeThreads = 512;
 constexpr int64_t kScratchBudget = (int64_t)16 << 30;  // bytes of scratch per plan
@@ -67,6 +68,7 @@ struct qft_plan_s {
   int64_t wait_ns;            // limit of the kernels' waits for staged copies (ns; 0: 2 s)
   int withhold_copy;          // one-shot test: the next execute withholds each CTA's first staged copy
   int64_t channels;           // spectral-filter plans: C (batch holds B)
+  void* d_fx;                 // fixed-point plans (QFT_DTYPE_I16): the secant constants (qfx::Sec)
   // large-row path (N > 2^kMaxRowLog2): schedule, scratch copies A and B
   QftLargePlan* large_host;
   QftLargePlan* d_large;
@@ -145,5 +147,7 @@ int qft_launch_filter(qft_plan p, int backward, const float* x, const void* W, c
                       void* gW, cudaStream_t st);
 int qft_filter_smem(int N, int LF, int backward);
 int qft_filter_parts();
+int qft_fixed_prepare(qft_plan p);
+int qft_launch_fixed(qft_plan p, const void* in, void* out, int32_t* exps, cudaStream_t st);
 int qft_launch_ragged_class(qft_plan sub, const QftIoArgs* d_args, const int64_t* d_offsets,
                             const int32_t* d_rows, cudaStream_t st);

@@ -24,7 +24,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_qft_gb300.so")
 
 KIND_C2C, KIND_R2C, KIND_DCT0, KIND_DST0 = 0, 1, 2, 3
-DTYPE_F32, DTYPE_F16, DTYPE_BF16 = 0, 1, 2
+DTYPE_F32, DTYPE_F16, DTYPE_BF16, DTYPE_I16 = 0, 1, 2, 3
 OP_FORWARD, OP_INVERSE, OP_FORWARD_ADJOINT, OP_INVERSE_ADJOINT = 0, 1, 2, 3
 PLAN_AUTOTUNE = 1
 PLAN_FP32_PLAIN = 2
@@ -59,6 +59,7 @@ def load_library(path: str | None = None):
         lib.qft_plan_create_ragged.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
                                                i64, ci, ci, ctypes.c_uint]
         lib.qft_execute.argtypes = [vp, ci, vp, vp, vp]
+        lib.qft_execute_fixed.argtypes = [vp, vp, vp, vp, vp]
         for f in (lib.qft_execute_forward, lib.qft_execute_inverse, lib.qft_execute_backward):
             f.argtypes = [vp, vp, vp, vp]
         lib.qft_plan_destroy.argtypes = [vp]
@@ -149,6 +150,14 @@ class Plan:
                                         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_handle(stream))),
                    "qft_execute")
         return out
+
+    def execute_fixed(self, inp: torch.Tensor, out: torch.Tensor, exps: torch.Tensor, stream=None):
+        """Fixed-point forward (QFT_DTYPE_I16 plans, qft_execute_fixed)."""
+        with torch.cuda.device(self.device):
+            _check(self.lib.qft_execute_fixed(self.handle, ctypes.c_void_p(inp.data_ptr()),
+                                              ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(exps.data_ptr()),
+                                              ctypes.c_void_p(_stream_handle(stream))), "qft_execute_fixed")
+        return out, exps
 
     def info(self):
         t, c, s, l = (ctypes.c_int() for _ in range(4))
@@ -294,7 +303,7 @@ def get_plan(n: int, batch: int, kind: int, dtype: int, device: torch.device) ->
     key = (n, batch, kind, dtype, device.index, _autotune)
     p = _plans.get(key)
     if p is None:
-        p = Plan(n, batch, kind, dtype, device, autotune=_autotune)
+        p = Plan(n, batch, kind, dtype, device, autotune=_autotune and dtype != DTYPE_I16)
         _plans[key] = p
     return p
 
@@ -334,6 +343,22 @@ def fft_bf16(x: torch.Tensor, op: int = OP_FORWARD) -> torch.Tensor:
     out = torch.empty_like(x)
     get_plan(n, x.numel() // (2 * n), KIND_C2C, DTYPE_BF16, x.device).execute(op, x, out)
     return out
+
+
+def fft_fixed(z: torch.Tensor):
+    """Fixed-point forward DFT (the improved QFT in int32 block floating
+    point, qft_execute_fixed): z is an int16 tensor [..., N, 2] of Q15 (re, im)
+    samples (value q 2^-15), 2 <= N <= 2^13.  Returns (mantissas int32
+    [..., N, 2], exponents int32 [...]); X(k) = mantissa(k) * 2^exponent."""
+    _need_cuda(z)
+    if z.dtype != torch.int16 or z.dim() < 2 or z.shape[-1] != 2:
+        raise TypeError("fft_fixed expects an int16 tensor [..., N, 2]")
+    z = z.contiguous()
+    n = z.shape[-2]
+    out = torch.empty(z.shape, dtype=torch.int32, device=z.device)
+    exps = torch.empty(z.shape[:-2], dtype=torch.int32, device=z.device)
+    get_plan(n, z.numel() // (2 * n), KIND_C2C, DTYPE_I16, z.device).execute_fixed(z, out, exps)
+    return out, exps
 
 
 def _real_fwd(x: torch.Tensor, op: int) -> torch.Tensor:

@@ -12,6 +12,36 @@ DEPS = [os.path.join(ROOT, "paper_1301_0763_gb300", "csrc", f)
         for f in ("qft_engine.cuh", "qft_io.cuh", "qft_planner.h", "qft_plan.h", "qft_consts.h")]
 LIB = os.path.join(HERE, "_qft_emu.so")
 _lib = None
+SRC_FX = os.path.join(HERE, "qft_fx_emu.cpp")
+DEP_FX = os.path.join(ROOT, "paper_1301_0763_gb300", "csrc", "qft_fixed.cuh")
+LIB_FX = os.path.join(HERE, "_qft_fx_emu.so")
+_lib_fx = None
+
+
+def load_fx():
+    """The host emulation of the fixed-point kernel (qft_fx_emu.cpp)."""
+    global _lib_fx
+    if _lib_fx is not None:
+        return _lib_fx
+    newest = max(os.path.getmtime(p) for p in (SRC_FX, DEP_FX))
+    if not os.path.exists(LIB_FX) or os.path.getmtime(LIB_FX) < newest:
+        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", SRC_FX, "-o", LIB_FX], check=True)
+    lib = ctypes.CDLL(LIB_FX)
+    lib.emu_cdft_fx.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    _lib_fx = lib
+    return lib
+
+
+def cdft_fx(z):
+    """z int16 [..., N, 2] -> (int32 mantissas [..., N, 2], int32 exponents [...])."""
+    z = np.ascontiguousarray(z, dtype=np.int16)
+    N = z.shape[-2]
+    X = np.empty(z.shape, dtype=np.int32)
+    E = np.empty(z.shape[:-2], dtype=np.int32)
+    rc = load_fx().emu_cdft_fx(N, z.size // (2 * N), z.ctypes.data, X.ctypes.data, E.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"fixed-point emulation failed (rc={rc})")
+    return X, E
 
 
 def load():
