@@ -20,9 +20,9 @@
 // is a function of block operands and block maxima only, so the order in which
 // threads run does not change a bit.
 //
-// Shared-memory layout of one row (N = 2^r, 4 <= N <= 2^kMaxLog2), per side s
-// (0: DCT network on c(n) = z(n) + z(N-n), 1: DST network on d(n) = z(n) -
-// z(N-n)): cells V[s][0 .. N/2].  The class of 2-adic valuation j (a dct_ot /
+// Layout of one row (N = 2^r, 4 <= N <= 2^kMaxLog2) in each of its two cell
+// buffers, per side s (0: DCT network on c(n) = z(n) + z(N-n), 1: DST network
+// on d(n) = z(n) - z(N-n)): cells V[s][0 .. N/2].  The class of 2-adic valuation j (a dct_ot /
 // dst_ot of periodization M = N/2^j with P = N/2^(j+2) points; lp = log2 P)
 // holds slots [off, off + P), off = N/2 - 2P, its time index n = 2^j (2i+1)
 // at slot off + i.  The DCT chain's base pair c(0), c(N/2) sits at N/2 - 1,
@@ -68,10 +68,17 @@ QFX_HD int blen64(uint64_t v) {
 }
 QFX_HD uint64_t mag64(int64_t v) { return v < 0 ? (uint64_t)(-v) : (uint64_t)v; }
 QFX_HD int imax(int a, int b) { return a > b ? a : b; }
-// bit length of the larger magnitude of a cell (0 for a zero cell)
+QFX_HD int blen32(uint32_t v) {
+#if defined(__CUDA_ARCH__)
+  return 32 - __clz((int)v);
+#else
+  return v ? 32 - __builtin_clz(v) : 0;
+#endif
+}
+// bit length of the larger magnitude of a cell (0 for a zero cell; |x|, |y| < 2^31)
 QFX_HD int key(Cell a) {
-  const uint64_t mx = mag64(a.x), my = mag64(a.y);
-  return blen64(mx > my ? mx : my);
+  const uint32_t mx = (uint32_t)(a.x < 0 ? -a.x : a.x), my = (uint32_t)(a.y < 0 ? -a.y : a.y);
+  return blen32(mx > my ? mx : my);
 }
 // v 2^-s rounded half up (floor((v + 2^(s-1)) / 2^s)); s <= 0: exact left shift
 QFX_HD int64_t rs(int64_t v, int s) {
@@ -79,10 +86,18 @@ QFX_HD int64_t rs(int64_t v, int s) {
   if (s >= 63) return 0;   // |v| < 2^61
   return (v + ((int64_t)1 << (s - 1))) >> s;
 }
+// rs() of an int32 mantissa in 32-bit arithmetic: with q = floor(v / 2^(s-1)),
+// floor((v + 2^(s-1)) / 2^s) = floor((q + 1) / 2); shifts of 32 or more give
+// q in {0, -1}, i.e. 0.  Left shifts stay below 2^31 (at most 29 places).
+QFX_HD int32_t rs32(int32_t v, int s) {
+  if (s <= 0) return (int32_t)((uint32_t)v << (-s));
+  const int t = s - 1 < 31 ? s - 1 : 31;
+  return ((v >> t) + 1) >> 1;
+}
 QFX_HD Cell rsc(Cell a, int s) {
   Cell r;
-  r.x = (int32_t)rs(a.x, s);
-  r.y = (int32_t)rs(a.y, s);
+  r.x = rs32(a.x, s);
+  r.y = rs32(a.y, s);
   return r;
 }
 QFX_HD Cell add(Cell a, Cell b) { Cell r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
@@ -116,33 +131,52 @@ inline void fill_consts(int N, Sec* tab) {
   }
 }
 
-// shared-memory bytes of one row of length N
-QFX_HD int slot_count(int N) { return N >= 64 ? N / 32 : 2; }
-QFX_HD size_t smem_bytes(int N) {
-  return sizeof(Cell) * 2 * (size_t)(N / 2 + 2) + sizeof(int16_t) * 2 * (size_t)N +
-         sizeof(int) * 4 * (size_t)slot_count(N) + sizeof(int) * 32;
-}
+// ------------------------------------------------------------ row storage
+// One row in shared memory: two cell buffers (each a DCT side and a DST side
+// of N/2 + 2 cells; a step reads one and writes the other, so that its stores
+// need no second barrier), the tree-node exponents of both sides (int16, N
+// each) and the chain exponents (32 ints).  Buffer 1 first holds the staged
+// input row (N words).
+QFX_HD size_t row_bytes(int N) { return 32 * (size_t)(N / 2 + 2) + 4 * (size_t)N + 128; }
+// block-maximum slots of a CTA whose steps have up to `items` items: two
+// alternating sets of two keys
+QFX_HD int slot_count(int items) { return items >= 64 ? items / 32 : 2; }
 
 struct Row {
-  Cell* V0;            // DCT side, N/2 + 2 cells
-  Cell* V1;            // DST side
+  const Cell* V0;      // DCT side of the buffer this step reads
+  const Cell* V1;      // DST side
+  Cell* W0;            // DCT side of the buffer this step writes
+  Cell* W1;            // DST side
   int16_t* X0;         // tree-node exponents of the DCT side, N (class heap at 2 off)
   int16_t* X1;         // of the DST side
   int* ch;             // chain exponents: ch[16 s + lp + 1]
   const Sec* sec;      // fill_consts table
   int r, N;
 };
-// side selects (no indexed member arrays: they would put the row in local memory)
-QFX_HD Cell* side(const Row& R, int s) { return s ? R.V1 : R.V0; }
+// a row's view for a step that reads buffer `rb` and writes the other one
+QFX_HD Row make_row(unsigned char* base, int r, int rb, const Sec* sec) {
+  const int N = 1 << r, L = N / 2 + 2;
+  Cell* c = reinterpret_cast<Cell*>(base);
+  Row R;
+  R.V0 = c + rb * 2 * L;
+  R.V1 = R.V0 + L;
+  R.W0 = c + (rb ^ 1) * 2 * L;
+  R.W1 = R.W0 + L;
+  R.X0 = reinterpret_cast<int16_t*>(c + 4 * L);
+  R.X1 = R.X0 + N;
+  R.ch = reinterpret_cast<int*>(R.X1 + N);
+  R.sec = sec;
+  R.r = r;
+  R.N = N;
+  return R;
+}
+QFX_HD const Cell* rd(const Row& R, int s) { return s ? R.V1 : R.V0; }
+QFX_HD Cell* wr(const Row& R, int s) { return s ? R.W1 : R.W0; }
 QFX_HD int16_t* exps(const Row& R, int s) { return s ? R.X1 : R.X0; }
-
-// One item of a step: up to two output cells and two block keys.
-struct Item {
-  Cell a, b;
-  int k1, k2;
-  int seg;             // items of the item's block (a power of two); 0: no work
-};
-QFX_HD void item_none(Item& it) { it.k1 = 0; it.k2 = 0; it.seg = 0; it.a = zero(); it.b = zero(); }
+// the staged input row (buffer 1)
+QFX_HD const uint32_t* staged(unsigned char* base, int r) {
+  return reinterpret_cast<const uint32_t*>(reinterpret_cast<Cell*>(base) + 2 * ((1 << r) / 2 + 2));
+}
 
 QFX_HD Cell load_z(const uint32_t* z, int n) {
   const uint32_t w = z[n];
@@ -152,37 +186,45 @@ QFX_HD Cell load_z(const uint32_t* z, int n) {
   return c;
 }
 
+// Every step: items w in [0, items of the row); the *_key functions give an
+// item's block key(s) and block size seg (a power of two; 0: no work), the
+// *_write functions recompute the item's values from the read buffer and
+// store them, shifted by the block maxima, into the write buffer.
+
 // ---------------------------------------------------------------- fold step
 // Items w in [0, N): side s = w / (N/2), slot w1 = w mod (N/2) < N/2 - 1: the
 // fold value c(n) or d(n) of that slot, one block per class (a NORM of the
 // fold output followed by the lossless NORMs of the even/odd separations of
-// Sec. 3.1 is one NORM per class).
+// Sec. 3.1 is one NORM per class).  Reads the staged input row z.
 struct FoldDec { int s, w1, lp, P, off, i; };
-QFX_HD bool fold_dec(const Row& R, int w, FoldDec& d) {
+QFX_HD bool fold_eval(const Row& R, const uint32_t* z, int w, FoldDec& d, Cell& v) {
   const int H = R.N / 2;
   d.s = w >= H;
   d.w1 = w - d.s * H;
   if (d.w1 >= H - 1) return false;
-  d.lp = blen64((uint64_t)(H - 1 - d.w1)) - 1;
+  d.lp = blen32((uint32_t)(H - 1 - d.w1)) - 1;
   d.P = 1 << d.lp;
   d.off = H - 2 * d.P;
   d.i = d.w1 - d.off;
-  return true;
-}
-QFX_HD void fold_compute(const Row& R, const uint32_t* z, int w, Item& it) {
-  item_none(it);
-  FoldDec d;
-  if (!fold_dec(R, w, d)) return;
   const int n = (2 * d.i + 1) << (R.r - 2 - d.lp);
   const Cell a = load_z(z, n), b = load_z(z, R.N - n);
-  it.a = d.s ? sub(a, b) : add(a, b);
-  it.k1 = key(it.a);
-  it.seg = d.P;
+  v = d.s ? sub(a, b) : add(a, b);
+  return true;
 }
-QFX_HD void fold_write(const Row& R, int w, const Item& it, int bl) {
+QFX_HD void fold_key(const Row& R, const uint32_t* z, int w, int& k, int& seg) {
   FoldDec d;
-  fold_dec(R, w, d);
-  side(R, d.s)[d.w1] = rsc(it.a, bl - kBits);
+  Cell v;
+  k = 0;
+  seg = 0;
+  if (!fold_eval(R, z, w, d, v)) return;
+  k = key(v);
+  seg = d.P;
+}
+QFX_HD void fold_write(const Row& R, const uint32_t* z, int w, int bl) {
+  FoldDec d;
+  Cell v;
+  fold_eval(R, z, w, d, v);
+  wr(R, d.s)[d.w1] = rsc(v, bl - kBits);
   if (d.i == 0) {
     const int E = norm_exp(bl, kInExp);
     exps(R, d.s)[2 * d.off] = (int16_t)E;
@@ -199,9 +241,9 @@ QFX_HD void fold_base(const Row& R, const uint32_t* z) {
   b1 = rsc(b1, bl - kBits);
   const Cell c0 = add(b0, b1), c1 = sub(b0, b1);
   const int bl2 = imax(key(c0), key(c1));
-  R.V0[H - 1] = rsc(c0, bl2 - kBits);
-  R.V0[H] = rsc(c1, bl2 - kBits);
-  R.ch[0] = bl ? norm_exp(bl2, E) : kEZero;
+  R.W0[H - 1] = rsc(c0, bl2 - kBits);
+  R.W0[H] = rsc(c1, bl2 - kBits);
+  R.ch[0] = norm_exp(bl2, E);
 }
 
 // ------------------------------------------------------- forward step (depth d)
@@ -209,13 +251,14 @@ QFX_HD void fold_base(const Row& R, const uint32_t* z) {
 // butterflies of its 2^d nodes of m = P / 2^d cells, one pair (i, m-1-i) per
 // item, i < m/2 (eqs qft_1, qft_2; DST roles swapped, Sec. 3.2), and the
 // secant products of the odd-harmonic half (eq qft_38A).  Keys: k1 for the
-// even-harmonic child, k2 for the product block (x + bits + kKeyOff).
+// even-harmonic child, k2 for the product block (x + bits + kKeyOff).  The
+// classes with lp <= d and the DCT base are copied (fwd_copy).
 struct FwdDec { int s, lp, off, q, i, m, base; };
-QFX_HD bool fwd_dec(const Row& R, int dep, int w, FwdDec& d) {
+QFX_HD bool fwd_eval(const Row& R, int dep, int w, FwdDec& d, Cell& e, Cell& o) {
   const int Q4 = R.N / 4;
   d.s = w >= Q4;
   const int w1 = w - d.s * Q4;
-  d.lp = blen64((uint64_t)(Q4 - 1 - w1));
+  d.lp = blen32((uint32_t)(Q4 - 1 - w1));
   if (d.lp < dep + 1) return false;
   const int P = 1 << d.lp;
   d.off = R.N / 2 - 2 * P;
@@ -225,44 +268,60 @@ QFX_HD bool fwd_dec(const Row& R, int dep, int w, FwdDec& d) {
   d.i = w2 & ((1 << hb) - 1);
   d.m = 2 << hb;
   d.base = d.off + d.q * d.m;
+  const Cell* V = rd(R, d.s);
+  const Cell a = V[d.base + d.i], b = V[d.base + d.m - 1 - d.i];
+  e = d.s ? sub(a, b) : add(a, b);   // even-harmonic child
+  o = d.s ? add(a, b) : sub(a, b);   // odd-harmonic child, before the secant
   return true;
 }
-QFX_HD void fwd_compute(const Row& R, int dep, int w, Item& it) {
-  item_none(it);
+QFX_HD void fwd_key(const Row& R, int dep, int w, int& k1, int& k2, int& seg) {
   FwdDec d;
-  if (!fwd_dec(R, dep, w, d)) return;
-  const Cell* V = side(R, d.s);
-  const Cell a = V[d.base + d.i], b = V[d.base + d.m - 1 - d.i];
-  it.a = d.s ? sub(a, b) : add(a, b);   // even-harmonic child
-  it.b = d.s ? add(a, b) : sub(a, b);   // odd-harmonic child (before the secant)
-  it.k1 = key(it.a);
+  Cell e, o;
+  k1 = 0;
+  k2 = 0;
+  seg = 0;
+  if (!fwd_eval(R, dep, w, d, e, o)) return;
+  k1 = key(e);
   const Sec c = R.sec[(d.m >> 1) - 1 + d.i];
-  const int64_t px = (int64_t)it.b.x * c.c, py = (int64_t)it.b.y * c.c;
+  const int64_t px = (int64_t)o.x * c.c, py = (int64_t)o.y * c.c;
   const uint64_t mx = mag64(px), my = mag64(py);
   const int bl = blen64(mx > my ? mx : my);
-  it.k2 = bl ? c.x + bl + kKeyOff : 0;
-  it.seg = d.m >> 1;
+  k2 = bl ? c.x + bl + kKeyOff : 0;
+  seg = d.m >> 1;
 }
-QFX_HD void fwd_write(const Row& R, int dep, int w, const Item& it, int k1, int k2) {
+QFX_HD void fwd_write(const Row& R, int dep, int w, int k1, int k2) {
   FwdDec d;
-  fwd_dec(R, dep, w, d);
-  Cell* V = side(R, d.s);
+  Cell e, o;
+  fwd_eval(R, dep, w, d, e, o);
+  Cell* W = wr(R, d.s);
   int16_t* X = exps(R, d.s);
   const int Ein = X[2 * d.off + (1 << dep) - 1 + d.q];
-  V[d.base + d.i] = rsc(it.a, k1 - kBits);
+  W[d.base + d.i] = rsc(e, k1 - kBits);
   const Sec c = R.sec[(d.m >> 1) - 1 + d.i];
   const int top = k2 - kKeyOff - kBits;   // product block exponent - Ein
   Cell t = zero();
   if (k2) {
-    t.x = (int32_t)rs((int64_t)it.b.x * c.c, top - c.x);
-    t.y = (int32_t)rs((int64_t)it.b.y * c.c, top - c.x);
+    t.x = (int32_t)rs((int64_t)o.x * c.c, top - c.x);
+    t.y = (int32_t)rs((int64_t)o.y * c.c, top - c.x);
   }
-  V[d.base + (d.m >> 1) + d.i] = t;
+  W[d.base + (d.m >> 1) + d.i] = t;
   if (d.i == 0) {
     const int hc = 2 * d.off + (2 << dep) - 1 + 2 * d.q;
     X[hc] = (int16_t)norm_exp(k1, Ein);
     X[hc + 1] = (int16_t)(k2 ? Ein + top : kEZero);
   }
+}
+// cells a forward step leaves alone: i in [0, 2^(d+2)) -> side and slot
+// (DCT [N/2 - 2^(d+1), N/2], DST [N/2 - 2^(d+1), N/2 - 1)); returns false
+// for the indices past the DST range
+QFX_HD bool fwd_copy(const Row& R, int dep, int i) {
+  const int H = R.N / 2, c0 = (2 << dep) + 1;
+  const int s = i >= c0;
+  const int j = i - s * c0;
+  if (s && j >= (2 << dep) - 1) return false;
+  const int slot = H - (2 << dep) + j;
+  wr(R, s)[slot] = rd(R, s)[slot];
+  return true;
 }
 
 // ----------------------------------------------------- backward step (height h)
@@ -272,13 +331,14 @@ QFX_HD void fwd_write(const Row& R, int dep, int w, const Item& it, int k1, int 
 //  - lp == h - 1: item t of the class chain's combine dct(4P) (or dst(4P),
 //    lp >= 1): outputs t and 2P - t (eqs qft_5C, qft_5D; DCT item 0 also
 //    the middle output, eq qft_6).
+// Together they write every cell but the DST base at h = 1 (bwd_copy).
 struct BwdDec { int s, lp, P, off, w2; };
 QFX_HD int bwd_dec(const Row& R, int h, int w, BwdDec& d) {
   const int H = R.N / 2;
   d.s = w >= H;
   const int w1 = w - d.s * H;
   if (w1 >= H - 1) return 0;
-  d.lp = blen64((uint64_t)(H - 1 - w1)) - 1;
+  d.lp = blen32((uint32_t)(H - 1 - w1)) - 1;
   d.P = 1 << d.lp;
   d.off = H - 2 * d.P;
   d.w2 = w1 - d.off;
@@ -286,134 +346,125 @@ QFX_HD int bwd_dec(const Row& R, int h, int w, BwdDec& d) {
   if (d.lp == h - 1 && (d.s == 0 || d.lp >= 1)) return 2;    // chain item
   return 0;
 }
-QFX_HD int tree_ex(const Row& R, const BwdDec& d, int h, int& Ee, int& Ey) {
-  const int dep = d.lp - h, q = d.w2 >> h;
-  const int hc = 2 * d.off + (2 << dep) - 1 + 2 * q;
-  Ee = exps(R, d.s)[hc];
-  Ey = exps(R, d.s)[hc + 1];
-  return imax(Ee, Ey);
-}
-QFX_HD int chain_ex(const Row& R, const BwdDec& d, int& EE, int& EO) {
-  EO = exps(R, d.s)[2 * d.off];
-  EE = R.ch[16 * d.s + d.lp];
-  return imax(EE, EO);
-}
-QFX_HD void bwd_compute(const Row& R, int h, int w, Item& it) {
-  item_none(it);
-  BwdDec d;
+// The item's aligned output values (a; b and, DCT chain item 0, mid too) and
+// the exponent they are aligned to; returns the kind (0: no work).
+QFX_HD int bwd_eval(const Row& R, int h, int w, BwdDec& d, Cell& a, Cell& b, Cell& mid, int& Ex) {
   const int kind = bwd_dec(R, h, w, d);
-  if (!kind) return;
-  const Cell* V = side(R, d.s);
+  if (!kind) return 0;
+  const Cell* V = rd(R, d.s);
+  const int16_t* X = exps(R, d.s);
+  b = zero();
+  mid = zero();
   if (kind == 1) {
-    int Ee, Ey;
-    const int Ex = tree_ex(R, d, h, Ee, Ey);
+    const int dep = d.lp - h, q = d.w2 >> h;
+    const int hc = 2 * d.off + (2 << dep) - 1 + 2 * q;
+    const int Ee = X[hc], Ey = X[hc + 1];
+    Ex = imax(Ee, Ey);
     const int m = 1 << h, k = d.w2 & (m - 1);
-    const int base = d.off + (d.w2 >> h) * m, half = base + (m >> 1);
-    Cell v;
+    const int base = d.off + q * m, half = base + (m >> 1);
     if (d.s == 0) {            // DCT: X(2j) = E(j); X(2j+1) = Y(j) + Y(j+1); X(m-1) = Y(m/2-1)
-      if (!(k & 1)) v = rsc(V[base + (k >> 1)], Ex - Ee);
-      else if (k < m - 1) v = rsc(add(V[half + (k >> 1)], V[half + (k >> 1) + 1]), Ex - Ey);
-      else v = rsc(V[half + (m >> 1) - 1], Ex - Ey);
+      if (!(k & 1)) a = rsc(V[base + (k >> 1)], Ex - Ee);
+      else if (k < m - 1) a = rsc(add(V[half + (k >> 1)], V[half + (k >> 1) + 1]), Ex - Ey);
+      else a = rsc(V[half + (m >> 1) - 1], Ex - Ey);
     } else {                   // DST, slot k holds X(k+1): X(2j) = E(j); X(1) = Z(1); X(2j+1) = Z(j) + Z(j+1)
       const int kk = k + 1;
-      if (!(kk & 1)) v = rsc(V[base + (kk >> 1) - 1], Ex - Ee);
-      else if (kk == 1) v = rsc(V[half], Ex - Ey);
-      else v = rsc(add(V[half + (kk >> 1) - 1], V[half + (kk >> 1)]), Ex - Ey);
+      if (!(kk & 1)) a = rsc(V[base + (kk >> 1) - 1], Ex - Ee);
+      else if (kk == 1) a = rsc(V[half], Ex - Ey);
+      else a = rsc(add(V[half + (kk >> 1) - 1], V[half + (kk >> 1)]), Ex - Ey);
     }
-    it.a = v;
-    it.k1 = key(v);
-    it.seg = m;
-    return;
+    return 1;
   }
-  int EE, EO;
-  const int Ex = chain_ex(R, d, EE, EO);
+  const int EO = X[2 * d.off], EE = R.ch[16 * d.s + d.lp];
+  Ex = imax(EE, EO);
   const int t = d.w2, P = d.P, off = d.off;
   if (d.s == 0) {              // C(t) = E(t) + O(t), C(2P-t) = E(t) - O(t), C(P) = E(P)
     const Cell e = rsc(V[off + P + t], Ex - EE), o = rsc(V[off + t], Ex - EO);
-    it.a = add(e, o);
-    it.b = sub(e, o);
-    it.k1 = imax(key(it.a), key(it.b));
-    if (t == 0) it.k1 = imax(it.k1, key(rsc(V[off + 2 * P], Ex - EE)));
+    a = add(e, o);
+    b = sub(e, o);
+    if (t == 0) mid = rsc(V[off + 2 * P], Ex - EE);
   } else if (t == 0) {         // S(P) = O(P)
-    it.a = rsc(V[off + P - 1], Ex - EO);
-    it.k1 = key(it.a);
+    a = rsc(V[off + P - 1], Ex - EO);
   } else {                     // S(t) = E(t) + O(t), S(2P-t) = O(t) - E(t)
     const Cell e = rsc(V[off + P + t - 1], Ex - EE), o = rsc(V[off + t - 1], Ex - EO);
-    it.a = add(e, o);
-    it.b = sub(o, e);
-    it.k1 = imax(key(it.a), key(it.b));
+    a = add(e, o);
+    b = sub(o, e);
   }
-  it.seg = P;
+  return 2;
 }
-QFX_HD void bwd_write(const Row& R, int h, int w, const Item& it, int bl) {
+QFX_HD void bwd_key(const Row& R, int h, int w, int& k, int& seg) {
   BwdDec d;
-  const int kind = bwd_dec(R, h, w, d);
-  Cell* V = side(R, d.s);
+  Cell a, b, mid;
+  int Ex;
+  const int kind = bwd_eval(R, h, w, d, a, b, mid, Ex);
+  k = 0;
+  seg = 0;
+  if (!kind) return;
+  k = imax(key(a), imax(key(b), key(mid)));
+  seg = kind == 1 ? 1 << h : d.P;
+}
+QFX_HD void bwd_write(const Row& R, int h, int w, int bl) {
+  BwdDec d;
+  Cell a, b, mid;
+  int Ex;
+  const int kind = bwd_eval(R, h, w, d, a, b, mid, Ex);
+  Cell* W = wr(R, d.s);
   const int sh = bl - kBits;
   if (kind == 1) {
-    int Ee, Ey;
-    const int Ex = tree_ex(R, d, h, Ee, Ey);
     const int m = 1 << h, k = d.w2 & (m - 1), q = d.w2 >> h;
-    V[d.off + q * m + k] = rsc(it.a, sh);
+    W[d.off + q * m + k] = rsc(a, sh);
     if (k == 0) exps(R, d.s)[2 * d.off + (1 << (d.lp - h)) - 1 + q] = (int16_t)norm_exp(bl, Ex);
     return;
   }
-  int EE, EO;
-  const int Ex = chain_ex(R, d, EE, EO);
   const int t = d.w2, P = d.P, off = d.off;
   if (d.s == 0) {
+    W[off + t] = rsc(a, sh);
+    W[off + 2 * P - t] = rsc(b, sh);
     if (t == 0) {
-      const Cell mid = rsc(V[off + 2 * P], Ex - EE);   // E(P), read before C(2P) replaces it
-      V[off + P] = rsc(mid, sh);
+      W[off + P] = rsc(mid, sh);
       R.ch[d.lp + 1] = norm_exp(bl, Ex);
     }
-    V[off + t] = rsc(it.a, sh);
-    V[off + 2 * P - t] = rsc(it.b, sh);
   } else if (t == 0) {
-    V[off + P - 1] = rsc(it.a, sh);
+    W[off + P - 1] = rsc(a, sh);
     R.ch[16 + d.lp + 1] = norm_exp(bl, Ex);
   } else {
-    V[off + t - 1] = rsc(it.a, sh);
-    V[off + 2 * P - t - 1] = rsc(it.b, sh);
+    W[off + t - 1] = rsc(a, sh);
+    W[off + 2 * P - t - 1] = rsc(b, sh);
   }
+}
+// the one cell a backward step leaves alone: the DST base at h = 1
+QFX_HD void bwd_copy(const Row& R, int h) {
+  if (h == 1) R.W1[R.N / 2 - 2] = R.V1[R.N / 2 - 2];
 }
 
 // ------------------------------------------------------------- final step
 // Items k in [0, N/2): X(k) = C(k) - i S(k), X(N-k) = C(k) + i S(k) (Sec.
 // 4.1 on complex data), item 0: X(0) = C(0), X(N/2) = C(N/2); one block.
-QFX_HD int fin_ex(const Row& R, int& EC, int& ES) {
-  EC = R.ch[R.r - 1];
-  ES = R.ch[16 + R.r - 1];
-  return imax(EC, ES);
-}
-QFX_HD void fin_values(const Row& R, int k, Cell& lo, Cell& hi) {
-  int EC, ES;
-  const int Ex = fin_ex(R, EC, ES);
+QFX_HD int fin_eval(const Row& R, int k, Cell& lo, Cell& hi) {
+  const int EC = R.ch[R.r - 1], ES = R.ch[16 + R.r - 1];
+  const int Ex = imax(EC, ES);
   if (k == 0) {
     lo = rsc(R.V0[0], Ex - EC);
     hi = rsc(R.V0[R.N / 2], Ex - EC);
-    return;
+    return Ex;
   }
   const Cell a = rsc(R.V0[k], Ex - EC), b = rsc(R.V1[k - 1], Ex - ES);
   lo.x = a.x + b.y; lo.y = a.y - b.x;
   hi.x = a.x - b.y; hi.y = a.y + b.x;
+  return Ex;
 }
-QFX_HD void fin_compute(const Row& R, int k, Item& it) {
-  fin_values(R, k, it.a, it.b);
-  it.k1 = imax(key(it.a), key(it.b));
-  it.k2 = 0;
-  it.seg = R.N / 2;
+QFX_HD void fin_key(const Row& R, int k, int& key1, int& seg) {
+  Cell lo, hi;
+  fin_eval(R, k, lo, hi);
+  key1 = imax(key(lo), key(hi));
+  seg = R.N / 2;
 }
 // out: the row's N cells; *E the row exponent (0 for a row of zeros)
 QFX_HD void fin_write(const Row& R, int k, int bl, Cell* out, int* E) {
   Cell lo, hi;
-  fin_values(R, k, lo, hi);
+  const int Ex = fin_eval(R, k, lo, hi);
   out[k] = rsc(lo, bl - kBits);
   out[k == 0 ? R.N / 2 : R.N - k] = rsc(hi, bl - kBits);
-  if (k == 0) {
-    int EC, ES;
-    *E = bl ? fin_ex(R, EC, ES) + bl - kBits : 0;
-  }
+  if (k == 0) *E = bl ? Ex + bl - kBits : 0;
 }
 
 // N = 2: X(0) = z(0) + z(1), X(1) = z(0) - z(1), one block.

@@ -1,14 +1,16 @@
 // qft_k_fixed.cu -- the fixed-point variant's kernel (qft_fixed.cuh) and its
 // launcher.
 //
-// One CTA transforms one row at a time in shared memory (persistent grid over
-// the rows).  A row is a sequence of steps -- fold, the forward depths of the
-// class trees, the backward heights (tree nodes and the class chain), the
-// CDFT combine -- and every step has two phases separated by a CTA barrier:
-// each thread computes its items (register values and block keys) and takes
-// the block maxima (butterfly shuffles within a warp for blocks of fewer than
-// 32 items, which are aligned runs of lanes; one shared-memory atomicMax per
-// warp for larger blocks), then, after the barrier, shifts and stores.
+// One CTA transforms G rows at a time in shared memory (persistent grid over
+// the rows; G > 1 for rows up to 2^10).  A row is a sequence of steps --
+// fold, the forward depths of the class trees, the backward heights (tree
+// nodes and the class chain), the CDFT combine -- and every step has two
+// phases separated by a CTA barrier: each thread evaluates its items and
+// takes their block maxima (butterfly shuffles within a warp for blocks of
+// fewer than 32 items, which are aligned runs of lanes; one shared-memory
+// atomicMax per warp for larger blocks); after the barrier it evaluates them
+// again from the step's read buffer and stores them, shifted, into the other
+// buffer (so only the keys live across the barrier).
 #include "qft_internal.h"
 #include "qft_fixed.cuh"
 
@@ -32,147 +34,154 @@ __device__ __forceinline__ int block_max(int k, int seg, int* slot, int w) {
 __device__ __forceinline__ int block_get(int k, int seg, const int* slot, int w) {
   return seg >= 32 ? slot[(w & ~(seg - 1)) >> 5] : k;
 }
+// the same value, hidden from the compiler, so that the store phase decodes its
+// items again instead of keeping the evaluation phase's registers alive
+__device__ __forceinline__ int opaque(int v) {
+  int r;
+  asm volatile("mov.b32 %0, %1;" : "=r"(r) : "r"(v));
+  return r;
+}
 
-// NT threads, K items per thread per step (K * NT >= N).
+// One step over `items` items of the CTA's rows: NI items per thread; kf(w,
+// k1, k2, seg) gives an item's block keys and block size, wf(w, max1, max2)
+// stores it.  TWO: the step has a second key (the forward products).
+template <int NT, int NI, bool TWO, class KF, class WF>
+__device__ __forceinline__ void fx_step(int* slots, int NS, int items, KF kf, WF wf) {
+  int k1[NI], k2[NI], sg[NI];
+#pragma unroll
+  for (int kk = 0; kk < NI; ++kk) {
+    const int w = threadIdx.x + kk * NT;
+    k1[kk] = 0;
+    k2[kk] = 0;
+    sg[kk] = 0;
+    if (w < items) kf(w, k1[kk], k2[kk], sg[kk]);
+    k1[kk] = block_max(k1[kk], sg[kk], slots, w);
+    if (TWO) k2[kk] = block_max(k2[kk], sg[kk], slots + NS, w);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int kk = 0; kk < NI; ++kk) {
+    const int w = opaque(threadIdx.x + kk * NT);
+    if (sg[kk]) wf(w, block_get(k1[kk], sg[kk], slots, w), TWO ? block_get(k2[kk], sg[kk], slots + NS, w) : 0);
+  }
+}
+
+// NT threads, K items per thread in the fold and backward steps (K NT = G N:
+// G = 2^lgG rows per CTA pass); the forward and final steps have half as many.
 template <int NT, int K>
-__global__ void __launch_bounds__(NT) k_fixed(const uint32_t* __restrict__ z, Cell* __restrict__ out,
+__global__ void __launch_bounds__(NT, 1024 / NT) k_fixed(const uint32_t* __restrict__ z, Cell* __restrict__ out,
                                               int* __restrict__ eout, const Sec* __restrict__ sec, int r,
-                                              int64_t batch) {
+                                              int64_t batch, int lgG) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int N = 1 << r, H = N / 2, NS = slot_count(N);
-  Row R;
-  R.V0 = reinterpret_cast<Cell*>(sm);
-  R.V1 = R.V0 + (H + 2);
-  R.X0 = reinterpret_cast<int16_t*>(R.V1 + (H + 2));
-  R.X1 = R.X0 + N;
-  int* slots = reinterpret_cast<int*>(R.X1 + N);   // [2 alternates][2 keys][NS]
-  R.ch = slots + 4 * NS;
-  R.sec = sec;
-  R.r = r;
-  R.N = N;
-  const int tid = threadIdx.x;
-  for (int64_t row = blockIdx.x; row < batch; row += gridDim.x) {
-    const uint32_t* zr = z + row * N;
-    Cell* orow = out + row * N;
-    if (N == 2) {
-      if (tid == 0) row_n2(zr, orow, eout + row);
-      continue;
+  const int N = 1 << r, G = 1 << lgG, tid = threadIdx.x;
+  if (N == 2) {   // one row per thread
+    for (int64_t row = (int64_t)blockIdx.x * NT + tid; row < batch; row += (int64_t)gridDim.x * NT)
+      row_n2(z + 2 * row, out + 2 * row, eout + row);
+    return;
+  }
+  const int rbytes = (int)row_bytes(N);
+  const int NS = slot_count(G * N);
+  int* slot_base = reinterpret_cast<int*>(sm + G * rbytes);   // [2 alternates][2 keys][NS]
+  for (int64_t r0 = (int64_t)blockIdx.x * G; r0 < batch; r0 += (int64_t)gridDim.x * G) {
+    const int gv = batch - r0 < G ? (int)(batch - r0) : G;
+    for (int i = tid; i < gv * N; i += NT) {   // stage the rows' input (coalesced)
+      const int g = i >> r;
+      const_cast<uint32_t*>(staged(sm + g * rbytes, r))[i & (N - 1)] = z[(r0 + g) * N + (i & (N - 1))];
     }
-    for (int i = tid; i < 4 * NS; i += NT) slots[i] = 0;
+    for (int i = tid; i < 4 * NS; i += NT) slot_base[i] = 0;
     __syncthreads();
-    int cur = 0;
-    // the slots of the next step are cleared while this step stores
-    const auto clear_next = [&]() {
-      int* nx = slots + (cur ^ 1) * 2 * NS;
+    int cur = 0, rb = 1;   // slot set; buffer the next step reads (the fold reads the staged input)
+    const auto row_of = [&](int g) { return make_row(sm + g * rbytes, r, rb, sec); };
+    const auto end_step = [&]() {
+      int* nx = slot_base + (cur ^ 1) * 2 * NS;   // cleared for the next step while this one stores
       for (int i = tid; i < 2 * NS; i += NT) nx[i] = 0;
+      __syncthreads();
+      cur ^= 1;
+      rb ^= 1;
     };
     {  // fold (Sec. 4.2 on complex data) and the class blocks
-      Item it[K];
-      if (tid == 0) fold_base(R, zr);
-#pragma unroll
-      for (int kk = 0; kk < K; ++kk) {
-        const int w = tid + kk * NT;
-        if (w < N) fold_compute(R, zr, w, it[kk]);
-        else item_none(it[kk]);
-        it[kk].k1 = block_max(it[kk].k1, it[kk].seg, slots + cur * 2 * NS, w);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < K; ++kk) {
-        const int w = tid + kk * NT;
-        if (it[kk].seg) fold_write(R, w, it[kk], block_get(it[kk].k1, it[kk].seg, slots + cur * 2 * NS, w));
-      }
-      clear_next();
-      __syncthreads();
-      cur ^= 1;
+      int* sl = slot_base + cur * 2 * NS;
+      for (int g = tid; g < gv; g += NT) fold_base(row_of(g), staged(sm + g * rbytes, r));
+      fx_step<NT, K, false>(
+          sl, NS, gv * N,
+          [&](int w, int& k1, int&, int& seg) {
+            const int g = w >> r;
+            fold_key(row_of(g), staged(sm + g * rbytes, r), w & (N - 1), k1, seg);
+          },
+          [&](int w, int m1, int) {
+            const int g = w >> r;
+            fold_write(row_of(g), staged(sm + g * rbytes, r), w & (N - 1), m1);
+          });
+      end_step();
     }
     for (int dep = 0; dep <= r - 3; ++dep) {   // mirror butterflies and secant products
-      Item it[K / 2 > 0 ? K / 2 : 1];
-#pragma unroll
-      for (int kk = 0; kk < (K / 2 > 0 ? K / 2 : 1); ++kk) {
-        const int w = tid + kk * NT;
-        if (w < H) fwd_compute(R, dep, w, it[kk]);
-        else item_none(it[kk]);
-        it[kk].k1 = block_max(it[kk].k1, it[kk].seg, slots + cur * 2 * NS, w);
-        it[kk].k2 = block_max(it[kk].k2, it[kk].seg, slots + cur * 2 * NS + NS, w);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < (K / 2 > 0 ? K / 2 : 1); ++kk) {
-        const int w = tid + kk * NT;
-        if (it[kk].seg)
-          fwd_write(R, dep, w, it[kk], block_get(it[kk].k1, it[kk].seg, slots + cur * 2 * NS, w),
-                    block_get(it[kk].k2, it[kk].seg, slots + cur * 2 * NS + NS, w));
-      }
-      clear_next();
-      __syncthreads();
-      cur ^= 1;
+      int* sl = slot_base + cur * 2 * NS;
+      fx_step<NT, K / 2, true>(
+          sl, NS, gv * (N / 2),
+          [&](int w, int& k1, int& k2, int& seg) { fwd_key(row_of(w >> (r - 1)), dep, w & (N / 2 - 1), k1, k2, seg); },
+          [&](int w, int m1, int m2) { fwd_write(row_of(w >> (r - 1)), dep, w & (N / 2 - 1), m1, m2); });
+      const int cl = dep + 2;   // 2^(dep+2) copy indices per row
+      for (int i = tid; i < (gv << cl); i += NT) fwd_copy(row_of(i >> cl), dep, i & ((1 << cl) - 1));
+      end_step();
     }
     for (int h = 1; h <= r - 1; ++h) {         // node outputs and the class chain
-      Item it[K];
-#pragma unroll
-      for (int kk = 0; kk < K; ++kk) {
-        const int w = tid + kk * NT;
-        if (w < N) bwd_compute(R, h, w, it[kk]);
-        else item_none(it[kk]);
-        it[kk].k1 = block_max(it[kk].k1, it[kk].seg, slots + cur * 2 * NS, w);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < K; ++kk) {
-        const int w = tid + kk * NT;
-        if (it[kk].seg) bwd_write(R, h, w, it[kk], block_get(it[kk].k1, it[kk].seg, slots + cur * 2 * NS, w));
-      }
-      clear_next();
-      __syncthreads();
-      cur ^= 1;
+      int* sl = slot_base + cur * 2 * NS;
+      fx_step<NT, K, false>(
+          sl, NS, gv * N,
+          [&](int w, int& k1, int&, int& seg) { bwd_key(row_of(w >> r), h, w & (N - 1), k1, seg); },
+          [&](int w, int m1, int) { bwd_write(row_of(w >> r), h, w & (N - 1), m1); });
+      if (h == 1)
+        for (int g = tid; g < gv; g += NT) bwd_copy(row_of(g), h);
+      end_step();
     }
-    {  // CDFT combine, one block: the row exponent
-      int kf[K / 2 > 0 ? K / 2 : 1], sg[K / 2 > 0 ? K / 2 : 1];
-#pragma unroll
-      for (int kk = 0; kk < (K / 2 > 0 ? K / 2 : 1); ++kk) {
-        const int w = tid + kk * NT;
-        Item it;
-        if (w < H) fin_compute(R, w, it);
-        else item_none(it);
-        kf[kk] = block_max(it.k1, it.seg, slots + cur * 2 * NS, w);
-        sg[kk] = it.seg;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < (K / 2 > 0 ? K / 2 : 1); ++kk) {
-        const int w = tid + kk * NT;
-        if (sg[kk]) fin_write(R, w, block_get(kf[kk], sg[kk], slots + cur * 2 * NS, w), orow, eout + row);
-      }
-      __syncthreads();   // the next row reuses the shared memory
+    {  // CDFT combine, one block per row: the row exponents
+      int* sl = slot_base + cur * 2 * NS;
+      fx_step<NT, K / 2, false>(
+          sl, NS, gv * (N / 2),
+          [&](int w, int& k1, int&, int& seg) { fin_key(row_of(w >> (r - 1)), w & (N / 2 - 1), k1, seg); },
+          [&](int w, int m1, int) {
+            const int g = w >> (r - 1);
+            fin_write(row_of(g), w & (N / 2 - 1), m1, out + (r0 + g) * N, eout + r0 + g);
+          });
+      end_step();   // the next pass restages buffer 1
     }
   }
 }
 
 struct FxCfg {
-  int nt, k;
+  int nt, k, lgG;
 };
-// threads and items per thread of a row of length 2^r
+// threads, items per thread and rows per CTA pass for rows of length 2^r:
+// about 48 KB of shared memory per CTA up to 2^11 (four CTAs of 256 threads
+// per SM), one row of 2^12 (512 threads) or 2^13 (1024 threads)
 inline FxCfg fx_cfg(int r) {
+  if (r <= 1) return {256, 8, 0};
+  if (r == 12) return {512, 8, 0};
+  if (r == 13) return {1024, 8, 0};
   const int N = 1 << r;
-  if (N <= 128) return {32, 4};
-  if (N <= 2048) return {N / 4, 4};
-  return {N / 8, 8};
+  int G = 2048 >> r;
+  while (G > 1 && (size_t)G * row_bytes(N) > 49152) G >>= 1;
+  int lg = 0;
+  while ((1 << lg) < G) ++lg;
+  return {256, G * N / 256, lg};
 }
 
 template <int NT, int K>
-cudaError_t launch_k(const qft_plan p, const uint32_t* z, Cell* out, int* eout, cudaStream_t st) {
-  const size_t smem = smem_bytes((int)p->n);
+cudaError_t launch_k(const qft_plan p, const FxCfg& c, const uint32_t* z, Cell* out, int* eout, cudaStream_t st) {
+  const int N = (int)p->n, G = 1 << c.lgG;
+  const size_t smem = N == 2 ? 0 : G * row_bytes(N) + sizeof(int) * 4 * (size_t)slot_count(G * N);
   cudaError_t e = cudaFuncSetAttribute(k_fixed<NT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fixed<NT, K>, NT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t per_cta = N == 2 ? NT : G;
   int64_t grid = (int64_t)per_sm * p->sms;
-  if (grid > p->batch) grid = p->batch;
+  const int64_t need = (p->batch + per_cta - 1) / per_cta;
+  if (grid > need) grid = need;
   k_fixed<NT, K><<<(unsigned)grid, NT, smem, st>>>(z, out, eout, reinterpret_cast<const Sec*>(p->d_fx), p->r,
-                                                  p->batch);
+                                                  p->batch, c.lgG);
   return cudaGetLastError();
 }
 
@@ -190,7 +199,7 @@ int qft_fixed_prepare(qft_plan p) {
   if (e != cudaSuccess) return qft_set_cuda(p, e);
   const FxCfg c = fx_cfg(p->r);
   p->threads = c.nt;
-  p->smem = smem_bytes(N);
+  p->smem = N == 2 ? 0 : (size_t)(1 << c.lgG) * row_bytes(N) + sizeof(int) * 4 * (size_t)slot_count((1 << c.lgG) * N);
   return QFT_OK;
 }
 
@@ -198,18 +207,15 @@ int qft_launch_fixed(qft_plan p, const void* in, void* out, int32_t* exps, cudaS
   const uint32_t* z = static_cast<const uint32_t*>(in);
   Cell* o = static_cast<Cell*>(out);
   int* eo = reinterpret_cast<int*>(exps);
+  const FxCfg c = fx_cfg(p->r);
   cudaError_t e;
   qft_time_begin(p, st, QFT_KERNEL_ROWS);
-  switch (p->r) {
-  case 1: case 2: case 3: case 4: case 5: case 6: case 7: e = launch_k<32, 4>(p, z, o, eo, st); break;
-  case 8: e = launch_k<64, 4>(p, z, o, eo, st); break;
-  case 9: e = launch_k<128, 4>(p, z, o, eo, st); break;
-  case 10: e = launch_k<256, 4>(p, z, o, eo, st); break;
-  case 11: e = launch_k<512, 4>(p, z, o, eo, st); break;
-  case 12: e = launch_k<512, 8>(p, z, o, eo, st); break;
-  case 13: e = launch_k<1024, 8>(p, z, o, eo, st); break;
-  default: return QFT_ERR_INVALID_N;
-  }
+  if (c.nt == 256 && c.k == 2) e = launch_k<256, 2>(p, c, z, o, eo, st);
+  else if (c.nt == 256 && c.k == 4) e = launch_k<256, 4>(p, c, z, o, eo, st);
+  else if (c.nt == 256 && c.k == 8) e = launch_k<256, 8>(p, c, z, o, eo, st);
+  else if (c.nt == 512) e = launch_k<512, 8>(p, c, z, o, eo, st);
+  else if (c.nt == 1024) e = launch_k<1024, 8>(p, c, z, o, eo, st);
+  else return QFT_ERR_INVALID_N;
   qft_time_end(p, st);
   return qft_set_cuda(p, e);
 }

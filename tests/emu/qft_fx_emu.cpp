@@ -16,29 +16,29 @@ using namespace qfx;
 
 namespace {
 
-// block maxima of k1 / k2 over aligned runs of `seg` items; returns false if
-// the block structure breaks the kernel's assumptions
-bool reduce(const std::vector<Item>& it, std::vector<int>& m1, std::vector<int>& m2) {
-  const int n = (int)it.size();
+// One step's keys -> block maxima over aligned runs of `seg` items; false if
+// the block structure breaks the kernel's assumptions.
+bool reduce(const std::vector<int>& seg, const std::vector<int>& k1, const std::vector<int>& k2,
+            std::vector<int>& m1, std::vector<int>& m2) {
+  const int n = (int)seg.size();
   std::vector<int> b1(n, 0), b2(n, 0);
   for (int w = 0; w < n; ++w) {
-    const int sg = it[w].seg;
+    const int sg = seg[w];
     if (!sg) continue;
     if (sg & (sg - 1)) return false;
     const int b = w & ~(sg - 1);
     if (b + sg > n) return false;
     for (int v = b; v < b + sg; ++v)
-      if (it[v].seg != sg) return false;   // same block size everywhere in the block
-    b1[b] = imax(b1[b], it[w].k1);
-    b2[b] = imax(b2[b], it[w].k2);
+      if (seg[v] != sg) return false;   // same block size everywhere in the block
+    b1[b] = imax(b1[b], k1[w]);
+    b2[b] = imax(b2[b], k2[w]);
   }
   m1.assign(n, 0);
   m2.assign(n, 0);
   for (int w = 0; w < n; ++w) {
-    const int sg = it[w].seg;
-    if (!sg) continue;
-    m1[w] = b1[w & ~(sg - 1)];
-    m2[w] = b2[w & ~(sg - 1)];
+    if (!seg[w]) continue;
+    m1[w] = b1[w & ~(seg[w] - 1)];
+    m2[w] = b2[w & ~(seg[w] - 1)];
   }
   return true;
 }
@@ -46,36 +46,46 @@ bool reduce(const std::vector<Item>& it, std::vector<int>& m1, std::vector<int>&
 int row(int r, const uint32_t* z, Cell* out, int* E, const std::vector<Sec>& sec) {
   const int N = 1 << r, H = N / 2;
   if (N == 2) { row_n2(z, out, E); return 0; }
-  std::vector<Cell> V0(H + 2), V1(H + 2);
-  std::vector<int16_t> X0(N, 0x5555), X1(N, 0x5555);   // garbage: every read must follow a write
-  std::vector<int> ch(32, 0x5555);
-  Row R;
-  R.V0 = V0.data(); R.V1 = V1.data(); R.X0 = X0.data(); R.X1 = X1.data(); R.ch = ch.data();
-  R.sec = sec.data(); R.r = r; R.N = N;
-  std::vector<int> m1, m2;
+  // the row's shared-memory image; garbage everywhere, so that a read before a write shows
+  std::vector<unsigned char> mem(row_bytes(N), 0x55);
+  unsigned char* base = mem.data();
+  uint32_t* zs = const_cast<uint32_t*>(staged(base, r));
+  for (int n = 0; n < N; ++n) zs[n] = z[n];
+  int rb = 1;
+  std::vector<int> k1, k2, sg, m1, m2;
+  const auto keys = [&](int items) { k1.assign(items, 0); k2.assign(items, 0); sg.assign(items, 0); };
   {
-    std::vector<Item> it(N);
-    fold_base(R, z);
-    for (int w = 0; w < N; ++w) fold_compute(R, z, w, it[w]);
-    if (!reduce(it, m1, m2)) return -2;
-    for (int w = 0; w < N; ++w) if (it[w].seg) fold_write(R, w, it[w], m1[w]);
+    Row R = make_row(base, r, rb, sec.data());
+    keys(N);
+    fold_base(R, zs);
+    for (int w = 0; w < N; ++w) fold_key(R, zs, w, k1[w], sg[w]);
+    if (!reduce(sg, k1, k2, m1, m2)) return -2;
+    for (int w = 0; w < N; ++w) if (sg[w]) fold_write(R, zs, w, m1[w]);
+    rb ^= 1;
   }
   for (int dep = 0; dep <= r - 3; ++dep) {
-    std::vector<Item> it(H);
-    for (int w = 0; w < H; ++w) fwd_compute(R, dep, w, it[w]);
-    if (!reduce(it, m1, m2)) return -3;
-    for (int w = 0; w < H; ++w) if (it[w].seg) fwd_write(R, dep, w, it[w], m1[w], m2[w]);
+    Row R = make_row(base, r, rb, sec.data());
+    keys(H);
+    for (int w = 0; w < H; ++w) fwd_key(R, dep, w, k1[w], k2[w], sg[w]);
+    if (!reduce(sg, k1, k2, m1, m2)) return -3;
+    for (int w = 0; w < H; ++w) if (sg[w]) fwd_write(R, dep, w, m1[w], m2[w]);
+    for (int i = 0; i < (4 << dep); ++i) fwd_copy(R, dep, i);
+    rb ^= 1;
   }
   for (int h = 1; h <= r - 1; ++h) {
-    std::vector<Item> it(N);
-    for (int w = 0; w < N; ++w) bwd_compute(R, h, w, it[w]);
-    if (!reduce(it, m1, m2)) return -4;
-    for (int w = 0; w < N; ++w) if (it[w].seg) bwd_write(R, h, w, it[w], m1[w]);
+    Row R = make_row(base, r, rb, sec.data());
+    keys(N);
+    for (int w = 0; w < N; ++w) bwd_key(R, h, w, k1[w], sg[w]);
+    if (!reduce(sg, k1, k2, m1, m2)) return -4;
+    for (int w = 0; w < N; ++w) if (sg[w]) bwd_write(R, h, w, m1[w]);
+    bwd_copy(R, h);
+    rb ^= 1;
   }
   {
-    std::vector<Item> it(H);
-    for (int w = 0; w < H; ++w) fin_compute(R, w, it[w]);
-    if (!reduce(it, m1, m2)) return -5;
+    Row R = make_row(base, r, rb, sec.data());
+    keys(H);
+    for (int w = 0; w < H; ++w) fin_key(R, w, k1[w], sg[w]);
+    if (!reduce(sg, k1, k2, m1, m2)) return -5;
     for (int w = 0; w < H; ++w) fin_write(R, w, m1[w], out, E);
   }
   return 0;
