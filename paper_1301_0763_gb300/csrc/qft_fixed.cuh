@@ -20,9 +20,9 @@
 // is a function of block operands and block maxima only, so the order in which
 // threads run does not change a bit.
 //
-// Layout of one row (N = 2^r, 4 <= N <= 2^kMaxLog2) in each of its two cell
-// buffers, per side s (0: DCT network on c(n) = z(n) + z(N-n), 1: DST network
-// on d(n) = z(n) - z(N-n)): cells V[s][0 .. N/2].  The class of 2-adic valuation j (a dct_ot /
+// Shared-memory layout of one row (N = 2^r, 4 <= N <= 2^kMaxLog2), per side s
+// (0: DCT network on c(n) = z(n) + z(N-n), 1: DST network on d(n) = z(n) -
+// z(N-n)): cells V[s][0 .. N/2].  The class of 2-adic valuation j (a dct_ot /
 // dst_ot of periodization M = N/2^j with P = N/2^(j+2) points; lp = log2 P)
 // holds slots [off, off + P), off = N/2 - 2P, its time index n = 2^j (2i+1)
 // at slot off + i.  The DCT chain's base pair c(0), c(N/2) sits at N/2 - 1,
@@ -132,37 +132,30 @@ inline void fill_consts(int N, Sec* tab) {
 }
 
 // ------------------------------------------------------------ row storage
-// One row in shared memory: two cell buffers (each a DCT side and a DST side
-// of N/2 + 2 cells; a step reads one and writes the other, so that its stores
-// need no second barrier), the tree-node exponents of both sides (int16, N
-// each) and the chain exponents (32 ints).  Buffer 1 first holds the staged
-// input row (N words).
-QFX_HD size_t row_bytes(int N) { return 32 * (size_t)(N / 2 + 2) + 4 * (size_t)N + 128; }
+// One row in shared memory: the cells of both sides (N/2 + 2 each), the
+// tree-node exponents of both sides (int16, N each) and the chain exponents
+// (32 ints).  The DST side first holds the staged input row (N words): the
+// fold step reads all of it before it stores any cell.
+QFX_HD size_t row_bytes(int N) { return 16 * (size_t)(N / 2 + 2) + 4 * (size_t)N + 128; }
 // block-maximum slots of a CTA whose steps have up to `items` items: two
 // alternating sets of two keys
 QFX_HD int slot_count(int items) { return items >= 64 ? items / 32 : 2; }
 
 struct Row {
-  const Cell* V0;      // DCT side of the buffer this step reads
-  const Cell* V1;      // DST side
-  Cell* W0;            // DCT side of the buffer this step writes
-  Cell* W1;            // DST side
+  Cell* V0;            // DCT side
+  Cell* V1;            // DST side
   int16_t* X0;         // tree-node exponents of the DCT side, N (class heap at 2 off)
   int16_t* X1;         // of the DST side
   int* ch;             // chain exponents: ch[16 s + lp + 1]
   const Sec* sec;      // fill_consts table
   int r, N;
 };
-// a row's view for a step that reads buffer `rb` and writes the other one
-QFX_HD Row make_row(unsigned char* base, int r, int rb, const Sec* sec) {
+QFX_HD Row make_row(unsigned char* base, int r, const Sec* sec) {
   const int N = 1 << r, L = N / 2 + 2;
-  Cell* c = reinterpret_cast<Cell*>(base);
   Row R;
-  R.V0 = c + rb * 2 * L;
+  R.V0 = reinterpret_cast<Cell*>(base);
   R.V1 = R.V0 + L;
-  R.W0 = c + (rb ^ 1) * 2 * L;
-  R.W1 = R.W0 + L;
-  R.X0 = reinterpret_cast<int16_t*>(c + 4 * L);
+  R.X0 = reinterpret_cast<int16_t*>(R.V1 + L);
   R.X1 = R.X0 + N;
   R.ch = reinterpret_cast<int*>(R.X1 + N);
   R.sec = sec;
@@ -170,13 +163,10 @@ QFX_HD Row make_row(unsigned char* base, int r, int rb, const Sec* sec) {
   R.N = N;
   return R;
 }
-QFX_HD const Cell* rd(const Row& R, int s) { return s ? R.V1 : R.V0; }
-QFX_HD Cell* wr(const Row& R, int s) { return s ? R.W1 : R.W0; }
+QFX_HD Cell* side(const Row& R, int s) { return s ? R.V1 : R.V0; }
 QFX_HD int16_t* exps(const Row& R, int s) { return s ? R.X1 : R.X0; }
-// the staged input row (buffer 1)
-QFX_HD const uint32_t* staged(unsigned char* base, int r) {
-  return reinterpret_cast<const uint32_t*>(reinterpret_cast<Cell*>(base) + 2 * ((1 << r) / 2 + 2));
-}
+// the staged input row (over the DST side)
+QFX_HD uint32_t* staged(const Row& R) { return reinterpret_cast<uint32_t*>(R.V1); }
 
 QFX_HD Cell load_z(const uint32_t* z, int n) {
   const uint32_t w = z[n];
@@ -186,18 +176,25 @@ QFX_HD Cell load_z(const uint32_t* z, int n) {
   return c;
 }
 
-// Every step: items w in [0, items of the row); the *_key functions give an
-// item's block key(s) and block size seg (a power of two; 0: no work), the
-// *_write functions recompute the item's values from the read buffer and
-// store them, shifted by the block maxima, into the write buffer.
+// Every step: items w in [0, items of the row).  An item's eval function
+// reads its operands and gives its (unnormalized) values, its block key(s)
+// and its block size seg (a power of two; 0: no work); after the CTA barrier
+// its store function writes the values, shifted by the block maxima, in place.
+struct Val {
+  Cell a, b;           // output values
+  int k1, k2;          // block keys
+  int seg;
+  int ex;              // exponent the values are aligned to (backward, final)
+};
+QFX_HD void val_none(Val& v) { v.a = zero(); v.b = zero(); v.k1 = 0; v.k2 = 0; v.seg = 0; v.ex = 0; }
 
 // ---------------------------------------------------------------- fold step
 // Items w in [0, N): side s = w / (N/2), slot w1 = w mod (N/2) < N/2 - 1: the
 // fold value c(n) or d(n) of that slot, one block per class (a NORM of the
 // fold output followed by the lossless NORMs of the even/odd separations of
-// Sec. 3.1 is one NORM per class).  Reads the staged input row z.
+// Sec. 3.1 is one NORM per class).
 struct FoldDec { int s, w1, lp, P, off, i; };
-QFX_HD bool fold_eval(const Row& R, const uint32_t* z, int w, FoldDec& d, Cell& v) {
+QFX_HD bool fold_dec(const Row& R, int w, FoldDec& d) {
   const int H = R.N / 2;
   d.s = w >= H;
   d.w1 = w - d.s * H;
@@ -206,25 +203,22 @@ QFX_HD bool fold_eval(const Row& R, const uint32_t* z, int w, FoldDec& d, Cell& 
   d.P = 1 << d.lp;
   d.off = H - 2 * d.P;
   d.i = d.w1 - d.off;
-  const int n = (2 * d.i + 1) << (R.r - 2 - d.lp);
-  const Cell a = load_z(z, n), b = load_z(z, R.N - n);
-  v = d.s ? sub(a, b) : add(a, b);
   return true;
 }
-QFX_HD void fold_key(const Row& R, const uint32_t* z, int w, int& k, int& seg) {
+QFX_HD void fold_eval(const Row& R, const uint32_t* z, int w, Val& v) {
+  val_none(v);
   FoldDec d;
-  Cell v;
-  k = 0;
-  seg = 0;
-  if (!fold_eval(R, z, w, d, v)) return;
-  k = key(v);
-  seg = d.P;
+  if (!fold_dec(R, w, d)) return;
+  const int n = (2 * d.i + 1) << (R.r - 2 - d.lp);
+  const Cell a = load_z(z, n), b = load_z(z, R.N - n);
+  v.a = d.s ? sub(a, b) : add(a, b);
+  v.k1 = key(v.a);
+  v.seg = d.P;
 }
-QFX_HD void fold_write(const Row& R, const uint32_t* z, int w, int bl) {
+QFX_HD void fold_store(const Row& R, int w, const Val& v, int bl) {
   FoldDec d;
-  Cell v;
-  fold_eval(R, z, w, d, v);
-  wr(R, d.s)[d.w1] = rsc(v, bl - kBits);
+  fold_dec(R, w, d);
+  side(R, d.s)[d.w1] = rsc(v.a, bl - kBits);
   if (d.i == 0) {
     const int E = norm_exp(bl, kInExp);
     exps(R, d.s)[2 * d.off] = (int16_t)E;
@@ -232,6 +226,8 @@ QFX_HD void fold_write(const Row& R, const uint32_t* z, int w, int bl) {
   }
 }
 // The DCT chain's base: c(0), c(N/2) normalized, then dct(2) (eq qft_0B).
+// Reads z(0), z(N/2) before the fold's barrier; the two cells it stores are
+// on the DCT side, away from the staged row.
 QFX_HD void fold_base(const Row& R, const uint32_t* z) {
   const int H = R.N / 2;
   Cell b0 = load_z(z, 0), b1 = load_z(z, H);
@@ -241,8 +237,8 @@ QFX_HD void fold_base(const Row& R, const uint32_t* z) {
   b1 = rsc(b1, bl - kBits);
   const Cell c0 = add(b0, b1), c1 = sub(b0, b1);
   const int bl2 = imax(key(c0), key(c1));
-  R.W0[H - 1] = rsc(c0, bl2 - kBits);
-  R.W0[H] = rsc(c1, bl2 - kBits);
+  R.V0[H - 1] = rsc(c0, bl2 - kBits);
+  R.V0[H] = rsc(c1, bl2 - kBits);
   R.ch[0] = norm_exp(bl2, E);
 }
 
@@ -251,10 +247,10 @@ QFX_HD void fold_base(const Row& R, const uint32_t* z) {
 // butterflies of its 2^d nodes of m = P / 2^d cells, one pair (i, m-1-i) per
 // item, i < m/2 (eqs qft_1, qft_2; DST roles swapped, Sec. 3.2), and the
 // secant products of the odd-harmonic half (eq qft_38A).  Keys: k1 for the
-// even-harmonic child, k2 for the product block (x + bits + kKeyOff).  The
-// classes with lp <= d and the DCT base are copied (fwd_copy).
+// even-harmonic child, k2 for the product block (x + bits + kKeyOff); the
+// values are the child e and the difference o before the secant.
 struct FwdDec { int s, lp, off, q, i, m, base; };
-QFX_HD bool fwd_eval(const Row& R, int dep, int w, FwdDec& d, Cell& e, Cell& o) {
+QFX_HD bool fwd_dec(const Row& R, int dep, int w, FwdDec& d) {
   const int Q4 = R.N / 4;
   d.s = w >= Q4;
   const int w1 = w - d.s * Q4;
@@ -268,60 +264,44 @@ QFX_HD bool fwd_eval(const Row& R, int dep, int w, FwdDec& d, Cell& e, Cell& o) 
   d.i = w2 & ((1 << hb) - 1);
   d.m = 2 << hb;
   d.base = d.off + d.q * d.m;
-  const Cell* V = rd(R, d.s);
-  const Cell a = V[d.base + d.i], b = V[d.base + d.m - 1 - d.i];
-  e = d.s ? sub(a, b) : add(a, b);   // even-harmonic child
-  o = d.s ? add(a, b) : sub(a, b);   // odd-harmonic child, before the secant
   return true;
 }
-QFX_HD void fwd_key(const Row& R, int dep, int w, int& k1, int& k2, int& seg) {
+QFX_HD void fwd_eval(const Row& R, int dep, int w, Val& v) {
+  val_none(v);
   FwdDec d;
-  Cell e, o;
-  k1 = 0;
-  k2 = 0;
-  seg = 0;
-  if (!fwd_eval(R, dep, w, d, e, o)) return;
-  k1 = key(e);
+  if (!fwd_dec(R, dep, w, d)) return;
+  const Cell* V = side(R, d.s);
+  const Cell a = V[d.base + d.i], b = V[d.base + d.m - 1 - d.i];
+  v.a = d.s ? sub(a, b) : add(a, b);   // even-harmonic child
+  v.b = d.s ? add(a, b) : sub(a, b);   // odd-harmonic child, before the secant
+  v.k1 = key(v.a);
   const Sec c = R.sec[(d.m >> 1) - 1 + d.i];
-  const int64_t px = (int64_t)o.x * c.c, py = (int64_t)o.y * c.c;
+  const int64_t px = (int64_t)v.b.x * c.c, py = (int64_t)v.b.y * c.c;
   const uint64_t mx = mag64(px), my = mag64(py);
   const int bl = blen64(mx > my ? mx : my);
-  k2 = bl ? c.x + bl + kKeyOff : 0;
-  seg = d.m >> 1;
+  v.k2 = bl ? c.x + bl + kKeyOff : 0;
+  v.seg = d.m >> 1;
 }
-QFX_HD void fwd_write(const Row& R, int dep, int w, int k1, int k2) {
+QFX_HD void fwd_store(const Row& R, int dep, int w, const Val& v, int k1, int k2) {
   FwdDec d;
-  Cell e, o;
-  fwd_eval(R, dep, w, d, e, o);
-  Cell* W = wr(R, d.s);
+  fwd_dec(R, dep, w, d);
+  Cell* V = side(R, d.s);
   int16_t* X = exps(R, d.s);
   const int Ein = X[2 * d.off + (1 << dep) - 1 + d.q];
-  W[d.base + d.i] = rsc(e, k1 - kBits);
+  V[d.base + d.i] = rsc(v.a, k1 - kBits);
   const Sec c = R.sec[(d.m >> 1) - 1 + d.i];
   const int top = k2 - kKeyOff - kBits;   // product block exponent - Ein
   Cell t = zero();
   if (k2) {
-    t.x = (int32_t)rs((int64_t)o.x * c.c, top - c.x);
-    t.y = (int32_t)rs((int64_t)o.y * c.c, top - c.x);
+    t.x = (int32_t)rs((int64_t)v.b.x * c.c, top - c.x);
+    t.y = (int32_t)rs((int64_t)v.b.y * c.c, top - c.x);
   }
-  W[d.base + (d.m >> 1) + d.i] = t;
+  V[d.base + (d.m >> 1) + d.i] = t;
   if (d.i == 0) {
     const int hc = 2 * d.off + (2 << dep) - 1 + 2 * d.q;
     X[hc] = (int16_t)norm_exp(k1, Ein);
     X[hc + 1] = (int16_t)(k2 ? Ein + top : kEZero);
   }
-}
-// cells a forward step leaves alone: i in [0, 2^(d+2)) -> side and slot
-// (DCT [N/2 - 2^(d+1), N/2], DST [N/2 - 2^(d+1), N/2 - 1)); returns false
-// for the indices past the DST range
-QFX_HD bool fwd_copy(const Row& R, int dep, int i) {
-  const int H = R.N / 2, c0 = (2 << dep) + 1;
-  const int s = i >= c0;
-  const int j = i - s * c0;
-  if (s && j >= (2 << dep) - 1) return false;
-  const int slot = H - (2 << dep) + j;
-  wr(R, s)[slot] = rd(R, s)[slot];
-  return true;
 }
 
 // ----------------------------------------------------- backward step (height h)
@@ -331,7 +311,6 @@ QFX_HD bool fwd_copy(const Row& R, int dep, int i) {
 //  - lp == h - 1: item t of the class chain's combine dct(4P) (or dst(4P),
 //    lp >= 1): outputs t and 2P - t (eqs qft_5C, qft_5D; DCT item 0 also
 //    the middle output, eq qft_6).
-// Together they write every cell but the DST base at h = 1 (bwd_copy).
 struct BwdDec { int s, lp, P, off, w2; };
 QFX_HD int bwd_dec(const Row& R, int h, int w, BwdDec& d) {
   const int H = R.N / 2;
@@ -346,22 +325,21 @@ QFX_HD int bwd_dec(const Row& R, int h, int w, BwdDec& d) {
   if (d.lp == h - 1 && (d.s == 0 || d.lp >= 1)) return 2;    // chain item
   return 0;
 }
-// The item's aligned output values (a; b and, DCT chain item 0, mid too) and
-// the exponent they are aligned to; returns the kind (0: no work).
-QFX_HD int bwd_eval(const Row& R, int h, int w, BwdDec& d, Cell& a, Cell& b, Cell& mid, int& Ex) {
+QFX_HD void bwd_eval(const Row& R, int h, int w, Val& v) {
+  val_none(v);
+  BwdDec d;
   const int kind = bwd_dec(R, h, w, d);
-  if (!kind) return 0;
-  const Cell* V = rd(R, d.s);
+  if (!kind) return;
+  const Cell* V = side(R, d.s);
   const int16_t* X = exps(R, d.s);
-  b = zero();
-  mid = zero();
   if (kind == 1) {
     const int dep = d.lp - h, q = d.w2 >> h;
     const int hc = 2 * d.off + (2 << dep) - 1 + 2 * q;
     const int Ee = X[hc], Ey = X[hc + 1];
-    Ex = imax(Ee, Ey);
+    const int Ex = imax(Ee, Ey);
     const int m = 1 << h, k = d.w2 & (m - 1);
     const int base = d.off + q * m, half = base + (m >> 1);
+    Cell a;
     if (d.s == 0) {            // DCT: X(2j) = E(j); X(2j+1) = Y(j) + Y(j+1); X(m-1) = Y(m/2-1)
       if (!(k & 1)) a = rsc(V[base + (k >> 1)], Ex - Ee);
       else if (k < m - 1) a = rsc(add(V[half + (k >> 1)], V[half + (k >> 1) + 1]), Ex - Ey);
@@ -372,99 +350,86 @@ QFX_HD int bwd_eval(const Row& R, int h, int w, BwdDec& d, Cell& a, Cell& b, Cel
       else if (kk == 1) a = rsc(V[half], Ex - Ey);
       else a = rsc(add(V[half + (kk >> 1) - 1], V[half + (kk >> 1)]), Ex - Ey);
     }
-    return 1;
+    v.a = a;
+    v.k1 = key(a);
+    v.seg = m;
+    v.ex = Ex;
+    return;
   }
   const int EO = X[2 * d.off], EE = R.ch[16 * d.s + d.lp];
-  Ex = imax(EE, EO);
+  const int Ex = imax(EE, EO);
   const int t = d.w2, P = d.P, off = d.off;
   if (d.s == 0) {              // C(t) = E(t) + O(t), C(2P-t) = E(t) - O(t), C(P) = E(P)
     const Cell e = rsc(V[off + P + t], Ex - EE), o = rsc(V[off + t], Ex - EO);
-    a = add(e, o);
-    b = sub(e, o);
-    if (t == 0) mid = rsc(V[off + 2 * P], Ex - EE);
+    v.a = add(e, o);
+    v.b = sub(e, o);
+    v.k1 = imax(key(v.a), key(v.b));
+    if (t == 0) v.k1 = imax(v.k1, key(rsc(V[off + 2 * P], Ex - EE)));
   } else if (t == 0) {         // S(P) = O(P)
-    a = rsc(V[off + P - 1], Ex - EO);
+    v.a = rsc(V[off + P - 1], Ex - EO);
+    v.k1 = key(v.a);
   } else {                     // S(t) = E(t) + O(t), S(2P-t) = O(t) - E(t)
     const Cell e = rsc(V[off + P + t - 1], Ex - EE), o = rsc(V[off + t - 1], Ex - EO);
-    a = add(e, o);
-    b = sub(o, e);
+    v.a = add(e, o);
+    v.b = sub(o, e);
+    v.k1 = imax(key(v.a), key(v.b));
   }
-  return 2;
+  v.seg = P;
+  v.ex = Ex;
 }
-QFX_HD void bwd_key(const Row& R, int h, int w, int& k, int& seg) {
+QFX_HD void bwd_store(const Row& R, int h, int w, const Val& v, int bl) {
   BwdDec d;
-  Cell a, b, mid;
-  int Ex;
-  const int kind = bwd_eval(R, h, w, d, a, b, mid, Ex);
-  k = 0;
-  seg = 0;
-  if (!kind) return;
-  k = imax(key(a), imax(key(b), key(mid)));
-  seg = kind == 1 ? 1 << h : d.P;
-}
-QFX_HD void bwd_write(const Row& R, int h, int w, int bl) {
-  BwdDec d;
-  Cell a, b, mid;
-  int Ex;
-  const int kind = bwd_eval(R, h, w, d, a, b, mid, Ex);
-  Cell* W = wr(R, d.s);
+  const int kind = bwd_dec(R, h, w, d);
+  Cell* V = side(R, d.s);
   const int sh = bl - kBits;
   if (kind == 1) {
     const int m = 1 << h, k = d.w2 & (m - 1), q = d.w2 >> h;
-    W[d.off + q * m + k] = rsc(a, sh);
-    if (k == 0) exps(R, d.s)[2 * d.off + (1 << (d.lp - h)) - 1 + q] = (int16_t)norm_exp(bl, Ex);
+    V[d.off + q * m + k] = rsc(v.a, sh);
+    if (k == 0) exps(R, d.s)[2 * d.off + (1 << (d.lp - h)) - 1 + q] = (int16_t)norm_exp(bl, v.ex);
     return;
   }
   const int t = d.w2, P = d.P, off = d.off;
   if (d.s == 0) {
-    W[off + t] = rsc(a, sh);
-    W[off + 2 * P - t] = rsc(b, sh);
-    if (t == 0) {
-      W[off + P] = rsc(mid, sh);
-      R.ch[d.lp + 1] = norm_exp(bl, Ex);
+    if (t == 0) {              // E(P), read before C(2P) replaces it; only this item touches both cells
+      const Cell mid = rsc(V[off + 2 * P], v.ex - R.ch[d.lp]);
+      V[off + P] = rsc(mid, sh);
+      R.ch[d.lp + 1] = norm_exp(bl, v.ex);
     }
+    V[off + t] = rsc(v.a, sh);
+    V[off + 2 * P - t] = rsc(v.b, sh);
   } else if (t == 0) {
-    W[off + P - 1] = rsc(a, sh);
-    R.ch[16 + d.lp + 1] = norm_exp(bl, Ex);
+    V[off + P - 1] = rsc(v.a, sh);
+    R.ch[16 + d.lp + 1] = norm_exp(bl, v.ex);
   } else {
-    W[off + t - 1] = rsc(a, sh);
-    W[off + 2 * P - t - 1] = rsc(b, sh);
+    V[off + t - 1] = rsc(v.a, sh);
+    V[off + 2 * P - t - 1] = rsc(v.b, sh);
   }
-}
-// the one cell a backward step leaves alone: the DST base at h = 1
-QFX_HD void bwd_copy(const Row& R, int h) {
-  if (h == 1) R.W1[R.N / 2 - 2] = R.V1[R.N / 2 - 2];
 }
 
 // ------------------------------------------------------------- final step
 // Items k in [0, N/2): X(k) = C(k) - i S(k), X(N-k) = C(k) + i S(k) (Sec.
 // 4.1 on complex data), item 0: X(0) = C(0), X(N/2) = C(N/2); one block.
-QFX_HD int fin_eval(const Row& R, int k, Cell& lo, Cell& hi) {
+QFX_HD void fin_eval(const Row& R, int k, Val& v) {
   const int EC = R.ch[R.r - 1], ES = R.ch[16 + R.r - 1];
   const int Ex = imax(EC, ES);
   if (k == 0) {
-    lo = rsc(R.V0[0], Ex - EC);
-    hi = rsc(R.V0[R.N / 2], Ex - EC);
-    return Ex;
+    v.a = rsc(R.V0[0], Ex - EC);
+    v.b = rsc(R.V0[R.N / 2], Ex - EC);
+  } else {
+    const Cell a = rsc(R.V0[k], Ex - EC), b = rsc(R.V1[k - 1], Ex - ES);
+    v.a.x = a.x + b.y; v.a.y = a.y - b.x;
+    v.b.x = a.x - b.y; v.b.y = a.y + b.x;
   }
-  const Cell a = rsc(R.V0[k], Ex - EC), b = rsc(R.V1[k - 1], Ex - ES);
-  lo.x = a.x + b.y; lo.y = a.y - b.x;
-  hi.x = a.x - b.y; hi.y = a.y + b.x;
-  return Ex;
-}
-QFX_HD void fin_key(const Row& R, int k, int& key1, int& seg) {
-  Cell lo, hi;
-  fin_eval(R, k, lo, hi);
-  key1 = imax(key(lo), key(hi));
-  seg = R.N / 2;
+  v.k1 = imax(key(v.a), key(v.b));
+  v.k2 = 0;
+  v.seg = R.N / 2;
+  v.ex = Ex;
 }
 // out: the row's N cells; *E the row exponent (0 for a row of zeros)
-QFX_HD void fin_write(const Row& R, int k, int bl, Cell* out, int* E) {
-  Cell lo, hi;
-  const int Ex = fin_eval(R, k, lo, hi);
-  out[k] = rsc(lo, bl - kBits);
-  out[k == 0 ? R.N / 2 : R.N - k] = rsc(hi, bl - kBits);
-  if (k == 0) *E = bl ? Ex + bl - kBits : 0;
+QFX_HD void fin_store(const Row& R, int k, const Val& v, int bl, Cell* out, int* E) {
+  out[k] = rsc(v.a, bl - kBits);
+  out[k == 0 ? R.N / 2 : R.N - k] = rsc(v.b, bl - kBits);
+  if (k == 0) *E = bl ? v.ex + bl - kBits : 0;
 }
 
 // N = 2: X(0) = z(0) + z(1), X(1) = z(0) - z(1), one block.

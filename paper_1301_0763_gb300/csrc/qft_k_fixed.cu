@@ -2,15 +2,14 @@
 // launcher.
 //
 // One CTA transforms G rows at a time in shared memory (persistent grid over
-// the rows; G > 1 for rows up to 2^10).  A row is a sequence of steps --
-// fold, the forward depths of the class trees, the backward heights (tree
-// nodes and the class chain), the CDFT combine -- and every step has two
-// phases separated by a CTA barrier: each thread evaluates its items and
-// takes their block maxima (butterfly shuffles within a warp for blocks of
-// fewer than 32 items, which are aligned runs of lanes; one shared-memory
-// atomicMax per warp for larger blocks); after the barrier it evaluates them
-// again from the step's read buffer and stores them, shifted, into the other
-// buffer (so only the keys live across the barrier).
+// the rows; G > 1 for rows up to 2^9).  A row is a sequence of steps -- fold,
+// the forward depths of the class trees, the backward heights (tree nodes
+// and the class chain), the CDFT combine -- and every step has two phases
+// separated by a CTA barrier: each thread evaluates its items (values kept in
+// registers) and takes their block maxima (butterfly shuffles within a warp
+// for blocks of fewer than 32 items, which are aligned runs of lanes; one
+// shared-memory atomicMax per warp for larger blocks); after the barrier it
+// stores them, shifted, in place (every read of the step came before it).
 #include "qft_internal.h"
 #include "qft_fixed.cuh"
 
@@ -34,42 +33,40 @@ __device__ __forceinline__ int block_max(int k, int seg, int* slot, int w) {
 __device__ __forceinline__ int block_get(int k, int seg, const int* slot, int w) {
   return seg >= 32 ? slot[(w & ~(seg - 1)) >> 5] : k;
 }
-// the same value, hidden from the compiler, so that the store phase decodes its
-// items again instead of keeping the evaluation phase's registers alive
-__device__ __forceinline__ int opaque(int v) {
-  int r;
-  asm volatile("mov.b32 %0, %1;" : "=r"(r) : "r"(v));
-  return r;
-}
 
-// One step over `items` items of the CTA's rows: NI items per thread; kf(w,
-// k1, k2, seg) gives an item's block keys and block size, wf(w, max1, max2)
-// stores it.  TWO: the step has a second key (the forward products).
-template <int NT, int NI, bool TWO, class KF, class WF>
-__device__ __forceinline__ void fx_step(int* slots, int NS, int items, KF kf, WF wf) {
-  int k1[NI], k2[NI], sg[NI];
+// One step over `items` items of the CTA's rows, NI items per thread: ev(w,
+// v) evaluates an item (its values stay in registers), st(w, v, max1, max2)
+// stores it after the barrier.  TWO: the step has a second key.
+template <int NT, int NI, bool TWO, class EV, class ST>
+__device__ __forceinline__ void fx_step(int* slots, int NS, int items, EV ev, ST st) {
+  Val v[NI];
 #pragma unroll
   for (int kk = 0; kk < NI; ++kk) {
     const int w = threadIdx.x + kk * NT;
-    k1[kk] = 0;
-    k2[kk] = 0;
-    sg[kk] = 0;
-    if (w < items) kf(w, k1[kk], k2[kk], sg[kk]);
-    k1[kk] = block_max(k1[kk], sg[kk], slots, w);
-    if (TWO) k2[kk] = block_max(k2[kk], sg[kk], slots + NS, w);
+    if (w < items) ev(w, v[kk]);
+    else val_none(v[kk]);
+    v[kk].k1 = block_max(v[kk].k1, v[kk].seg, slots, w);
+    if (TWO) v[kk].k2 = block_max(v[kk].k2, v[kk].seg, slots + NS, w);
   }
   __syncthreads();
 #pragma unroll
   for (int kk = 0; kk < NI; ++kk) {
-    const int w = opaque(threadIdx.x + kk * NT);
-    if (sg[kk]) wf(w, block_get(k1[kk], sg[kk], slots, w), TWO ? block_get(k2[kk], sg[kk], slots + NS, w) : 0);
+    const int w = threadIdx.x + kk * NT;
+    if (v[kk].seg)
+      st(w, v[kk], block_get(v[kk].k1, v[kk].seg, slots, w), TWO ? block_get(v[kk].k2, v[kk].seg, slots + NS, w) : 0);
   }
 }
 
 // NT threads, K items per thread in the fold and backward steps (K NT = G N:
 // G = 2^lgG rows per CTA pass); the forward and final steps have half as many.
+// resident CTAs per SM the register allocation targets (QFX_CAP64: 64 registers a thread)
+#ifdef QFX_CAP64
+#define QFX_MIN_CTAS(nt) (1024 / (nt))
+#else
+#define QFX_MIN_CTAS(nt) 1
+#endif
 template <int NT, int K>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_fixed(const uint32_t* __restrict__ z, Cell* __restrict__ out,
+__global__ void __launch_bounds__(NT, QFX_MIN_CTAS(NT)) k_fixed(const uint32_t* __restrict__ z, Cell* __restrict__ out,
                                               int* __restrict__ eout, const Sec* __restrict__ sec, int r,
                                               int64_t batch, int lgG) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -82,69 +79,48 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fixed(const uint32_t* __restr
   const int rbytes = (int)row_bytes(N);
   const int NS = slot_count(G * N);
   int* slot_base = reinterpret_cast<int*>(sm + G * rbytes);   // [2 alternates][2 keys][NS]
+  const auto row_of = [&](int g) { return make_row(sm + g * rbytes, r, sec); };
   for (int64_t r0 = (int64_t)blockIdx.x * G; r0 < batch; r0 += (int64_t)gridDim.x * G) {
     const int gv = batch - r0 < G ? (int)(batch - r0) : G;
-    for (int i = tid; i < gv * N; i += NT) {   // stage the rows' input (coalesced)
-      const int g = i >> r;
-      const_cast<uint32_t*>(staged(sm + g * rbytes, r))[i & (N - 1)] = z[(r0 + g) * N + (i & (N - 1))];
-    }
+    for (int i = tid; i < gv * N; i += NT)     // stage the rows' input (coalesced)
+      staged(row_of(i >> r))[i & (N - 1)] = z[(r0 + (i >> r)) * N + (i & (N - 1))];
     for (int i = tid; i < 4 * NS; i += NT) slot_base[i] = 0;
     __syncthreads();
-    int cur = 0, rb = 1;   // slot set; buffer the next step reads (the fold reads the staged input)
-    const auto row_of = [&](int g) { return make_row(sm + g * rbytes, r, rb, sec); };
+    int cur = 0;
     const auto end_step = [&]() {
       int* nx = slot_base + (cur ^ 1) * 2 * NS;   // cleared for the next step while this one stores
       for (int i = tid; i < 2 * NS; i += NT) nx[i] = 0;
       __syncthreads();
       cur ^= 1;
-      rb ^= 1;
     };
-    {  // fold (Sec. 4.2 on complex data) and the class blocks
-      int* sl = slot_base + cur * 2 * NS;
-      for (int g = tid; g < gv; g += NT) fold_base(row_of(g), staged(sm + g * rbytes, r));
-      fx_step<NT, K, false>(
-          sl, NS, gv * N,
-          [&](int w, int& k1, int&, int& seg) {
-            const int g = w >> r;
-            fold_key(row_of(g), staged(sm + g * rbytes, r), w & (N - 1), k1, seg);
-          },
-          [&](int w, int m1, int) {
-            const int g = w >> r;
-            fold_write(row_of(g), staged(sm + g * rbytes, r), w & (N - 1), m1);
-          });
-      end_step();
-    }
+    for (int g = tid; g < gv; g += NT) fold_base(row_of(g), staged(row_of(g)));
+    fx_step<NT, K, false>(
+        slot_base + cur * 2 * NS, NS, gv * N,
+        [&](int w, Val& v) { const Row R = row_of(w >> r); fold_eval(R, staged(R), w & (N - 1), v); },
+        [&](int w, const Val& v, int m1, int) { fold_store(row_of(w >> r), w & (N - 1), v, m1); });
+    end_step();
     for (int dep = 0; dep <= r - 3; ++dep) {   // mirror butterflies and secant products
-      int* sl = slot_base + cur * 2 * NS;
       fx_step<NT, K / 2, true>(
-          sl, NS, gv * (N / 2),
-          [&](int w, int& k1, int& k2, int& seg) { fwd_key(row_of(w >> (r - 1)), dep, w & (N / 2 - 1), k1, k2, seg); },
-          [&](int w, int m1, int m2) { fwd_write(row_of(w >> (r - 1)), dep, w & (N / 2 - 1), m1, m2); });
-      const int cl = dep + 2;   // 2^(dep+2) copy indices per row
-      for (int i = tid; i < (gv << cl); i += NT) fwd_copy(row_of(i >> cl), dep, i & ((1 << cl) - 1));
+          slot_base + cur * 2 * NS, NS, gv * (N / 2),
+          [&](int w, Val& v) { fwd_eval(row_of(w >> (r - 1)), dep, w & (N / 2 - 1), v); },
+          [&](int w, const Val& v, int m1, int m2) { fwd_store(row_of(w >> (r - 1)), dep, w & (N / 2 - 1), v, m1, m2); });
       end_step();
     }
     for (int h = 1; h <= r - 1; ++h) {         // node outputs and the class chain
-      int* sl = slot_base + cur * 2 * NS;
       fx_step<NT, K, false>(
-          sl, NS, gv * N,
-          [&](int w, int& k1, int&, int& seg) { bwd_key(row_of(w >> r), h, w & (N - 1), k1, seg); },
-          [&](int w, int m1, int) { bwd_write(row_of(w >> r), h, w & (N - 1), m1); });
-      if (h == 1)
-        for (int g = tid; g < gv; g += NT) bwd_copy(row_of(g), h);
+          slot_base + cur * 2 * NS, NS, gv * N,
+          [&](int w, Val& v) { bwd_eval(row_of(w >> r), h, w & (N - 1), v); },
+          [&](int w, const Val& v, int m1, int) { bwd_store(row_of(w >> r), h, w & (N - 1), v, m1); });
       end_step();
     }
-    {  // CDFT combine, one block per row: the row exponents
-      int* sl = slot_base + cur * 2 * NS;
-      fx_step<NT, K / 2, false>(
-          sl, NS, gv * (N / 2),
-          [&](int w, int& k1, int&, int& seg) { fin_key(row_of(w >> (r - 1)), w & (N / 2 - 1), k1, seg); },
-          [&](int w, int m1, int) {
-            const int g = w >> (r - 1);
-            fin_write(row_of(g), w & (N / 2 - 1), m1, out + (r0 + g) * N, eout + r0 + g);
-          });
-      end_step();   // the next pass restages buffer 1
-    }
+    fx_step<NT, K / 2, false>(                   // CDFT combine, one block per row
+        slot_base + cur * 2 * NS, NS, gv * (N / 2),
+        [&](int w, Val& v) { fin_eval(row_of(w >> (r - 1)), w & (N / 2 - 1), v); },
+        [&](int w, const Val& v, int m1, int) {
+          const int g = w >> (r - 1);
+          fin_store(row_of(g), w & (N / 2 - 1), v, m1, out + (r0 + g) * N, eout + r0 + g);
+        });
+    end_step();   // the next pass restages the rows
   }
 }
 
@@ -152,14 +128,15 @@ struct FxCfg {
   int nt, k, lgG;
 };
 // threads, items per thread and rows per CTA pass for rows of length 2^r:
-// about 48 KB of shared memory per CTA up to 2^11 (four CTAs of 256 threads
-// per SM), one row of 2^12 (512 threads) or 2^13 (1024 threads)
+// 256 threads and up to 1024 items (at most 48 KB of rows) per CTA up to 2^10,
+// then one row per CTA with 4 items per thread (8 at 2^13)
 inline FxCfg fx_cfg(int r) {
-  if (r <= 1) return {256, 8, 0};
-  if (r == 12) return {512, 8, 0};
+  if (r <= 1) return {256, 4, 0};
+  if (r == 11) return {512, 4, 0};
+  if (r == 12) return {1024, 4, 0};
   if (r == 13) return {1024, 8, 0};
   const int N = 1 << r;
-  int G = 2048 >> r;
+  int G = 1024 >> r;
   while (G > 1 && (size_t)G * row_bytes(N) > 49152) G >>= 1;
   int lg = 0;
   while ((1 << lg) < G) ++lg;
@@ -212,9 +189,9 @@ int qft_launch_fixed(qft_plan p, const void* in, void* out, int32_t* exps, cudaS
   qft_time_begin(p, st, QFT_KERNEL_ROWS);
   if (c.nt == 256 && c.k == 2) e = launch_k<256, 2>(p, c, z, o, eo, st);
   else if (c.nt == 256 && c.k == 4) e = launch_k<256, 4>(p, c, z, o, eo, st);
-  else if (c.nt == 256 && c.k == 8) e = launch_k<256, 8>(p, c, z, o, eo, st);
-  else if (c.nt == 512) e = launch_k<512, 8>(p, c, z, o, eo, st);
-  else if (c.nt == 1024) e = launch_k<1024, 8>(p, c, z, o, eo, st);
+  else if (c.nt == 512 && c.k == 4) e = launch_k<512, 4>(p, c, z, o, eo, st);
+  else if (c.nt == 1024 && c.k == 4) e = launch_k<1024, 4>(p, c, z, o, eo, st);
+  else if (c.nt == 1024 && c.k == 8) e = launch_k<1024, 8>(p, c, z, o, eo, st);
   else return QFT_ERR_INVALID_N;
   qft_time_end(p, st);
   return qft_set_cuda(p, e);

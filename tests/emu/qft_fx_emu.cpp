@@ -43,51 +43,46 @@ bool reduce(const std::vector<int>& seg, const std::vector<int>& k1, const std::
   return true;
 }
 
+// the kernel's two phases of a step: evaluate every item, reduce, store every item
+template <class EV, class ST>
+bool step(int items, EV ev, ST st) {
+  std::vector<Val> v(items);
+  std::vector<int> sg(items), k1(items), k2(items), m1, m2;
+  for (int w = 0; w < items; ++w) {
+    ev(w, v[w]);
+    sg[w] = v[w].seg;
+    k1[w] = v[w].k1;
+    k2[w] = v[w].k2;
+  }
+  if (!reduce(sg, k1, k2, m1, m2)) return false;
+  for (int w = 0; w < items; ++w)
+    if (sg[w]) st(w, v[w], m1[w], m2[w]);
+  return true;
+}
+
 int row(int r, const uint32_t* z, Cell* out, int* E, const std::vector<Sec>& sec) {
   const int N = 1 << r, H = N / 2;
   if (N == 2) { row_n2(z, out, E); return 0; }
   // the row's shared-memory image; garbage everywhere, so that a read before a write shows
   std::vector<unsigned char> mem(row_bytes(N), 0x55);
-  unsigned char* base = mem.data();
-  uint32_t* zs = const_cast<uint32_t*>(staged(base, r));
+  const Row R = make_row(mem.data(), r, sec.data());
+  uint32_t* zs = staged(R);
   for (int n = 0; n < N; ++n) zs[n] = z[n];
-  int rb = 1;
-  std::vector<int> k1, k2, sg, m1, m2;
-  const auto keys = [&](int items) { k1.assign(items, 0); k2.assign(items, 0); sg.assign(items, 0); };
-  {
-    Row R = make_row(base, r, rb, sec.data());
-    keys(N);
-    fold_base(R, zs);
-    for (int w = 0; w < N; ++w) fold_key(R, zs, w, k1[w], sg[w]);
-    if (!reduce(sg, k1, k2, m1, m2)) return -2;
-    for (int w = 0; w < N; ++w) if (sg[w]) fold_write(R, zs, w, m1[w]);
-    rb ^= 1;
-  }
-  for (int dep = 0; dep <= r - 3; ++dep) {
-    Row R = make_row(base, r, rb, sec.data());
-    keys(H);
-    for (int w = 0; w < H; ++w) fwd_key(R, dep, w, k1[w], k2[w], sg[w]);
-    if (!reduce(sg, k1, k2, m1, m2)) return -3;
-    for (int w = 0; w < H; ++w) if (sg[w]) fwd_write(R, dep, w, m1[w], m2[w]);
-    for (int i = 0; i < (4 << dep); ++i) fwd_copy(R, dep, i);
-    rb ^= 1;
-  }
-  for (int h = 1; h <= r - 1; ++h) {
-    Row R = make_row(base, r, rb, sec.data());
-    keys(N);
-    for (int w = 0; w < N; ++w) bwd_key(R, h, w, k1[w], sg[w]);
-    if (!reduce(sg, k1, k2, m1, m2)) return -4;
-    for (int w = 0; w < N; ++w) if (sg[w]) bwd_write(R, h, w, m1[w]);
-    bwd_copy(R, h);
-    rb ^= 1;
-  }
-  {
-    Row R = make_row(base, r, rb, sec.data());
-    keys(H);
-    for (int w = 0; w < H; ++w) fin_key(R, w, k1[w], sg[w]);
-    if (!reduce(sg, k1, k2, m1, m2)) return -5;
-    for (int w = 0; w < H; ++w) fin_write(R, w, m1[w], out, E);
-  }
+  fold_base(R, zs);
+  if (!step(N, [&](int w, Val& v) { fold_eval(R, zs, w, v); },
+            [&](int w, const Val& v, int m1, int) { fold_store(R, w, v, m1); }))
+    return -2;
+  for (int dep = 0; dep <= r - 3; ++dep)
+    if (!step(H, [&](int w, Val& v) { fwd_eval(R, dep, w, v); },
+              [&](int w, const Val& v, int m1, int m2) { fwd_store(R, dep, w, v, m1, m2); }))
+      return -3;
+  for (int h = 1; h <= r - 1; ++h)
+    if (!step(N, [&](int w, Val& v) { bwd_eval(R, h, w, v); },
+              [&](int w, const Val& v, int m1, int) { bwd_store(R, h, w, v, m1); }))
+      return -4;
+  if (!step(H, [&](int w, Val& v) { fin_eval(R, w, v); },
+            [&](int w, const Val& v, int m1, int) { fin_store(R, w, v, m1, out, E); }))
+    return -5;
   return 0;
 }
 
