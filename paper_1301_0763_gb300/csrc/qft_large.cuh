@@ -41,6 +41,13 @@ namespace {
 
 constexpr int kLargeNT = 256;   // threads of the GLOBAL / SLICE kernels
 constexpr int kLargeTPT = 4;    // tasks per thread per CTA in those kernels
+// resident CTAs per SM the GLOBAL and SLICE kernels' register allocation targets
+#ifndef QFT_GLOBAL_MINB
+#define QFT_GLOBAL_MINB 2
+#endif
+#ifndef QFT_SLICE_MINB
+#define QFT_SLICE_MINB 2
+#endif
 
 __device__ __forceinline__ Eng large_eng(const LargeArgs& a, int copy, int64_t row) {
   Eng e;
@@ -61,7 +68,7 @@ __device__ __forceinline__ Eng large_eng(const LargeArgs& a, int copy, int64_t r
 // GLOBAL phase (F1, DIF, FINAL): blockIdx.y = row within the chunk, blockIdx.x
 // = block of kLargeNT * kLargeTPT consecutive tasks of that row's phase.
 template <class FAC, int L1, bool COMP>
-__global__ void __launch_bounds__(kLargeNT, 2) k_large_global(LargeArgs a, int phase, FAC fac) {
+__global__ void __launch_bounds__(kLargeNT, QFT_GLOBAL_MINB) k_large_global(LargeArgs a, int phase, FAC fac) {
   const QftLargePlan* P = a.plan;
   const QftLargePhase ph = P->phases[phase];
   const int64_t row = blockIdx.y;
@@ -94,7 +101,7 @@ __host__ __device__ inline size_t node_smem_bytes(int NB, int comp = 0) {
 #ifdef QFT_NODE_TU
 // SLICE phase above the node depth: reads copy sg.pad[0], writes copy sg.pad[1].
 template <bool COMP>
-__global__ void __launch_bounds__(kLargeNT, 2) k_large_slice(LargeArgs a, int phase) {
+__global__ void __launch_bounds__(kLargeNT, QFT_SLICE_MINB) k_large_slice(LargeArgs a, int phase) {
   const QftLargePlan* P = a.plan;
   const QftLargePhase ph = P->phases[phase];
   const int64_t row = blockIdx.y;
