@@ -450,62 +450,91 @@ def dst0(d: torch.Tensor) -> torch.Tensor:
 _host_streams: dict = {}
 
 
-def fft_host(x: torch.Tensor, out: torch.Tensor | None = None, chunk_bytes: int = 256 << 20,
-             device=None) -> torch.Tensor:
+def fft_host(x, out=None, chunk_bytes: int = 256 << 20, device=None):
     """Forward DFT of complex64 rows [..., N] held in pinned host memory, written
-    to pinned host memory (``out``, allocated if None).  The rows move in chunks
-    of about ``chunk_bytes``: the copy of chunk i+1 to the device, the transform
-    of chunk i and the copy of chunk i-1 back run on three streams and overlap.
-    Returns ``out`` once the current stream has been ordered after the last copy
-    (synchronise before reading it on the host)."""
-    if x.is_cuda or not x.is_pinned():
-        raise ValueError("fft_host takes a pinned host tensor")
-    assert x.dtype == torch.complex64
-    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-    N = x.shape[-1]
-    rows = x.numel() // N if N else 0
+    to pinned host memory (``out``, allocated if None).  ``x`` may also be a
+    list of such tensors (each with its own N; ``out`` then a list or None):
+    one pipeline runs through all of them.  The rows move in chunks of about
+    ``chunk_bytes`` through three device buffer pairs: the copy of chunk i+1 to
+    the device, the transform of chunk i and the copy of chunk i-1 back run on
+    three streams and overlap, and a buffer is refilled as soon as the transform
+    that read it is done.  Returns ``out`` once the current stream has been
+    ordered after the last copy (synchronise before reading it on the host)."""
+    xs = list(x) if isinstance(x, (list, tuple)) else [x]
     if out is None:
-        out = torch.empty(x.shape, dtype=x.dtype).pin_memory()
-    if rows == 0:
-        return out
-    xv, ov = x.view(rows, N), out.view(rows, N)
-    chunk = max(1, min(rows, chunk_bytes // (8 * N)))
+        outs = [None] * len(xs)
+    else:
+        outs = list(out) if isinstance(out, (list, tuple)) else [out]
+    if len(outs) != len(xs):
+        raise ValueError("fft_host: one output per input")
+    for i, t in enumerate(xs):
+        if t.is_cuda or not t.is_pinned():
+            raise ValueError("fft_host takes pinned host tensors")
+        if t.dtype != torch.complex64:
+            raise TypeError("fft_host takes complex64 tensors")
+        if not t.is_contiguous():
+            raise ValueError("fft_host takes contiguous tensors")
+        if outs[i] is None:
+            outs[i] = torch.empty(t.shape, dtype=t.dtype).pin_memory()
+        elif outs[i].shape != t.shape or outs[i].dtype != t.dtype or outs[i].is_cuda:
+            raise ValueError("fft_host: out must be a host tensor of the input's shape and dtype")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    # the chunks of every input, in order: (input rows, output rows, N)
+    work = []
+    for t, o in zip(xs, outs):
+        N = t.shape[-1]
+        rows = t.numel() // N if N else 0
+        if rows == 0:
+            continue
+        xv, ov = t.view(rows, N), o.view(rows, N)
+        chunk = max(1, min(rows, chunk_bytes // (8 * N)))
+        for r0 in range(0, rows, chunk):
+            n = min(chunk, rows - r0)
+            work.append((xv[r0:r0 + n], ov[r0:r0 + n], N))
+    if not work:
+        return outs if isinstance(x, (list, tuple)) else outs[0]
     key = dev.index
     if key not in _host_streams:
         _host_streams[key] = tuple(torch.cuda.Stream(device=dev) for _ in range(3))
     s_in, s_cmp, s_out = _host_streams[key]
     nbuf = 3
-    din = [torch.empty(chunk, N, dtype=torch.complex64, device=dev) for _ in range(nbuf)]
-    dout = [torch.empty(chunk, N, dtype=torch.complex64, device=dev) for _ in range(nbuf)]
-    ev_in = [torch.cuda.Event() for _ in range(nbuf)]
-    ev_cmp = [torch.cuda.Event() for _ in range(nbuf)]
-    ev_free = [None] * nbuf
+    cells = max(a.numel() for a, _, _ in work)
+    din = [torch.empty(cells, dtype=torch.complex64, device=dev) for _ in range(nbuf)]
+    dout = [torch.empty(cells, dtype=torch.complex64, device=dev) for _ in range(nbuf)]
+    ev_read = [None] * nbuf    # the transform that read din[b] is done
+    ev_sent = [None] * nbuf    # the copy out of dout[b] is done
     cur = torch.cuda.current_stream(dev)
-    for s in (s_in, s_cmp, s_out):
-        s.wait_stream(cur)
-    for i, r0 in enumerate(range(0, rows, chunk)):
+    s_in.wait_stream(cur)
+    for i, (a, o, N) in enumerate(work):
         b = i % nbuf
-        n = min(chunk, rows - r0)
+        n = a.shape[0]
+        di = din[b][: n * N].view(n, N)
+        do = dout[b][: n * N].view(n, N)
         with torch.cuda.stream(s_in):
-            if ev_free[b] is not None:
-                s_in.wait_event(ev_free[b])          # buffer b's previous chunk has left the device
-            din[b][:n].copy_(xv[r0:r0 + n], non_blocking=True)
-            ev_in[b].record(s_in)
-        s_cmp.wait_event(ev_in[b])
-        get_plan(N, n, KIND_C2C, DTYPE_F32, dev).execute(OP_FORWARD, din[b][:n], dout[b][:n], s_cmp)
-        ev_cmp[b].record(s_cmp)
+            if ev_read[b] is not None:
+                s_in.wait_event(ev_read[b])
+            di.copy_(a, non_blocking=True)
+            e_in = torch.cuda.Event()
+            e_in.record(s_in)
+        s_cmp.wait_event(e_in)
+        if ev_sent[b] is not None:
+            s_cmp.wait_event(ev_sent[b])
+        get_plan(N, n, KIND_C2C, DTYPE_F32, dev).execute(OP_FORWARD, di, do, s_cmp)
+        e_c = torch.cuda.Event()
+        e_c.record(s_cmp)
+        ev_read[b] = e_c
         with torch.cuda.stream(s_out):
-            s_out.wait_event(ev_cmp[b])
-            ov[r0:r0 + n].copy_(dout[b][:n], non_blocking=True)
-            e = torch.cuda.Event()
-            e.record(s_out)
-            ev_free[b] = e
+            s_out.wait_event(e_c)
+            o.copy_(do, non_blocking=True)
+            e_o = torch.cuda.Event()
+            e_o.record(s_out)
+            ev_sent[b] = e_o
     cur.wait_stream(s_out)
     for t in din + dout:
         t.record_stream(s_in)
         t.record_stream(s_cmp)
         t.record_stream(s_out)
-    return out
+    return outs if isinstance(x, (list, tuple)) else outs[0]
 
 
 def fft(x: torch.Tensor) -> torch.Tensor:

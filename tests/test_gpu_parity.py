@@ -523,6 +523,22 @@ def test_fft_host_pipelined_matches_device_fft(q):
     assert bits_equal(out.numpy(), ref)
 
 
+def test_fft_host_list_pipeline(q):
+    """One fft_host call over several pinned host tensors of different lengths
+    (row kernel and large-row path, several chunks each, buffers reused across
+    the sizes) gives each one the bits of its device transform."""
+    sizes = [(1024, 40), (1 << 16, 5), (256, 300)]
+    hosts, refs = [], []
+    for k, (N, rows) in enumerate(sizes):
+        z = inputs.normal_complex(rows, N, seed=95 + k)
+        hosts.append(torch.from_numpy(z).pin_memory())
+        refs.append(q.fft(gpu(z)).cpu().numpy())
+    outs = q.fft_host(hosts, chunk_bytes=3 * (1 << 16) * 8)
+    torch.cuda.synchronize()
+    for o, ref in zip(outs, refs):
+        assert bits_equal(o.numpy(), ref)
+
+
 # ------------------------------------------------- bounded waits (failure path)
 @pytest.mark.parametrize("lg", [12, 16])
 def test_bounded_wait_times_out_and_recovers(q, lg):
