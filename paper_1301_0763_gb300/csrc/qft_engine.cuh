@@ -188,6 +188,16 @@ struct Eng {
 QFT_HD qc* side_ptr(const Eng& e, int s) { return s ? e.side1 : e.side0; }
 QFT_HD qc* lo_ptr(const Eng& e, int s) { return s ? e.lo1 : e.lo0; }
 
+// L2 prefetch of one cell of a scratch row in global memory (a hint; the
+// large-row kernels give it the cells of the task a thread runs next)
+QFT_HD void prefetch_cell(const qc* p) {
+#if defined(__CUDA_ARCH__)
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+#else
+  (void)p;
+#endif
+}
+
 // ------------------------------------------------- forward mirror levels
 // L levels of the forward phase on registers v[t], t in [0, 2^L).  Register t
 // holds node slot t*H + lo (H = 2^(nb-L)) of a node of 2^nb cells.  Level l
@@ -477,6 +487,23 @@ QFT_HD void task_dif_c(const Eng& e, int j, int D, int tau) {
   }
 }
 
+// The cells task_dif / task_dif_c(tau) reads (and their lo parts if `lo`),
+// prefetched into L2.
+template <int L, int SIDE>
+QFT_HD void task_dif_prefetch(const Eng& e, int j, int D, int tau, bool lo) {
+  const int nb = cls_bits(e.r, j) - D;
+  const int h = nb - L;
+  const int base = cls_off(e.r, j) + ((tau >> h) << nb) + (tau & ((1 << h) - 1));
+  const qc* A = side_ptr(e, SIDE);
+  const qc* Al = lo_ptr(e, SIDE);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) {
+    const int pi = qft_pidx(base + (t << h));
+    prefetch_cell(A + pi);
+    if (lo) prefetch_cell(Al + pi);
+  }
+}
+
 template <int L, int SIDE>
 QFT_HD void task_leaf_c(const Eng& e, int j, int q) {
   qc* A = side_ptr(e, SIDE);
@@ -557,6 +584,26 @@ QFT_HD void task_slice_read(const Eng& e, int j, int D, int tau, SliceRegs& s) {
   bwd_chunk<L, SIDE>(w, s.h, hv);
 #pragma unroll
   for (int t = 0; t < (1 << L); ++t) s.w[t] = w[t];
+}
+
+// The cells task_slice_read / task_slice_read_c(tau) reads from its node's
+// descendants (not the halo: a neighbour lane's cells), and their lo parts if
+// `lo`, prefetched into L2.
+template <int L, int SIDE>
+QFT_HD void task_slice_prefetch(const Eng& e, int j, int D, int tau, bool lo) {
+  const int b = cls_bits(e.r, j);
+  const int sb = b - D;
+  const int S = 1 << sb;
+  const int nb = b - (D - L);
+  const int nbase = cls_off(e.r, j) + ((tau >> sb) << nb) + (tau & (S - 1));
+  const qc* A = side_ptr(e, SIDE);
+  const qc* Al = lo_ptr(e, SIDE);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) {
+    const int pi = qft_pidx(nbase + t * S);
+    prefetch_cell(A + pi);
+    if (lo) prefetch_cell(Al + pi);
+  }
 }
 
 template <int L, int SIDE>
@@ -855,16 +902,24 @@ QFT_HD void run_plain_task(int LF, const QftSeg& sg, const Eng& e, const IO& io,
 // l = first, first + step, ... < end (task index g*count + l).  The switch on
 // the task kind is taken once per segment; the loop body is specialised, so
 // the class geometry is loop-invariant.
-template <int L1, class IO, bool COMP = false>
+// PF (large-row kernels, scratch in global memory): each DIF task first
+// prefetches the cells of the thread's next task into L2.
+template <int L1, class IO, bool COMP = false, bool PF = false>
 QFT_HD void run_plain_segment(int LF, const QftSeg& sg, const Eng& e, const IO& io, int first, int end,
                               int step, int g) {
   const int off = g * sg.count;
 #define QFT_LOOP(CALL) for (int l = first; l < end; l += step) { const int loc = off + l; (void)loc; CALL; }
+#define QFT_LOOP_PF(LL, SD, LO, CALL)                                                  \
+  for (int l = first; l < end; l += step) {                                           \
+    const int loc = off + l;                                                          \
+    if (PF && l + step < end) task_dif_prefetch<LL, SD>(e, sg.cls, sg.D, loc + step, LO); \
+    CALL;                                                                             \
+  }
   if (COMP && sg.pad[2]) {
     switch (sg.type) {
     case QFT_SEG_F1_BIG: QFT_LOOP(task_f1_big_c<L1>(e, io, sg.cls, loc)) return;
     case QFT_SEG_DIF:
-#define QFT_DIFC_CASE(LL) case LL: if (sg.side) { QFT_LOOP((task_dif_c<LL, 1>(e, sg.cls, sg.D, loc))) } else { QFT_LOOP((task_dif_c<LL, 0>(e, sg.cls, sg.D, loc))) } return;
+#define QFT_DIFC_CASE(LL) case LL: if (sg.side) { QFT_LOOP_PF(LL, 1, true, (task_dif_c<LL, 1>(e, sg.cls, sg.D, loc))) } else { QFT_LOOP_PF(LL, 0, true, (task_dif_c<LL, 0>(e, sg.cls, sg.D, loc))) } return;
       switch (sg.L) { QFT_DIFC_CASE(1) QFT_DIFC_CASE(2) QFT_DIFC_CASE(3) default: return; }
 #undef QFT_DIFC_CASE
     case QFT_SEG_LEAF:
@@ -888,7 +943,7 @@ QFT_HD void run_plain_segment(int LF, const QftSeg& sg, const Eng& e, const IO& 
     break;
   case QFT_SEG_F1_BASE: QFT_LOOP(task_f1_base(e, io)) break;
   case QFT_SEG_DIF:
-#define QFT_DIF_CASE(LL) case LL: if (sg.side) { QFT_LOOP((task_dif<LL, 1>(e, sg.cls, sg.D, loc))) } else { QFT_LOOP((task_dif<LL, 0>(e, sg.cls, sg.D, loc))) } break;
+#define QFT_DIF_CASE(LL) case LL: if (sg.side) { QFT_LOOP_PF(LL, 1, false, (task_dif<LL, 1>(e, sg.cls, sg.D, loc))) } else { QFT_LOOP_PF(LL, 0, false, (task_dif<LL, 0>(e, sg.cls, sg.D, loc))) } break;
     switch (sg.L) { QFT_DIF_CASE(1) QFT_DIF_CASE(2) QFT_DIF_CASE(3) QFT_DIF_CASE(4) default: break; }
 #undef QFT_DIF_CASE
     break;
@@ -910,6 +965,7 @@ QFT_HD void run_plain_segment(int LF, const QftSeg& sg, const Eng& e, const IO& 
   default: break;
   }
 #undef QFT_LOOP
+#undef QFT_LOOP_PF
 }
 
 QFT_HD void run_slice_read(const QftSeg& sg, const Eng& e, int loc, SliceRegs& s) {
@@ -922,6 +978,15 @@ QFT_HD void run_slice_read(const QftSeg& sg, const Eng& e, int loc, SliceRegs& s
     default: break;
   }
 #undef QFT_SR_CASE
+}
+
+QFT_HD void run_slice_prefetch(const QftSeg& sg, const Eng& e, int loc, bool lo) {
+  switch (sg.L) {
+  case 1: if (sg.side) task_slice_prefetch<1, 1>(e, sg.cls, sg.D, loc, lo); else task_slice_prefetch<1, 0>(e, sg.cls, sg.D, loc, lo); break;
+  case 2: if (sg.side) task_slice_prefetch<2, 1>(e, sg.cls, sg.D, loc, lo); else task_slice_prefetch<2, 0>(e, sg.cls, sg.D, loc, lo); break;
+  case 3: if (sg.side) task_slice_prefetch<3, 1>(e, sg.cls, sg.D, loc, lo); else task_slice_prefetch<3, 0>(e, sg.cls, sg.D, loc, lo); break;
+  default: break;
+  }
 }
 
 // MAXL: the largest L the caller's plans give compensated SLICE segments (the

@@ -48,6 +48,10 @@ constexpr int kLargeTPT = 4;    // tasks per thread per CTA in those kernels
 #ifndef QFT_SLICE_MINB
 #define QFT_SLICE_MINB 2
 #endif
+// 1: the GLOBAL (DIF tasks) and SLICE kernels prefetch each thread's next task into L2
+#ifndef QFT_LARGE_PF
+#define QFT_LARGE_PF 1
+#endif
 
 __device__ __forceinline__ Eng large_eng(const LargeArgs& a, int copy, int64_t row) {
   Eng e;
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(kLargeNT, QFT_GLOBAL_MINB) k_large_global(Larg
     if (first < 0) first += ((-first + kLargeNT - 1) / kLargeNT) * kLargeNT;
     int end = T1 - sg.begin;
     if (end > sg.count) end = sg.count;
-    run_plain_segment<L1, decltype(io), COMP>(P->LF, sg, e, io, first, end, kLargeNT, 0);
+    run_plain_segment<L1, decltype(io), COMP, QFT_LARGE_PF>(P->LF, sg, e, io, first, end, kLargeNT, 0);
   }
 }
 
@@ -115,6 +119,10 @@ __global__ void __launch_bounds__(kLargeNT, QFT_SLICE_MINB) k_large_slice(LargeA
     const QftSeg sg = P->segs[sgi];
     const Eng es = large_eng(a, sg.pad[0], row);
     const Eng ed = large_eng(a, sg.pad[1], row);
+    // the cells of this thread's next task go to L2 while this one is read
+    const int taun = tau + kLargeNT;
+    if (QFT_LARGE_PF && k + 1 < kLargeTPT && taun < ph.ntasks && taun < sg.begin + sg.count)
+      run_slice_prefetch(sg, es, taun - sg.begin, COMP && sg.pad[2]);
     if (COMP && sg.pad[2]) {
       SliceRegsC s;
       run_slice_read_c(sg, es, tau - sg.begin, s);
