@@ -450,6 +450,29 @@ def dst0(d: torch.Tensor) -> torch.Tensor:
 _host_streams: dict = {}
 
 
+def _host_state(dev: torch.device, cells: int) -> dict:
+    """The streams, device buffer pairs and events fft_host keeps per device
+    (reused by every call; grown, after the streams drain, when a call needs
+    larger chunks)."""
+    st = _host_streams.get(dev.index)
+    if st is None:
+        st = {"streams": tuple(torch.cuda.Stream(device=dev) for _ in range(3)), "cells": 0, "next": 0}
+        _host_streams[dev.index] = st
+    if st["cells"] < cells:
+        for s_ in st["streams"]:
+            s_.synchronize()
+        nbuf = 3
+        st["din"] = [torch.empty(cells, dtype=torch.complex64, device=dev) for _ in range(nbuf)]
+        st["dout"] = [torch.empty(cells, dtype=torch.complex64, device=dev) for _ in range(nbuf)]
+        st["ev_read"] = [torch.cuda.Event() for _ in range(nbuf)]
+        st["ev_sent"] = [torch.cuda.Event() for _ in range(nbuf)]
+        for e in st["ev_read"] + st["ev_sent"]:
+            e.record(st["streams"][0])
+        st["cells"] = cells
+        st["next"] = 0
+    return st
+
+
 def fft_host(x, out=None, chunk_bytes: int = 256 << 20, device=None):
     """Forward DFT of complex64 rows [..., N] held in pinned host memory, written
     to pinned host memory (``out``, allocated if None).  ``x`` may also be a
@@ -458,8 +481,9 @@ def fft_host(x, out=None, chunk_bytes: int = 256 << 20, device=None):
     ``chunk_bytes`` through three device buffer pairs: the copy of chunk i+1 to
     the device, the transform of chunk i and the copy of chunk i-1 back run on
     three streams and overlap, and a buffer is refilled as soon as the transform
-    that read it is done.  Returns ``out`` once the current stream has been
-    ordered after the last copy (synchronise before reading it on the host)."""
+    that read it is done.  The buffers, streams and events persist per device
+    across calls.  Returns ``out`` once the current stream has been ordered
+    after the last copy (synchronise before reading it on the host)."""
     xs = list(x) if isinstance(x, (list, tuple)) else [x]
     if out is None:
         outs = [None] * len(xs)
@@ -493,47 +517,32 @@ def fft_host(x, out=None, chunk_bytes: int = 256 << 20, device=None):
             work.append((xv[r0:r0 + n], ov[r0:r0 + n], N))
     if not work:
         return outs if isinstance(x, (list, tuple)) else outs[0]
-    key = dev.index
-    if key not in _host_streams:
-        _host_streams[key] = tuple(torch.cuda.Stream(device=dev) for _ in range(3))
-    s_in, s_cmp, s_out = _host_streams[key]
-    nbuf = 3
-    cells = max(a.numel() for a, _, _ in work)
-    din = [torch.empty(cells, dtype=torch.complex64, device=dev) for _ in range(nbuf)]
-    dout = [torch.empty(cells, dtype=torch.complex64, device=dev) for _ in range(nbuf)]
-    ev_read = [None] * nbuf    # the transform that read din[b] is done
-    ev_sent = [None] * nbuf    # the copy out of dout[b] is done
+    st = _host_state(dev, max(a.numel() for a, _, _ in work))
+    s_in, s_cmp, s_out = st["streams"]
+    din, dout, ev_read, ev_sent = st["din"], st["dout"], st["ev_read"], st["ev_sent"]
+    nbuf = len(din)
     cur = torch.cuda.current_stream(dev)
     s_in.wait_stream(cur)
     for i, (a, o, N) in enumerate(work):
-        b = i % nbuf
+        b = st["next"]
+        st["next"] = (b + 1) % nbuf
         n = a.shape[0]
         di = din[b][: n * N].view(n, N)
         do = dout[b][: n * N].view(n, N)
         with torch.cuda.stream(s_in):
-            if ev_read[b] is not None:
-                s_in.wait_event(ev_read[b])
+            s_in.wait_event(ev_read[b])             # the transform that last read din[b] is done
             di.copy_(a, non_blocking=True)
             e_in = torch.cuda.Event()
             e_in.record(s_in)
         s_cmp.wait_event(e_in)
-        if ev_sent[b] is not None:
-            s_cmp.wait_event(ev_sent[b])
+        s_cmp.wait_event(ev_sent[b])                # the copy that last read dout[b] is done
         get_plan(N, n, KIND_C2C, DTYPE_F32, dev).execute(OP_FORWARD, di, do, s_cmp)
-        e_c = torch.cuda.Event()
-        e_c.record(s_cmp)
-        ev_read[b] = e_c
+        ev_read[b].record(s_cmp)
         with torch.cuda.stream(s_out):
-            s_out.wait_event(e_c)
+            s_out.wait_event(ev_read[b])
             o.copy_(do, non_blocking=True)
-            e_o = torch.cuda.Event()
-            e_o.record(s_out)
-            ev_sent[b] = e_o
+            ev_sent[b].record(s_out)
     cur.wait_stream(s_out)
-    for t in din + dout:
-        t.record_stream(s_in)
-        t.record_stream(s_cmp)
-        t.record_stream(s_out)
     return outs if isinstance(x, (list, tuple)) else outs[0]
 
 
