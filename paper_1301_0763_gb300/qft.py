@@ -473,7 +473,7 @@ def _host_state(dev: torch.device, cells: int) -> dict:
     return st
 
 
-def fft_host(x, out=None, chunk_bytes: int = 256 << 20, device=None):
+def fft_host(x, out=None, chunk_bytes: int = 512 << 20, device=None):
     """Forward DFT of complex64 rows [..., N] held in pinned host memory, written
     to pinned host memory (``out``, allocated if None).  ``x`` may also be a
     list of such tensors (each with its own N; ``out`` then a list or None):
