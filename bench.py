@@ -689,6 +689,28 @@ def run_extras(args, dev, stream, torch, qft, orc, tune, peak):
     return ex
 
 
+def run_fixed_only(args):
+    """The fixed-point variant alone at one length (a profiling run): `warmup`
+    untimed and `steps` timed executes over 2^26 Q15 samples; one JSON line."""
+    import torch
+    from paper_1301_0763_gb300 import build, qft
+    build.build()
+    qft.load_library()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    N = 1 << args.fixed
+    rows = (1 << 26) // N
+    gen = torch.Generator(device=dev).manual_seed(13010763 + 8)
+    zq = torch.randint(-32768, 32768, (rows, N, 2), device=dev, dtype=torch.int32, generator=gen).to(torch.int16)
+    X = torch.empty((rows, N, 2), dtype=torch.int32, device=dev)
+    E = torch.empty(rows, dtype=torch.int32, device=dev)
+    p = qft.Plan(N, rows, dtype=qft.DTYPE_I16)
+    stream = torch.cuda.current_stream()
+    ms = _time(lambda: p.execute_fixed(zq, X, E), torch, stream, reps=max(1, args.steps), warm=max(1, args.warmup))
+    print(json.dumps({"workload": f"fixed-point forward, N = 2^{args.fixed}, {rows} rows", "ms": round(ms, 4),
+                      "gbs": round(rows * (12 * N + 4) / (ms * 1e-3) / 1e9, 1), "launches": args.steps + args.warmup}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -704,6 +726,8 @@ def main():
     ap.add_argument("--sizes", default="", help="comma-separated log2 N subset (profiling runs)")
     ap.add_argument("--elems-log2", type=int, default=28,
                     help="complex elements per size (28 = the benchmark; smaller for profiler captures)")
+    ap.add_argument("--fixed", type=int, default=0, metavar="LG",
+                    help="profiling runs: time only the fixed-point variant at N = 2^LG (2^26 samples)")
     args = ap.parse_args()
     global SIZES_OVERRIDE, ELEMS
     ELEMS = 1 << args.elems_log2
@@ -711,6 +735,8 @@ def main():
         SIZES_OVERRIDE = [int(v) for v in args.sizes.split(",")]
     if args.impl == "reference":
         run_reference(args)
+    elif args.fixed:
+        run_fixed_only(args)
     else:
         run_gpu(args)
 

@@ -20,14 +20,20 @@ using namespace qfx;
 
 // Maximum of `k` over the aligned block of `seg` consecutive items holding
 // item w (seg a power of two; 0 for a lane without work).  Blocks of 32 items
-// or more also fold their warp's maximum into slot[first item / 32].
+// or more fill whole warps: one warp reduction, and one shared-memory
+// atomicMax per warp into slot[first item / 32].  Smaller blocks sit inside a
+// warp and reduce with xor shuffles.
 __device__ __forceinline__ int block_max(int k, int seg, int* slot, int w) {
+  if (__all_sync(0xffffffffu, seg >= 32)) {
+    k = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);
+    if ((threadIdx.x & 31) == 0) atomicMax(slot + ((w & ~(seg - 1)) >> 5), k);
+    return k;
+  }
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int t = __shfl_xor_sync(0xffffffffu, k, o);
     if (o < seg) k = max(k, t);
   }
-  if (seg >= 32 && (threadIdx.x & 31) == 0) atomicMax(slot + ((w & ~(seg - 1)) >> 5), k);
   return k;
 }
 __device__ __forceinline__ int block_get(int k, int seg, const int* slot, int w) {
