@@ -305,25 +305,34 @@ QFX_HD void fwd_store(const Row& R, int dep, int w, const Val& v, int k1, int k2
 }
 
 // ----------------------------------------------------- backward step (height h)
-// Items w in [0, N): side s, slot w1 < N/2 - 1 of class lp.
-//  - lp >= h: output cell k of a tree node of m = 2^h cells at depth lp - h,
-//    from its children (eqs qft_4B, qft_38B, qft_38C; DST forms of Sec. 5).
-//  - lp == h - 1: item t of the class chain's combine dct(4P) (or dst(4P),
-//    lp >= 1): outputs t and 2P - t (eqs qft_5C, qft_5D; DCT item 0 also
-//    the middle output, eq qft_6).
+// Items w in [0, N/2): side s = w / (N/4), then, in the half-resolution layout
+// of the forward step (class lp at [N/4 - P, N/4 - P/2)), u = N/4 - 1 - w1:
+//  - u >= 2^(h-1): a tree item of class lp = bits(u) >= h: output cells 2j and
+//    2j + 1 of a node of m = 2^h cells at depth lp - h, from its children
+//    (eqs qft_4B, qft_38B, qft_38C; DST forms of Sec. 5);
+//  - u < 2^(h-1): item t of the class chain's combine of class c = h - 1,
+//    dct(4P) (or dst(4P), c >= 1), P = 2^c: outputs t and 2P - t (eqs qft_5C,
+//    qft_5D; DCT item 0 also the middle output, eq qft_6).  The chain's P items
+//    take the half-resolution slots of class c and of every smaller class.
 struct BwdDec { int s, lp, P, off, w2; };
 QFX_HD int bwd_dec(const Row& R, int h, int w, BwdDec& d) {
-  const int H = R.N / 2;
-  d.s = w >= H;
-  const int w1 = w - d.s * H;
-  if (w1 >= H - 1) return 0;
-  d.lp = blen32((uint32_t)(H - 1 - w1)) - 1;
+  const int Q4 = R.N / 4;
+  d.s = w >= Q4;
+  const int w1 = w - d.s * Q4;
+  const int u = Q4 - 1 - w1;
+  if (u >= (1 << (h - 1))) {                                 // tree item
+    d.lp = blen32((uint32_t)u);
+    d.P = 1 << d.lp;
+    d.off = R.N / 2 - 2 * d.P;
+    d.w2 = w1 - (Q4 - d.P);
+    return 1;
+  }
+  d.lp = h - 1;                                              // chain item
+  if (d.s == 1 && d.lp == 0) return 0;                       // dst(4) is its input
   d.P = 1 << d.lp;
-  d.off = H - 2 * d.P;
-  d.w2 = w1 - d.off;
-  if (d.lp >= h) return 1;                                   // tree item
-  if (d.lp == h - 1 && (d.s == 0 || d.lp >= 1)) return 2;    // chain item
-  return 0;
+  d.off = R.N / 2 - 2 * d.P;
+  d.w2 = w1 - (Q4 - d.P);
+  return 2;
 }
 QFX_HD void bwd_eval(const Row& R, int h, int w, Val& v) {
   val_none(v);
@@ -333,26 +342,20 @@ QFX_HD void bwd_eval(const Row& R, int h, int w, Val& v) {
   const Cell* V = side(R, d.s);
   const int16_t* X = exps(R, d.s);
   if (kind == 1) {
-    const int dep = d.lp - h, q = d.w2 >> h;
+    const int dep = d.lp - h, hm = h - 1, q = d.w2 >> hm, j = d.w2 & ((1 << hm) - 1);
     const int hc = 2 * d.off + (2 << dep) - 1 + 2 * q;
     const int Ee = X[hc], Ey = X[hc + 1];
     const int Ex = imax(Ee, Ey);
-    const int m = 1 << h, k = d.w2 & (m - 1);
-    const int base = d.off + q * m, half = base + (m >> 1);
-    Cell a;
-    if (d.s == 0) {            // DCT: X(2j) = E(j); X(2j+1) = Y(j) + Y(j+1); X(m-1) = Y(m/2-1)
-      if (!(k & 1)) a = rsc(V[base + (k >> 1)], Ex - Ee);
-      else if (k < m - 1) a = rsc(add(V[half + (k >> 1)], V[half + (k >> 1) + 1]), Ex - Ey);
-      else a = rsc(V[half + (m >> 1) - 1], Ex - Ey);
-    } else {                   // DST, slot k holds X(k+1): X(2j) = E(j); X(1) = Z(1); X(2j+1) = Z(j) + Z(j+1)
-      const int kk = k + 1;
-      if (!(kk & 1)) a = rsc(V[base + (kk >> 1) - 1], Ex - Ee);
-      else if (kk == 1) a = rsc(V[half], Ex - Ey);
-      else a = rsc(add(V[half + (kk >> 1) - 1], V[half + (kk >> 1)]), Ex - Ey);
+    const int m = 1 << h, base = d.off + q * m, half = base + (m >> 1);
+    if (d.s == 0) {            // DCT: X(2j) = E(j); X(2j+1) = Y(j) + Y(j+1), the last Y(m/2-1)
+      v.a = rsc(V[base + j], Ex - Ee);
+      v.b = rsc(j + 1 < (m >> 1) ? add(V[half + j], V[half + j + 1]) : V[half + j], Ex - Ey);
+    } else {                   // DST, slots 2j, 2j+1 hold X(2j+1), X(2j+2): X(1) = Z(1); X(2j+1) = Z(j) + Z(j+1); X(2j+2) = E(j+1)
+      v.a = rsc(j == 0 ? V[half] : add(V[half + j - 1], V[half + j]), Ex - Ey);
+      v.b = rsc(V[base + j], Ex - Ee);
     }
-    v.a = a;
-    v.k1 = key(a);
-    v.seg = m;
+    v.k1 = imax(key(v.a), key(v.b));
+    v.seg = m >> 1;
     v.ex = Ex;
     return;
   }
@@ -383,9 +386,11 @@ QFX_HD void bwd_store(const Row& R, int h, int w, const Val& v, int bl) {
   Cell* V = side(R, d.s);
   const int sh = bl - kBits;
   if (kind == 1) {
-    const int m = 1 << h, k = d.w2 & (m - 1), q = d.w2 >> h;
-    V[d.off + q * m + k] = rsc(v.a, sh);
-    if (k == 0) exps(R, d.s)[2 * d.off + (1 << (d.lp - h)) - 1 + q] = (int16_t)norm_exp(bl, v.ex);
+    const int hm = h - 1, q = d.w2 >> hm, j = d.w2 & ((1 << hm) - 1);
+    Cell* o = V + d.off + (q << h) + 2 * j;   // an even slot: the pair is 16-byte aligned
+    o[0] = rsc(v.a, sh);
+    o[1] = rsc(v.b, sh);
+    if (j == 0) exps(R, d.s)[2 * d.off + (1 << (d.lp - h)) - 1 + q] = (int16_t)norm_exp(bl, v.ex);
     return;
   }
   const int t = d.w2, P = d.P, off = d.off;

@@ -63,8 +63,8 @@ __device__ __forceinline__ void fx_step(int* slots, int NS, int items, EV ev, ST
   }
 }
 
-// NT threads, K items per thread in the fold and backward steps (K NT = G N:
-// G = 2^lgG rows per CTA pass); the forward and final steps have half as many.
+// NT threads, K items per thread in the fold step (K NT = G N: G = 2^lgG rows
+// per CTA pass); the forward, backward and final steps have half as many.
 // 64 registers a thread (1024 resident threads per SM): measured faster than
 // the unbounded allocation (110-120 registers) at every length, spills included
 template <int NT, int K>
@@ -108,11 +108,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fixed(const uint32_t* __restr
           [&](int w, const Val& v, int m1, int m2) { fwd_store(row_of(w >> (r - 1)), dep, w & (N / 2 - 1), v, m1, m2); });
       end_step();
     }
-    for (int h = 1; h <= r - 1; ++h) {         // node outputs and the class chain
-      fx_step<NT, K, false>(
-          slot_base + cur * 2 * NS, NS, gv * N,
-          [&](int w, Val& v) { bwd_eval(row_of(w >> r), h, w & (N - 1), v); },
-          [&](int w, const Val& v, int m1, int) { bwd_store(row_of(w >> r), h, w & (N - 1), v, m1); });
+    for (int h = 1; h <= r - 1; ++h) {         // node outputs (two cells an item) and the class chain
+      fx_step<NT, K / 2, false>(
+          slot_base + cur * 2 * NS, NS, gv * (N / 2),
+          [&](int w, Val& v) { bwd_eval(row_of(w >> (r - 1)), h, w & (N / 2 - 1), v); },
+          [&](int w, const Val& v, int m1, int) { bwd_store(row_of(w >> (r - 1)), h, w & (N / 2 - 1), v, m1); });
       end_step();
     }
     fx_step<NT, K / 2, false>(                   // CDFT combine, one block per row

@@ -77,7 +77,7 @@ int row(int r, const uint32_t* z, Cell* out, int* E, const std::vector<Sec>& sec
               [&](int w, const Val& v, int m1, int m2) { fwd_store(R, dep, w, v, m1, m2); }))
       return -3;
   for (int h = 1; h <= r - 1; ++h)
-    if (!step(N, [&](int w, Val& v) { bwd_eval(R, h, w, v); },
+    if (!step(H, [&](int w, Val& v) { bwd_eval(R, h, w, v); },
               [&](int w, const Val& v, int m1, int) { bwd_store(R, h, w, v, m1); }))
       return -4;
   if (!step(H, [&](int w, Val& v) { fin_eval(R, w, v); },
