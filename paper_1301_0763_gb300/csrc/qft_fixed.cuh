@@ -181,12 +181,15 @@ QFX_HD Cell load_z(const uint32_t* z, int n) {
 // and its block size seg (a power of two; 0: no work); after the CTA barrier
 // its store function writes the values, shifted by the block maxima, in place.
 struct Val {
-  Cell a, b;           // output values
+  Cell a, b, c, d;     // values (c, d: the forward step's second pair)
   int k1, k2;          // block keys
   int seg;
   int ex;              // exponent the values are aligned to (backward, final)
 };
-QFX_HD void val_none(Val& v) { v.a = zero(); v.b = zero(); v.k1 = 0; v.k2 = 0; v.seg = 0; v.ex = 0; }
+QFX_HD void val_none(Val& v) {
+  v.a = zero(); v.b = zero(); v.c = zero(); v.d = zero();
+  v.k1 = 0; v.k2 = 0; v.seg = 0; v.ex = 0;
+}
 
 // ---------------------------------------------------------------- fold step
 // Items w in [0, N): side s = w / (N/2), slot w1 = w mod (N/2) < N/2 - 1: the
@@ -243,64 +246,106 @@ QFX_HD void fold_base(const Row& R, const uint32_t* z) {
 }
 
 // ------------------------------------------------------- forward step (depth d)
-// Items w in [0, N/2): side s = w / (N/4); per class (lp >= d + 1) the mirror
-// butterflies of its 2^d nodes of m = P / 2^d cells, one pair (i, m-1-i) per
-// item, i < m/2 (eqs qft_1, qft_2; DST roles swapped, Sec. 3.2), and the
-// secant products of the odd-harmonic half (eq qft_38A).  Keys: k1 for the
-// even-harmonic child, k2 for the product block (x + bits + kKeyOff); the
-// values are the child e and the difference o before the secant.
-struct FwdDec { int s, lp, off, q, i, m, base; };
+// Items w in [0, N/4): side s = w / (N/8); item w1 takes the mirror pairs
+// p = 2 w1 and 2 w1 + 1 of the side's pair layout (class lp at pairs
+// [N/4 - P, N/4 - P/2), one pair (i, m-1-i), i < m/2, per pair of each of its
+// 2^d nodes of m = P / 2^d cells): the butterflies of eqs qft_1, qft_2 (DST
+// roles swapped, Sec. 3.2) and the secant products of the odd-harmonic half
+// (eq qft_38A).
+//  - m >= 4: both pairs (i, i+1) are in one node; keys: k1 for the
+//    even-harmonic child, k2 for the product block (x + bits + kKeyOff); the
+//    values: children a, c (pairs i, i+1) and differences b, d before the secant.
+//  - m = 2: the pairs are the only pairs of nodes q and q+1 (the second pair
+//    exists if lp >= 2): every child is a block of one cell, normalized by its
+//    own key (seg 1, no reduction).
+struct FwdDec { int s, lp, off, q, i, m, base; bool two; };
 QFX_HD bool fwd_dec(const Row& R, int dep, int w, FwdDec& d) {
-  const int Q4 = R.N / 4;
-  d.s = w >= Q4;
-  const int w1 = w - d.s * Q4;
-  d.lp = blen32((uint32_t)(Q4 - 1 - w1));
+  const int Q8 = R.N / 8, Q4 = R.N / 4;
+  d.s = w >= Q8;
+  const int p = 2 * (w - d.s * Q8);
+  d.lp = blen32((uint32_t)(Q4 - 1 - p));
   if (d.lp < dep + 1) return false;
   const int P = 1 << d.lp;
   d.off = R.N / 2 - 2 * P;
-  const int w2 = w1 - (Q4 - P);
+  const int w2 = p - (Q4 - P);
   const int hb = d.lp - dep - 1;
   d.q = w2 >> hb;
   d.i = w2 & ((1 << hb) - 1);
   d.m = 2 << hb;
   d.base = d.off + d.q * d.m;
+  d.two = hb >= 1 || d.lp >= 2;
   return true;
+}
+// key of an odd-harmonic difference o times the secant c (0 for zero)
+QFX_HD int prod_key(Cell o, Sec c) {
+  const int64_t px = (int64_t)o.x * c.c, py = (int64_t)o.y * c.c;
+  const uint64_t mx = mag64(px), my = mag64(py);
+  const int bl = blen64(mx > my ? mx : my);
+  return bl ? c.x + bl + kKeyOff : 0;
+}
+// the product block's member o c shifted to the block whose key is k2
+QFX_HD Cell prod_val(Cell o, Sec c, int k2) {
+  Cell t = zero();
+  if (k2) {
+    const int top = k2 - kKeyOff - kBits;
+    t.x = (int32_t)rs((int64_t)o.x * c.c, top - c.x);
+    t.y = (int32_t)rs((int64_t)o.y * c.c, top - c.x);
+  }
+  return t;
+}
+QFX_HD void butterfly(int s, Cell a, Cell b, Cell& e, Cell& o) {
+  e = s ? sub(a, b) : add(a, b);   // even-harmonic child
+  o = s ? add(a, b) : sub(a, b);   // odd-harmonic child, before the secant
 }
 QFX_HD void fwd_eval(const Row& R, int dep, int w, Val& v) {
   val_none(v);
   FwdDec d;
   if (!fwd_dec(R, dep, w, d)) return;
   const Cell* V = side(R, d.s);
-  const Cell a = V[d.base + d.i], b = V[d.base + d.m - 1 - d.i];
-  v.a = d.s ? sub(a, b) : add(a, b);   // even-harmonic child
-  v.b = d.s ? add(a, b) : sub(a, b);   // odd-harmonic child, before the secant
-  v.k1 = key(v.a);
-  const Sec c = R.sec[(d.m >> 1) - 1 + d.i];
-  const int64_t px = (int64_t)v.b.x * c.c, py = (int64_t)v.b.y * c.c;
-  const uint64_t mx = mag64(px), my = mag64(py);
-  const int bl = blen64(mx > my ? mx : my);
-  v.k2 = bl ? c.x + bl + kKeyOff : 0;
-  v.seg = d.m >> 1;
+  if (d.m >= 4) {
+    butterfly(d.s, V[d.base + d.i], V[d.base + d.m - 1 - d.i], v.a, v.b);
+    butterfly(d.s, V[d.base + d.i + 1], V[d.base + d.m - 2 - d.i], v.c, v.d);
+    const Sec* c = R.sec + (d.m >> 1) - 1 + d.i;
+    v.k1 = imax(key(v.a), key(v.c));
+    v.k2 = imax(prod_key(v.b, c[0]), prod_key(v.d, c[1]));
+    v.seg = d.m >> 2;
+  } else {
+    butterfly(d.s, V[d.base], V[d.base + 1], v.a, v.b);
+    if (d.two) butterfly(d.s, V[d.base + 2], V[d.base + 3], v.c, v.d);
+    v.seg = 1;
+  }
 }
 QFX_HD void fwd_store(const Row& R, int dep, int w, const Val& v, int k1, int k2) {
   FwdDec d;
   fwd_dec(R, dep, w, d);
   Cell* V = side(R, d.s);
   int16_t* X = exps(R, d.s);
-  const int Ein = X[2 * d.off + (1 << dep) - 1 + d.q];
-  V[d.base + d.i] = rsc(v.a, k1 - kBits);
-  const Sec c = R.sec[(d.m >> 1) - 1 + d.i];
-  const int top = k2 - kKeyOff - kBits;   // product block exponent - Ein
-  Cell t = zero();
-  if (k2) {
-    t.x = (int32_t)rs((int64_t)v.b.x * c.c, top - c.x);
-    t.y = (int32_t)rs((int64_t)v.b.y * c.c, top - c.x);
+  const int h0 = 2 * d.off + (1 << dep) - 1, h1 = 2 * d.off + (2 << dep) - 1;   // heap bases: depth dep, dep + 1
+  if (d.m >= 4) {
+    const Sec* c = R.sec + (d.m >> 1) - 1 + d.i;
+    Cell* e = V + d.base + d.i;                  // i even: both pairs 16-byte aligned
+    Cell* t = V + d.base + (d.m >> 1) + d.i;
+    e[0] = rsc(v.a, k1 - kBits);
+    e[1] = rsc(v.c, k1 - kBits);
+    t[0] = prod_val(v.b, c[0], k2);
+    t[1] = prod_val(v.d, c[1], k2);
+    if (d.i == 0) {
+      const int Ein = X[h0 + d.q];
+      X[h1 + 2 * d.q] = (int16_t)norm_exp(k1, Ein);
+      X[h1 + 2 * d.q + 1] = (int16_t)(k2 ? Ein + k2 - kKeyOff - kBits : kEZero);
+    }
+    return;
   }
-  V[d.base + (d.m >> 1) + d.i] = t;
-  if (d.i == 0) {
-    const int hc = 2 * d.off + (2 << dep) - 1 + 2 * d.q;
-    X[hc] = (int16_t)norm_exp(k1, Ein);
-    X[hc + 1] = (int16_t)(k2 ? Ein + top : kEZero);
+  // nodes of two cells: the secant of a node of 2 cells (periodization 8) is entry 0
+  const Sec c = R.sec[0];
+  for (int k = 0; k < (d.two ? 2 : 1); ++k) {
+    const Cell e = k ? v.c : v.a, o = k ? v.d : v.b;
+    const int q = d.q + k, ke = key(e), kt = prod_key(o, c);
+    const int Ein = X[h0 + q];
+    V[d.base + 2 * k] = rsc(e, ke - kBits);
+    V[d.base + 2 * k + 1] = prod_val(o, c, kt);
+    X[h1 + 2 * q] = (int16_t)norm_exp(ke, Ein);
+    X[h1 + 2 * q + 1] = (int16_t)(kt ? Ein + kt - kKeyOff - kBits : kEZero);
   }
 }
 

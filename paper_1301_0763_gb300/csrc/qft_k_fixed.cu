@@ -64,7 +64,8 @@ __device__ __forceinline__ void fx_step(int* slots, int NS, int items, EV ev, ST
 }
 
 // NT threads, K items per thread in the fold step (K NT = G N: G = 2^lgG rows
-// per CTA pass); the forward, backward and final steps have half as many.
+// per CTA pass); the backward and final steps have half as many, the forward
+// steps a quarter.
 // 64 registers a thread (1024 resident threads per SM): measured faster than
 // the unbounded allocation (110-120 registers) at every length, spills included
 template <int NT, int K>
@@ -102,10 +103,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fixed(const uint32_t* __restr
         [&](int w, const Val& v, int m1, int) { fold_store(row_of(w >> r), w & (N - 1), v, m1); });
     end_step();
     for (int dep = 0; dep <= r - 3; ++dep) {   // mirror butterflies and secant products
-      fx_step<NT, K / 2, true>(
-          slot_base + cur * 2 * NS, NS, gv * (N / 2),
-          [&](int w, Val& v) { fwd_eval(row_of(w >> (r - 1)), dep, w & (N / 2 - 1), v); },
-          [&](int w, const Val& v, int m1, int m2) { fwd_store(row_of(w >> (r - 1)), dep, w & (N / 2 - 1), v, m1, m2); });
+      fx_step<NT, (K / 4 > 0 ? K / 4 : 1), true>(
+          slot_base + cur * 2 * NS, NS, gv * (N / 4),
+          [&](int w, Val& v) { fwd_eval(row_of(w >> (r - 2)), dep, w & (N / 4 - 1), v); },
+          [&](int w, const Val& v, int m1, int m2) { fwd_store(row_of(w >> (r - 2)), dep, w & (N / 4 - 1), v, m1, m2); });
       end_step();
     }
     for (int h = 1; h <= r - 1; ++h) {         // node outputs (two cells an item) and the class chain

@@ -73,7 +73,7 @@ int row(int r, const uint32_t* z, Cell* out, int* E, const std::vector<Sec>& sec
             [&](int w, const Val& v, int m1, int) { fold_store(R, w, v, m1); }))
     return -2;
   for (int dep = 0; dep <= r - 3; ++dep)
-    if (!step(H, [&](int w, Val& v) { fwd_eval(R, dep, w, v); },
+    if (!step(N / 4, [&](int w, Val& v) { fwd_eval(R, dep, w, v); },
               [&](int w, const Val& v, int m1, int m2) { fwd_store(R, dep, w, v, m1, m2); }))
       return -3;
   for (int h = 1; h <= r - 1; ++h)
