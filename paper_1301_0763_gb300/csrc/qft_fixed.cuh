@@ -192,36 +192,44 @@ QFX_HD void val_none(Val& v) {
 }
 
 // ---------------------------------------------------------------- fold step
-// Items w in [0, N): side s = w / (N/2), slot w1 = w mod (N/2) < N/2 - 1: the
-// fold value c(n) or d(n) of that slot, one block per class (a NORM of the
-// fold output followed by the lossless NORMs of the even/odd separations of
-// Sec. 3.1 is one NORM per class).
+// Items w in [0, N/2): side s = w / (N/4), slots 2 w1 and 2 w1 + 1 of that
+// side: the fold values c(n) or d(n) of those slots, one block per class (a
+// NORM of the fold output followed by the lossless NORMs of the even/odd
+// separations of Sec. 3.1 is one NORM per class).  A class of P >= 2 slots
+// holds P/2 items; the last item of a side holds the class of one slot
+// (c(N/4), or the DST base d(N/4)) and nothing else (slot N/2 - 1 is the DCT
+// base, done by fold_base).  Reads the staged input row z.
 struct FoldDec { int s, w1, lp, P, off, i; };
 QFX_HD bool fold_dec(const Row& R, int w, FoldDec& d) {
-  const int H = R.N / 2;
-  d.s = w >= H;
-  d.w1 = w - d.s * H;
-  if (d.w1 >= H - 1) return false;
+  const int H = R.N / 2, Q4 = R.N / 4;
+  d.s = w >= Q4;
+  d.w1 = 2 * (w - d.s * Q4);   // the item's first slot
   d.lp = blen32((uint32_t)(H - 1 - d.w1)) - 1;
   d.P = 1 << d.lp;
   d.off = H - 2 * d.P;
   d.i = d.w1 - d.off;
   return true;
 }
+QFX_HD Cell fold_value(const Row& R, const uint32_t* z, int s, int lp, int i) {
+  const int n = (2 * i + 1) << (R.r - 2 - lp);
+  const Cell a = load_z(z, n), b = load_z(z, R.N - n);
+  return s ? sub(a, b) : add(a, b);
+}
 QFX_HD void fold_eval(const Row& R, const uint32_t* z, int w, Val& v) {
   val_none(v);
   FoldDec d;
-  if (!fold_dec(R, w, d)) return;
-  const int n = (2 * d.i + 1) << (R.r - 2 - d.lp);
-  const Cell a = load_z(z, n), b = load_z(z, R.N - n);
-  v.a = d.s ? sub(a, b) : add(a, b);
-  v.k1 = key(v.a);
-  v.seg = d.P;
+  fold_dec(R, w, d);
+  v.a = fold_value(R, z, d.s, d.lp, d.i);
+  if (d.P >= 2) v.b = fold_value(R, z, d.s, d.lp, d.i + 1);
+  v.k1 = imax(key(v.a), key(v.b));
+  v.seg = d.P >= 2 ? d.P >> 1 : 1;
 }
 QFX_HD void fold_store(const Row& R, int w, const Val& v, int bl) {
   FoldDec d;
   fold_dec(R, w, d);
-  side(R, d.s)[d.w1] = rsc(v.a, bl - kBits);
+  Cell* V = side(R, d.s);
+  V[d.w1] = rsc(v.a, bl - kBits);
+  if (d.P >= 2) V[d.w1 + 1] = rsc(v.b, bl - kBits);
   if (d.i == 0) {
     const int E = norm_exp(bl, kInExp);
     exps(R, d.s)[2 * d.off] = (int16_t)E;

@@ -63,9 +63,8 @@ __device__ __forceinline__ void fx_step(int* slots, int NS, int items, EV ev, ST
   }
 }
 
-// NT threads, K items per thread in the fold step (K NT = G N: G = 2^lgG rows
-// per CTA pass); the backward and final steps have half as many, the forward
-// steps a quarter.
+// NT threads and G = 2^lgG rows per CTA pass, K NT = G N: the fold, backward
+// and final steps have K/2 items per thread, the forward steps K/4.
 // 64 registers a thread (1024 resident threads per SM): measured faster than
 // the unbounded allocation (110-120 registers) at every length, spills included
 template <int NT, int K>
@@ -97,10 +96,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fixed(const uint32_t* __restr
       cur ^= 1;
     };
     for (int g = tid; g < gv; g += NT) fold_base(row_of(g), staged(row_of(g)));
-    fx_step<NT, K, false>(
-        slot_base + cur * 2 * NS, NS, gv * N,
-        [&](int w, Val& v) { const Row R = row_of(w >> r); fold_eval(R, staged(R), w & (N - 1), v); },
-        [&](int w, const Val& v, int m1, int) { fold_store(row_of(w >> r), w & (N - 1), v, m1); });
+    fx_step<NT, K / 2, false>(
+        slot_base + cur * 2 * NS, NS, gv * (N / 2),
+        [&](int w, Val& v) { const Row R = row_of(w >> (r - 1)); fold_eval(R, staged(R), w & (N / 2 - 1), v); },
+        [&](int w, const Val& v, int m1, int) { fold_store(row_of(w >> (r - 1)), w & (N / 2 - 1), v, m1); });
     end_step();
     for (int dep = 0; dep <= r - 3; ++dep) {   // mirror butterflies and secant products
       fx_step<NT, (K / 4 > 0 ? K / 4 : 1), true>(

@@ -69,7 +69,7 @@ int row(int r, const uint32_t* z, Cell* out, int* E, const std::vector<Sec>& sec
   uint32_t* zs = staged(R);
   for (int n = 0; n < N; ++n) zs[n] = z[n];
   fold_base(R, zs);
-  if (!step(N, [&](int w, Val& v) { fold_eval(R, zs, w, v); },
+  if (!step(H, [&](int w, Val& v) { fold_eval(R, zs, w, v); },
             [&](int w, const Val& v, int m1, int) { fold_store(R, w, v, m1); }))
     return -2;
   for (int dep = 0; dep <= r - 3; ++dep)
