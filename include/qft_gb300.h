@@ -171,7 +171,7 @@ int qft_execute_backward(qft_plan plan, const void* grad_out, void* grad_in, voi
  * secants are 31-bit mantissas with their own exponents and the 64-bit
  * products are normalized once per node.
  *   plan       created with kind QFT_KIND_C2C, dtype QFT_DTYPE_I16, flags 0,
- *              2 <= n <= 2^13 (QFT_ERR_INVALID_N otherwise).
+ *              2 <= n <= 2^14 (QFT_ERR_INVALID_N otherwise).
  *   in         device, [batch][n] complex int16 pairs (re, im): value q 2^-15;
  *              4-byte aligned.
  *   out        device, [batch][n] complex int32 mantissa pairs; 8-byte aligned.

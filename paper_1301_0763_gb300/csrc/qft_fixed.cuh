@@ -53,7 +53,7 @@ namespace qfx {
 constexpr int kBits = 29;          // significant bits of a normalized block's largest mantissa
 constexpr int kEZero = -16384;     // exponent of an all-zero block
 constexpr int kKeyOff = 64;        // offset that keeps product keys positive
-constexpr int kMaxLog2 = 13;       // largest row one CTA transforms
+constexpr int kMaxLog2 = 14;       // largest row one CTA transforms
 constexpr int kInExp = -15;        // exponent of the Q15 input
 
 struct Cell { int32_t x, y; };

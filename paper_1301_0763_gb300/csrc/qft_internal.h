@@ -30,7 +30,7 @@ struct __align__(8) qc_storage { float x, y; };
 namespace qft_lib {
 constexpr int kMaxRowLog2 = 14;   // largest row one CTA transforms in shared memory
 constexpr int kMaxLog2 = 24;      // largest transform length
-constexpr int kFixedMaxLog2 = 13; // largest row of the fixed-point variant (one CTA, shared memory)
+constexpr int kFixedMaxLog2 = 14; // largest row of the fixed-point variant (one CTA, shared memory)
 constexpr int kNodeLog2 = 12;     // largest node group of the large-row path (cells)
 constexpr int kNodeThreads = 512;
 constexpr int64_t kScratchBudget = (int64_t)16 << 30;  // bytes of scratch per plan

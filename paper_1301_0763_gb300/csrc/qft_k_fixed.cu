@@ -131,12 +131,13 @@ struct FxCfg {
 };
 // threads, items per thread and rows per CTA pass for rows of length 2^r:
 // 256 threads and up to 1024 items (at most 48 KB of rows) per CTA up to 2^10,
-// then one row per CTA with 4 items per thread (8 at 2^13)
+// then one row per CTA (1024 threads from 2^12; 192 KB of shared memory at 2^14)
 inline FxCfg fx_cfg(int r) {
   if (r <= 1) return {256, 4, 0};
   if (r == 11) return {512, 4, 0};
   if (r == 12) return {1024, 4, 0};
   if (r == 13) return {1024, 8, 0};
+  if (r == 14) return {1024, 16, 0};
   const int N = 1 << r;
   int G = 1024 >> r;
   while (G > 1 && (size_t)G * row_bytes(N) > 49152) G >>= 1;
@@ -194,6 +195,7 @@ int qft_launch_fixed(qft_plan p, const void* in, void* out, int32_t* exps, cudaS
   else if (c.nt == 512 && c.k == 4) e = launch_k<512, 4>(p, c, z, o, eo, st);
   else if (c.nt == 1024 && c.k == 4) e = launch_k<1024, 4>(p, c, z, o, eo, st);
   else if (c.nt == 1024 && c.k == 8) e = launch_k<1024, 8>(p, c, z, o, eo, st);
+  else if (c.nt == 1024 && c.k == 16) e = launch_k<1024, 16>(p, c, z, o, eo, st);
   else return QFT_ERR_INVALID_N;
   qft_time_end(p, st);
   return qft_set_cuda(p, e);

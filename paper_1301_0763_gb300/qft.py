@@ -348,7 +348,7 @@ def fft_bf16(x: torch.Tensor, op: int = OP_FORWARD) -> torch.Tensor:
 def fft_fixed(z: torch.Tensor):
     """Fixed-point forward DFT (the improved QFT in int32 block floating
     point, qft_execute_fixed): z is an int16 tensor [..., N, 2] of Q15 (re, im)
-    samples (value q 2^-15), 2 <= N <= 2^13.  Returns (mantissas int32
+    samples (value q 2^-15), 2 <= N <= 2^14.  Returns (mantissas int32
     [..., N, 2], exponents int32 [...]); X(k) = mantissa(k) * 2^exponent."""
     _need_cuda(z)
     if z.dtype != torch.int16 or z.dim() < 2 or z.shape[-1] != 2:

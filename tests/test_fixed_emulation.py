@@ -1,6 +1,6 @@
 """Host emulation of the fixed-point kernel (qft_fixed.cuh built for the CPU,
 steps run as the kernel runs them) against the fixed-point oracle: every
-mantissa and exponent equal, for N = 2 .. 2^13 and the edge cases (zeros,
+mantissa and exponent equal, for N = 2 .. 2^14 and the edge cases (zeros,
 full scale, impulses, sparse and real input, tiny values).  The emulation also
 checks the block structure the kernel's warp reduction relies on."""
 import os
@@ -37,7 +37,7 @@ def _cases(N, seed):
     return np.concatenate(cs)
 
 
-@pytest.mark.parametrize("lg", range(1, 14))
+@pytest.mark.parametrize("lg", range(1, 15))
 def test_fixed_emulation_bit_exact(lg):
     N = 1 << lg
     z = _cases(N, 800 + lg)

@@ -52,7 +52,7 @@ def _gpu_fx(q, z):
     return X.cpu().numpy(), E.cpu().numpy()
 
 
-@pytest.mark.parametrize("lg", range(1, 14))
+@pytest.mark.parametrize("lg", range(1, 15))
 def test_fixed_bit_exact(q, lg):
     N = 1 << lg
     z = _cases(N, 900 + lg)
@@ -62,7 +62,7 @@ def test_fixed_bit_exact(q, lg):
     assert np.array_equal(X, Xo)
 
 
-@pytest.mark.parametrize("lg,rows", [(4, 5000), (10, 1200), (12, 400), (13, 320)])
+@pytest.mark.parametrize("lg,rows", [(4, 5000), (10, 1200), (12, 400), (13, 320), (14, 200)])
 def test_fixed_many_rows_per_cta(q, lg, rows):
     """More rows than resident CTAs: every CTA loops over rows (shared memory reused)."""
     N = 1 << lg
@@ -102,7 +102,7 @@ def test_fixed_deterministic_and_accurate(q):
 def test_fixed_abi_errors(q):
     lib = q.load_library()
     h = ctypes.c_void_p()
-    assert lib.qft_plan_create(ctypes.byref(h), 1 << 14, 4, q.KIND_C2C, q.DTYPE_I16, 0) == -1   # INVALID_N
+    assert lib.qft_plan_create(ctypes.byref(h), 1 << 15, 4, q.KIND_C2C, q.DTYPE_I16, 0) == -1   # INVALID_N
     assert lib.qft_plan_create(ctypes.byref(h), 1 << 10, 4, q.KIND_R2C, q.DTYPE_I16, 0) == -3   # DTYPE
     assert lib.qft_plan_create(ctypes.byref(h), 1 << 10, 4, q.KIND_C2C, q.DTYPE_I16, 1) == -9   # flags
     p = q.Plan(1024, 4, q.KIND_C2C, q.DTYPE_I16)
