@@ -188,15 +188,16 @@ int qft_launch_fixed(qft_plan p, const void* in, void* out, int32_t* exps, cudaS
   Cell* o = static_cast<Cell*>(out);
   int* eo = reinterpret_cast<int*>(exps);
   const FxCfg c = fx_cfg(p->r);
-  cudaError_t e;
+  cudaError_t (*launch)(const qft_plan, const FxCfg&, const uint32_t*, Cell*, int*, cudaStream_t) = nullptr;
+  if (c.nt == 256 && c.k == 2) launch = launch_k<256, 2>;
+  else if (c.nt == 256 && c.k == 4) launch = launch_k<256, 4>;
+  else if (c.nt == 512 && c.k == 4) launch = launch_k<512, 4>;
+  else if (c.nt == 1024 && c.k == 4) launch = launch_k<1024, 4>;
+  else if (c.nt == 1024 && c.k == 8) launch = launch_k<1024, 8>;
+  else if (c.nt == 1024 && c.k == 16) launch = launch_k<1024, 16>;
+  if (!launch) return QFT_ERR_INVALID_N;
   qft_time_begin(p, st, QFT_KERNEL_ROWS);
-  if (c.nt == 256 && c.k == 2) e = launch_k<256, 2>(p, c, z, o, eo, st);
-  else if (c.nt == 256 && c.k == 4) e = launch_k<256, 4>(p, c, z, o, eo, st);
-  else if (c.nt == 512 && c.k == 4) e = launch_k<512, 4>(p, c, z, o, eo, st);
-  else if (c.nt == 1024 && c.k == 4) e = launch_k<1024, 4>(p, c, z, o, eo, st);
-  else if (c.nt == 1024 && c.k == 8) e = launch_k<1024, 8>(p, c, z, o, eo, st);
-  else if (c.nt == 1024 && c.k == 16) e = launch_k<1024, 16>(p, c, z, o, eo, st);
-  else return QFT_ERR_INVALID_N;
+  const cudaError_t e = launch(p, c, z, o, eo, st);
   qft_time_end(p, st);
   return qft_set_cuda(p, e);
 }
