@@ -260,16 +260,13 @@ QFX_HD void fold_base(const Row& R, const uint32_t* z) {
 // 2^d nodes of m = P / 2^d cells): the butterflies of eqs qft_1, qft_2 (DST
 // roles swapped, Sec. 3.2) and the secant products of the odd-harmonic half
 // (eq qft_38A).
-//  - m >= 8: both pairs (i, i+1) are in one node; keys: k1 for the
+//  - m >= 4: both pairs (i, i+1) are in one node; keys: k1 for the
 //    even-harmonic child, k2 for the product block (x + bits + kKeyOff); the
 //    values: children a, c (pairs i, i+1) and differences b, d before the secant.
-//  - m = 4: the item is the node's whole subtree: both forward levels and the
-//    two backward levels (eqs qft_4B, qft_38B, qft_38C) run in registers, every
-//    block of the subtree inside the item; it gives the node's four outputs and
-//    their exponent (the backward steps at heights 1 and 2 have no tree items).
-//  - m = 2: only class lp = 1 (whose root has two cells) has work here, the
-//    same way; the deeper nodes of two cells belong to subtrees of four.
-struct FwdDec { int s, lp, off, q, i, m, base; };
+//  - m = 2: the pairs are the only pairs of nodes q and q+1 (the second pair
+//    exists if lp >= 2): every child is a block of one cell, normalized by its
+//    own key (seg 1, no reduction).
+struct FwdDec { int s, lp, off, q, i, m, base; bool two; };
 QFX_HD bool fwd_dec(const Row& R, int dep, int w, FwdDec& d) {
   const int Q8 = R.N / 8, Q4 = R.N / 4;
   d.s = w >= Q8;
@@ -284,7 +281,8 @@ QFX_HD bool fwd_dec(const Row& R, int dep, int w, FwdDec& d) {
   d.i = w2 & ((1 << hb) - 1);
   d.m = 2 << hb;
   d.base = d.off + d.q * d.m;
-  return d.m >= 4 || d.lp == 1;
+  d.two = hb >= 1 || d.lp >= 2;
+  return true;
 }
 // key of an odd-harmonic difference o times the secant c (0 for zero)
 QFX_HD int prod_key(Cell o, Sec c) {
@@ -303,95 +301,35 @@ QFX_HD Cell prod_val(Cell o, Sec c, int k2) {
   }
   return t;
 }
-// exponent of a product block of key k2 whose differences have exponent Ein
-QFX_HD int prod_exp(int k2, int Ein) { return k2 ? Ein + k2 - kKeyOff - kBits : kEZero; }
 QFX_HD void butterfly(int s, Cell a, Cell b, Cell& e, Cell& o) {
   e = s ? sub(a, b) : add(a, b);   // even-harmonic child
   o = s ? add(a, b) : sub(a, b);   // odd-harmonic child, before the secant
-}
-// A node of two cells (x0, x1; exponent E) in registers: its mirror butterfly
-// (one-cell children, each its own block) and its output (two cells,
-// normalized); returns the output exponent.  sec0: the secant of a node of
-// two cells (cos(pi/4)).
-QFX_HD int node2(int s, Cell& x0, Cell& x1, int E, Sec sec0) {
-  Cell e, o;
-  butterfly(s, x0, x1, e, o);
-  const int ke = key(e), kt = prod_key(o, sec0);
-  const Cell ce = rsc(e, ke - kBits), ct = prod_val(o, sec0, kt);
-  const int Ee = norm_exp(ke, E), Et = prod_exp(kt, E);
-  // output: DCT X(0) = E(0), X(1) = Y(0); DST slots X(1) = Z(1), X(2) = E(1)
-  const int Ex = imax(Ee, Et);
-  Cell y0 = s ? rsc(ct, Ex - Et) : rsc(ce, Ex - Ee);
-  Cell y1 = s ? rsc(ce, Ex - Ee) : rsc(ct, Ex - Et);
-  const int bl = imax(key(y0), key(y1));
-  x0 = rsc(y0, bl - kBits);
-  x1 = rsc(y1, bl - kBits);
-  return norm_exp(bl, Ex);
 }
 QFX_HD void fwd_eval(const Row& R, int dep, int w, Val& v) {
   val_none(v);
   FwdDec d;
   if (!fwd_dec(R, dep, w, d)) return;
   const Cell* V = side(R, d.s);
-  v.seg = 1;
-  if (d.m >= 8) {
+  if (d.m >= 4) {
     butterfly(d.s, V[d.base + d.i], V[d.base + d.m - 1 - d.i], v.a, v.b);
     butterfly(d.s, V[d.base + d.i + 1], V[d.base + d.m - 2 - d.i], v.c, v.d);
     const Sec* c = R.sec + (d.m >> 1) - 1 + d.i;
     v.k1 = imax(key(v.a), key(v.c));
     v.k2 = imax(prod_key(v.b, c[0]), prod_key(v.d, c[1]));
     v.seg = d.m >> 2;
-    return;
+  } else {
+    butterfly(d.s, V[d.base], V[d.base + 1], v.a, v.b);
+    if (d.two) butterfly(d.s, V[d.base + 2], V[d.base + 3], v.c, v.d);
+    v.seg = 1;
   }
-  const int Ein = exps(R, d.s)[2 * d.off + (1 << dep) - 1 + d.q];
-  const Sec sec0 = R.sec[0];
-  if (d.m == 2) {                       // the root of class 1
-    v.a = V[d.base];
-    v.b = V[d.base + 1];
-    v.ex = node2(d.s, v.a, v.b, Ein, sec0);
-    return;
-  }
-  // a node of four cells: forward butterflies (pairs (0,3), (1,2)), children of two cells
-  Cell e0, o0, e1, o1;
-  butterfly(d.s, V[d.base], V[d.base + 3], e0, o0);
-  butterfly(d.s, V[d.base + 1], V[d.base + 2], e1, o1);
-  const Sec* c = R.sec + 1;             // the secants of a node of four cells
-  const int ke = imax(key(e0), key(e1));
-  const int kt = imax(prod_key(o0, c[0]), prod_key(o1, c[1]));
-  Cell x0 = rsc(e0, ke - kBits), x1 = rsc(e1, ke - kBits);
-  Cell y0 = prod_val(o0, c[0], kt), y1 = prod_val(o1, c[1], kt);
-  const int EE = node2(d.s, x0, x1, norm_exp(ke, Ein), sec0);
-  const int EY = node2(d.s, y0, y1, prod_exp(kt, Ein), sec0);
-  // the node's output from its children's (eqs qft_4B, qft_38B, qft_38C)
-  const int Ex = imax(EE, EY);
-  const Cell a0 = rsc(x0, Ex - EE), a1 = rsc(x1, Ex - EE);
-  Cell o[4];
-  if (d.s == 0) {   // X(0) = E(0), X(1) = Y(0) + Y(1), X(2) = E(1), X(3) = Y(1)
-    o[0] = a0;
-    o[1] = rsc(add(y0, y1), Ex - EY);
-    o[2] = a1;
-    o[3] = rsc(y1, Ex - EY);
-  } else {          // slots hold X(1..4): X(1) = Z(1), X(2) = E(1), X(3) = Z(1) + Z(2), X(4) = E(2)
-    o[0] = rsc(y0, Ex - EY);
-    o[1] = a0;
-    o[2] = rsc(add(y0, y1), Ex - EY);
-    o[3] = a1;
-  }
-  const int bl = imax(imax(key(o[0]), key(o[1])), imax(key(o[2]), key(o[3])));
-  v.a = rsc(o[0], bl - kBits);
-  v.b = rsc(o[1], bl - kBits);
-  v.c = rsc(o[2], bl - kBits);
-  v.d = rsc(o[3], bl - kBits);
-  v.ex = norm_exp(bl, Ex);
 }
 QFX_HD void fwd_store(const Row& R, int dep, int w, const Val& v, int k1, int k2) {
   FwdDec d;
   fwd_dec(R, dep, w, d);
   Cell* V = side(R, d.s);
   int16_t* X = exps(R, d.s);
-  const int h0 = 2 * d.off + (1 << dep) - 1;   // heap base of depth dep
-  if (d.m >= 8) {
-    const int h1 = 2 * d.off + (2 << dep) - 1;
+  const int h0 = 2 * d.off + (1 << dep) - 1, h1 = 2 * d.off + (2 << dep) - 1;   // heap bases: depth dep, dep + 1
+  if (d.m >= 4) {
     const Sec* c = R.sec + (d.m >> 1) - 1 + d.i;
     Cell* e = V + d.base + d.i;                  // i even: both pairs 16-byte aligned
     Cell* t = V + d.base + (d.m >> 1) + d.i;
@@ -402,27 +340,29 @@ QFX_HD void fwd_store(const Row& R, int dep, int w, const Val& v, int k1, int k2
     if (d.i == 0) {
       const int Ein = X[h0 + d.q];
       X[h1 + 2 * d.q] = (int16_t)norm_exp(k1, Ein);
-      X[h1 + 2 * d.q + 1] = (int16_t)prod_exp(k2, Ein);
+      X[h1 + 2 * d.q + 1] = (int16_t)(k2 ? Ein + k2 - kKeyOff - kBits : kEZero);
     }
     return;
   }
-  // a whole subtree: the node's outputs and their exponent
-  V[d.base] = v.a;
-  V[d.base + 1] = v.b;
-  if (d.m == 4) {
-    V[d.base + 2] = v.c;
-    V[d.base + 3] = v.d;
+  // nodes of two cells: the secant of a node of 2 cells (periodization 8) is entry 0
+  const Sec c = R.sec[0];
+  for (int k = 0; k < (d.two ? 2 : 1); ++k) {
+    const Cell e = k ? v.c : v.a, o = k ? v.d : v.b;
+    const int q = d.q + k, ke = key(e), kt = prod_key(o, c);
+    const int Ein = X[h0 + q];
+    V[d.base + 2 * k] = rsc(e, ke - kBits);
+    V[d.base + 2 * k + 1] = prod_val(o, c, kt);
+    X[h1 + 2 * q] = (int16_t)norm_exp(ke, Ein);
+    X[h1 + 2 * q + 1] = (int16_t)(kt ? Ein + kt - kKeyOff - kBits : kEZero);
   }
-  X[h0 + d.q] = (int16_t)v.ex;
 }
 
 // ----------------------------------------------------- backward step (height h)
 // Items w in [0, N/2): side s = w / (N/4), then, in the half-resolution layout
 // of the forward step (class lp at [N/4 - P, N/4 - P/2)), u = N/4 - 1 - w1:
-//  - u >= 2^(h-1), h >= 3: a tree item of class lp = bits(u) >= h: output
-//    cells 2j and 2j + 1 of a node of m = 2^h cells at depth lp - h, from its
-//    children (eqs qft_4B, qft_38B, qft_38C; DST forms of Sec. 5); nodes of 2
-//    and 4 cells got their outputs in the forward step (subtree items);
+//  - u >= 2^(h-1): a tree item of class lp = bits(u) >= h: output cells 2j and
+//    2j + 1 of a node of m = 2^h cells at depth lp - h, from its children
+//    (eqs qft_4B, qft_38B, qft_38C; DST forms of Sec. 5);
 //  - u < 2^(h-1): item t of the class chain's combine of class c = h - 1,
 //    dct(4P) (or dst(4P), c >= 1), P = 2^c: outputs t and 2P - t (eqs qft_5C,
 //    qft_5D; DCT item 0 also the middle output, eq qft_6).  The chain's P items
@@ -434,7 +374,6 @@ QFX_HD int bwd_dec(const Row& R, int h, int w, BwdDec& d) {
   const int w1 = w - d.s * Q4;
   const int u = Q4 - 1 - w1;
   if (u >= (1 << (h - 1))) {                                 // tree item
-    if (h <= 2) return 0;                                    // nodes of 2 and 4 cells: forward subtrees
     d.lp = blen32((uint32_t)u);
     d.P = 1 << d.lp;
     d.off = R.N / 2 - 2 * d.P;
