@@ -188,18 +188,6 @@ struct Eng {
 QFT_HD qc* side_ptr(const Eng& e, int s) { return s ? e.side1 : e.side0; }
 QFT_HD qc* lo_ptr(const Eng& e, int s) { return s ? e.lo1 : e.lo0; }
 
-// Store of one cell; GM (large-row kernels: the scratch row is in global
-// memory and is read again only by a later launch) marks it evict-first, so
-// that it does not push out of L2 input lines other tasks of the same launch
-// still read.
-template <bool GM>
-QFT_HD void st_cell(qc* p, qc v) {
-#if defined(__CUDA_ARCH__)
-  if (GM) { __stcs(p, v); return; }
-#endif
-  *p = v;
-}
-
 // L2 prefetch of one cell of a scratch row in global memory (a hint; the
 // large-row kernels give it the cells of the task a thread runs next)
 QFT_HD void prefetch_cell(const qc* p) {
@@ -334,7 +322,7 @@ QFT_HD void bwd_chunk_c(qc (&w)[1 << L], qc (&wl)[1 << L], const qc* h, const qc
 // lo = gray(ilo)) of both sides.  The cells are loaded straight from the row:
 // own cell c -> time index n = 2^j (2c+1); the IO object returns the folded
 // pair (c(n), d(n)).
-template <int L1, class IO, bool GM = false>
+template <int L1, class IO>
 QFT_HD void task_f1_big(const Eng& e, const IO& io, int j, int ilo) {
   const int b = cls_bits(e.r, j);
   const int h = b - L1;
@@ -354,21 +342,21 @@ QFT_HD void task_f1_big(const Eng& e, const IO& io, int j, int ilo) {
     const int p0 = qft_pidx(off + lo), ps = qft_pstride(h);
 #pragma unroll
     for (int t = 0; t < (1 << L1); ++t) {
-      st_cell<GM>(e.side0 + p0 + t * ps, vc[t]);
-      st_cell<GM>(e.side1 + p0 + t * ps, vs[t]);
+      e.side0[p0 + t * ps] = vc[t];
+      e.side1[p0 + t * ps] = vs[t];
     }
   } else {
 #pragma unroll
     for (int t = 0; t < (1 << L1); ++t) {
-      st_cell<GM>(e.side0 + qft_pidx(off + t * H + lo), vc[t]);
-      st_cell<GM>(e.side1 + qft_pidx(off + t * H + lo), vs[t]);
+      e.side0[qft_pidx(off + t * H + lo)] = vc[t];
+      e.side1[qft_pidx(off + t * H + lo)] = vs[t];
     }
   }
 }
 
 // The same task for a compensated class: the folded cells enter the class tree
 // as pairs (l = 0); h and l parts are stored.
-template <int L1, class IO, bool GM = false>
+template <int L1, class IO>
 QFT_HD void task_f1_big_c(const Eng& e, const IO& io, int j, int ilo) {
   const int b = cls_bits(e.r, j);
   const int h = b - L1;
@@ -391,10 +379,10 @@ QFT_HD void task_f1_big_c(const Eng& e, const IO& io, int j, int ilo) {
 #pragma unroll
   for (int t = 0; t < (1 << L1); ++t) {
     const int pi = lin ? p0 + t * ps : qft_pidx(off + t * H + lo);
-    st_cell<GM>(e.side0 + pi, vc[t]);
-    st_cell<GM>(e.side1 + pi, vs[t]);
-    st_cell<GM>(e.lo0 + pi, wc[t]);
-    st_cell<GM>(e.lo1 + pi, ws[t]);
+    e.side0[pi] = vc[t];
+    e.side1[pi] = vs[t];
+    e.lo0[pi] = wc[t];
+    e.lo1[pi] = ws[t];
   }
 }
 
@@ -915,8 +903,7 @@ QFT_HD void run_plain_task(int LF, const QftSeg& sg, const Eng& e, const IO& io,
 // the task kind is taken once per segment; the loop body is specialised, so
 // the class geometry is loop-invariant.
 // PF (large-row kernels, scratch in global memory): each DIF task first
-// prefetches the cells of the thread's next task into L2, and the F1 tasks
-// store their cells evict-first.
+// prefetches the cells of the thread's next task into L2.
 template <int L1, class IO, bool COMP = false, bool PF = false>
 QFT_HD void run_plain_segment(int LF, const QftSeg& sg, const Eng& e, const IO& io, int first, int end,
                               int step, int g) {
@@ -930,7 +917,7 @@ QFT_HD void run_plain_segment(int LF, const QftSeg& sg, const Eng& e, const IO& 
   }
   if (COMP && sg.pad[2]) {
     switch (sg.type) {
-    case QFT_SEG_F1_BIG: QFT_LOOP((task_f1_big_c<L1, IO, PF>(e, io, sg.cls, loc))) return;
+    case QFT_SEG_F1_BIG: QFT_LOOP(task_f1_big_c<L1>(e, io, sg.cls, loc)) return;
     case QFT_SEG_DIF:
 #define QFT_DIFC_CASE(LL) case LL: if (sg.side) { QFT_LOOP_PF(LL, 1, true, (task_dif_c<LL, 1>(e, sg.cls, sg.D, loc))) } else { QFT_LOOP_PF(LL, 0, true, (task_dif_c<LL, 0>(e, sg.cls, sg.D, loc))) } return;
       switch (sg.L) { QFT_DIFC_CASE(1) QFT_DIFC_CASE(2) QFT_DIFC_CASE(3) default: return; }
@@ -943,7 +930,7 @@ QFT_HD void run_plain_segment(int LF, const QftSeg& sg, const Eng& e, const IO& 
     }
   }
   switch (sg.type) {
-  case QFT_SEG_F1_BIG: QFT_LOOP((task_f1_big<L1, IO, PF>(e, io, sg.cls, loc))) break;
+  case QFT_SEG_F1_BIG: QFT_LOOP(task_f1_big<L1>(e, io, sg.cls, loc)) break;
   case QFT_SEG_F1_SMALL:
     switch (sg.L) {
     case 0: QFT_LOOP(task_f1_small<0>(e, io, sg.cls)) break;
