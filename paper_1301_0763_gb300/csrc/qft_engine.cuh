@@ -989,47 +989,6 @@ QFT_HD void run_slice_prefetch(const QftSeg& sg, const Eng& e, int loc, bool lo)
   }
 }
 
-// ------------------------------------------------- staged SLICE rounds
-// A round of a large-row SLICE launch is `nt` consecutive tasks of one CTA.
-// When they lie in one segment and one node (S >= nt), the 2^L descendant
-// columns the round reads are contiguous ranges of the padded row: a stage
-// window of kStageCols padded cells per column holds every cell the round
-// reads (halo included).  Window of column t: padded cells
-// [c0 + t ps, c0 + t ps + kStageCols), c0 = pidx(nbase + (rr0 & ~31)) minus
-// 2 on the DST side (whose halo is the previous cell), ps = pidx stride of S.
-constexpr int kStageCols = 320;   // >= 31 + nt + 1 cells (nt <= 256), padded (+ 1/16), + 2 on the DST side
-struct SliceRound {
-  int sgi, nbase, S, rr0, L, side, c0, ps;
-};
-// sgi: a segment index of the phase at or before tau0; false if the round
-// cannot be staged.
-QFT_HD bool slice_round(const QftSeg* segs, int seg0, int nseg, int ntasks, int r, int tau0, int nt, int sgi,
-                        SliceRound& g) {
-  while (sgi + 1 < seg0 + nseg && segs[sgi + 1].begin <= tau0) ++sgi;
-  const QftSeg& sg = segs[sgi];
-  g.sgi = sgi;
-  if (tau0 + nt > ntasks || tau0 + nt > sg.begin + sg.count || sg.L > 3 || nt > 256) return false;
-  const int b = cls_bits(r, sg.cls);
-  const int sb = b - sg.D;
-  if (sb < 8) return false;
-  g.S = 1 << sb;
-  const int loc0 = tau0 - sg.begin;
-  g.rr0 = loc0 & (g.S - 1);
-  if (g.rr0 + nt > g.S) return false;
-  g.nbase = cls_off(r, sg.cls) + ((loc0 >> sb) << (b - (sg.D - sg.L)));
-  g.L = sg.L;
-  g.side = sg.side;
-  g.c0 = qft_pidx(g.nbase + (g.rr0 & ~31)) - (sg.side ? 2 : 0);
-  g.ps = qft_pstride(sb);
-  return true;
-}
-// Offset in a column's stage window of the cell lane `lane` reads (halo: its
-// neighbour, the next cell for DCT, the previous one for DST).
-QFT_HD int slice_stage_index(const SliceRound& g, int lane, bool halo) {
-  const int x = (g.rr0 & 31) + lane + (halo ? (g.side ? -1 : 1) : 0);
-  return x + (x >> 4) + (g.side ? 2 : 0);   // x = -1 gives 0: the cell before the window's first task cell
-}
-
 // MAXL: the largest L the caller's plans give compensated SLICE segments (the
 // NODE kernel's sub-plans use at most 2, which keeps its registers in budget).
 template <int MAXL = 3>

@@ -45,16 +45,8 @@ cudaError_t qft_large_tab_launch(const LargeArgs& a, int64_t rows, int LF, cudaS
   return cudaGetLastError();
 }
 
-// SLICE launch: the dynamic shared memory holds the two stage buffers.
-template <bool COMP>
-static cudaError_t slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st) {
-  const size_t smem = slice_smem_bytes(COMP ? 1 : 0);
-  cudaError_t e = cudaFuncSetAttribute(k_large_slice<COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_large_slice<COMP><<<grid, kLargeNT, smem, st>>>(a, phase);
-  return cudaGetLastError();
-}
-
 cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st, int comp) {
-  return comp ? slice_launch<true>(a, phase, grid, st) : slice_launch<false>(a, phase, grid, st);
+  if (comp) k_large_slice<true><<<grid, kLargeNT, 0, st>>>(a, phase);
+  else k_large_slice<false><<<grid, kLargeNT, 0, st>>>(a, phase);
+  return cudaGetLastError();
 }

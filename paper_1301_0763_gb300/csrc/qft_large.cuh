@@ -102,196 +102,40 @@ __host__ __device__ inline size_t node_smem_bytes(int NB, int comp = 0) {
          (comp ? 4 : 2) * qft_lib::align16(8 * (size_t)node_buf_cells(NB));
 }
 
-// SLICE rounds staged in shared memory (slice_round, qft_engine.cuh): thread 0
-// copies each column's stage window (and its lo parts) with TMA bulk copies
-// completing on an mbarrier, one round ahead (two buffers).  A window ends at
-// most 40 cells past a node column, inside the smaller classes that follow it
-// in the row, and starts at most two padded cells before a side, inside the
-// row's scratch.  Other rounds load their cells directly.
-constexpr int kColCells = kStageCols;
-__host__ __device__ inline size_t slice_smem_bytes(int comp) {
-  return (size_t)2 * (comp ? 2 : 1) * 8 * kColCells * 8;
-}
-
 #ifdef QFT_NODE_TU
-// The task of lane x - (rr0 & 31) of a staged round: its descendant cells (and
-// halo) from the stage; then the backward levels, as task_slice_read(_c).
-// st: the round's columns (kColCells cells each), stl: their lo parts (COMP).
-template <int L, int SIDE, bool C>
-__device__ __forceinline__ void slice_read_staged(const qc* st, const qc* stl, const SliceRound& g, int lane,
-                                                  bool root, SliceRegs& p, qc* wl, qc* hl) {
-  const int rr = g.rr0 + lane;
-  const int lw = slice_stage_index(g, lane, false), lh = slice_stage_index(g, lane, true);
-  const bool hv = SIDE == 0 ? (rr + 1 < g.S) : (rr >= 1);
-#pragma unroll
-  for (int t = 0; t < (1 << L); ++t) {
-    p.w[t] = st[t * kColCells + lw];
-    if (C) wl[t] = stl[t * kColCells + lw];
-  }
-  if (hv) {
-#pragma unroll
-    for (int t = 1; t < (1 << L); ++t) {
-      p.h[t] = st[t * kColCells + lh];
-      if (C) hl[t] = stl[t * kColCells + lh];
-    }
-  }
-  p.hv = hv;
-  p.base = g.nbase + (rr << L);
-  qc w[1 << L];
-#pragma unroll
-  for (int t = 0; t < (1 << L); ++t) w[t] = p.w[t];
-  if (C) {
-    qc wlo[1 << L];
-#pragma unroll
-    for (int t = 0; t < (1 << L); ++t) wlo[t] = wl[t];
-    bwd_chunk_c<L, SIDE>(w, wlo, p.h, hl, hv);
-#pragma unroll
-    for (int t = 0; t < (1 << L); ++t) wl[t] = wlo[t];
-  } else {
-    bwd_chunk<L, SIDE>(w, p.h, hv);
-  }
-#pragma unroll
-  for (int t = 0; t < (1 << L); ++t) p.w[t] = w[t];
-  (void)root;
-}
-
-// SLICE phase above the node depth: reads copy sg.pad[0], writes copy
-// sg.pad[1]; rounds staged in shared memory where they can be (see above).
+// SLICE phase above the node depth: reads copy sg.pad[0], writes copy sg.pad[1].
 template <bool COMP>
 __global__ void __launch_bounds__(kLargeNT, QFT_SLICE_MINB) k_large_slice(LargeArgs a, int phase) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ int s_staged[2];
   const QftLargePlan* P = a.plan;
   const QftLargePhase ph = P->phases[phase];
   const int64_t row = blockIdx.y;
   const int t0 = blockIdx.x * (kLargeNT * kLargeTPT);
-  const int tid = threadIdx.x;
-  constexpr int kBufCells = (COMP ? 2 : 1) * 8 * kColCells;
-  qc* stage = reinterpret_cast<qc*>(smem);
-  if (tid == 0) {
-    mbar_init(smem_u32(&mbar[0]), 1);
-    mbar_init(smem_u32(&mbar[1]), 1);
-    fence_mbar_init();
-  }
-  // thread 0: stage round k into buffer k & 1 if its geometry and addresses allow
-  const auto issue = [&](int k) {
-    const int bf = k & 1;
-    SliceRound g;
-    bool ok = slice_round(P->segs, ph.seg0, ph.nseg, ph.ntasks, a.r, t0 + k * kLargeNT, kLargeNT, ph.seg0, g);
-    const QftSeg* sg = ok ? &P->segs[g.sgi] : nullptr;
-    const bool lo = ok && COMP && sg->pad[2];
-    const qc* A = nullptr;
-    const qc* Al = nullptr;
-    if (ok) {
-      const Eng es = large_eng(a, sg->pad[0], row);
-      A = side_ptr(es, g.side);
-      Al = lo ? lo_ptr(es, g.side) : nullptr;
-      const int ps = g.ps;
-      A += g.c0;
-      if (lo) Al += g.c0;
-      // every column start (the stride is a multiple of 16 bytes) and the stage are 16-byte aligned
-      ok = ((uintptr_t)A & 15) == 0 && (!lo || ((uintptr_t)Al & 15) == 0) && ((ps * 8) & 15) == 0 &&
-           (smem_u32(stage) & 15) == 0;
-      if (ok) {
-        const uint32_t bytes = kColCells * 8;
-        const int ncol = 1 << g.L;
-        fence_proxy_async_smem();
-        mbar_expect_tx(smem_u32(&mbar[bf]), bytes * ncol * (lo ? 2 : 1));
-        for (int t = 0; t < ncol; ++t) {
-          bulk_g2s(smem_u32(stage + bf * kBufCells + t * kColCells), A + t * ps, bytes, smem_u32(&mbar[bf]));
-          if (lo)
-            bulk_g2s(smem_u32(stage + bf * kBufCells + 8 * kColCells + t * kColCells), Al + t * ps, bytes,
-                     smem_u32(&mbar[bf]));
-        }
-      }
-    }
-    s_staged[bf] = ok ? 1 : 0;
-  };
-  __syncthreads();
-  if (tid == 0) {
-    issue(0);
-    if (kLargeTPT > 1) issue(1);
-  }
-  __syncthreads();
-  uint32_t parity[2] = {0, 0};
   int sgi = ph.seg0;
   const int sge = ph.seg0 + ph.nseg;
   for (int k = 0; k < kLargeTPT; ++k) {
-    const int tau0 = t0 + k * kLargeNT;
-    if (tau0 >= ph.ntasks) break;
-    const int bf = k & 1;
-    const bool staged = s_staged[bf] != 0;
-    if (staged) {
-      const uint64_t w0 = global_ns();
-      bool ok = true;
-      while (!mbar_try_wait(smem_u32(&mbar[bf]), parity[bf])) {
-        if (global_ns() - w0 > a.wait_ns) { ok = false; break; }
-      }
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-          if (a.status) atomicExch(a.status, QFT_ERR_TIMEOUT);
-          // copies in flight write this CTA's shared memory: wait for both buffers (bounded) before leaving
-          for (int q = 0; q < 2; ++q) {
-            if (!s_staged[q]) continue;
-            const uint64_t w1 = global_ns();
-            while (!mbar_try_wait(smem_u32(&mbar[q]), parity[q]) && global_ns() - w1 < kWaitLimitNs) {
-            }
-          }
-        }
-        __syncthreads();
-        return;
-      }
-      parity[bf] ^= 1;
+    const int tau = t0 + k * kLargeNT + (int)threadIdx.x;
+    if (tau >= ph.ntasks) break;
+    while (sgi + 1 < sge && P->segs[sgi + 1].begin <= tau) ++sgi;
+    const QftSeg sg = P->segs[sgi];
+    const Eng es = large_eng(a, sg.pad[0], row);
+    const Eng ed = large_eng(a, sg.pad[1], row);
+    // the cells of this thread's next task go to L2 while this one is read
+    const int taun = tau + kLargeNT;
+    if (QFT_LARGE_PF && k + 1 < kLargeTPT && taun < ph.ntasks && taun < sg.begin + sg.count)
+      run_slice_prefetch(sg, es, taun - sg.begin, COMP && sg.pad[2]);
+    if (COMP && sg.pad[2]) {
+      SliceRegsC s;
+      run_slice_read_c(sg, es, tau - sg.begin, s);
+      run_slice_write_c(sg, ed, s);
+    } else {
+      SliceRegs s;
+      run_slice_read(sg, es, tau - sg.begin, s);
+      run_slice_write(sg, ed, s);
     }
-    const int tau = tau0 + tid;
-    SliceRegsC s;
-    bool have = false;
-    int si = sgi;
-    if (tau < ph.ntasks) {
-      while (si + 1 < sge && P->segs[si + 1].begin <= tau) ++si;
-      const QftSeg& sg = P->segs[si];
-      const bool comp = COMP && sg.pad[2];
-      s.root = sg.D == sg.L;
-      if (staged) {
-        SliceRound g;
-        slice_round(P->segs, ph.seg0, ph.nseg, ph.ntasks, a.r, tau0, kLargeNT, ph.seg0, g);
-        const qc* st = stage + bf * kBufCells;
-        const qc* stl = st + 8 * kColCells;
-#define QFT_SRS(LL, SD)                                                                           \
-  if (comp) slice_read_staged<LL, SD, COMP>(st, stl, g, tid, s.root, s.p, s.wl, s.hl);           \
-  else slice_read_staged<LL, SD, false>(st, stl, g, tid, s.root, s.p, s.wl, s.hl);
-        switch (sg.L * 2 + sg.side) {
-        case 2: QFT_SRS(1, 0) break;
-        case 3: QFT_SRS(1, 1) break;
-        case 4: QFT_SRS(2, 0) break;
-        case 5: QFT_SRS(2, 1) break;
-        case 6: QFT_SRS(3, 0) break;
-        case 7: QFT_SRS(3, 1) break;
-        default: break;
-        }
-#undef QFT_SRS
-      } else {
-        const Eng es = large_eng(a, sg.pad[0], row);
-        if (comp) run_slice_read_c(sg, es, tau - sg.begin, s);
-        else run_slice_read(sg, es, tau - sg.begin, s.p);
-      }
-      have = true;
-    }
-    __syncthreads();   // every thread has read buffer bf: it takes round k + 2
-    if (tid == 0 && k + 2 < kLargeTPT && t0 + (k + 2) * kLargeNT < ph.ntasks) issue(k + 2);
-    if (have) {
-      const QftSeg& sg = P->segs[si];
-      const Eng ed = large_eng(a, sg.pad[1], row);
-      if (COMP && sg.pad[2]) run_slice_write_c(sg, ed, s);
-      else run_slice_write(sg, ed, s.p);
-    }
-    sgi = si;
   }
 }
-#endif  // QFT_NODE_TU
 
-#ifdef QFT_NODE_TU
+
 // NODE phase: blockIdx.x = node group (over all subs), blockIdx.y = row.  The
 // group's cells [base, base + group * 2^nb) of one side (copy A) are loaded
 // into shared memory, the sub-plan runs on them, and they are written to copy

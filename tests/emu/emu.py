@@ -62,8 +62,6 @@ def load():
     lib.emu_plan_info.argtypes = [ctypes.c_int, ip, ip, ip, ip]
     lib.emu_c2c_large.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.emu_r2c_large.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int]
-    lib.emu_slice_stage_check.argtypes = [ctypes.c_int] * 5
-    lib.emu_slice_stage_check.restype = ctypes.c_int64
     _lib = lib
     return lib
 

@@ -346,53 +346,3 @@ extern "C" int emu_r2c_large(int N, int64_t batch, const float* in, float* out, 
   }
   return 0;
 }
-
-// Staged SLICE rounds of the large-row path (slice_round / slice_stage_index,
-// the index logic of the kernel's shared-memory staging): for every SLICE
-// phase of the plan of length 2^r (LB, node size NB, J compensated classes),
-// every CTA (4 rounds of nt tasks) and every staged round, each cell a lane
-// reads through the stage must be the padded cell task_slice_read reads
-// directly, every stage index inside the window, every window inside its side
-// (two cells before the DST side allowed) and 16-byte aligned.  Returns the
-// number of staged rounds, or a negative code at the first failure.
-extern "C" int64_t emu_slice_stage_check(int r, int LB, int NB, int J, int nt) {
-  QftTune t = qft_default_tune(r);
-  t.L1 = 3;
-  t.LB = LB;
-  if (qft_build_large_plan(r, t, NB, 512, &g_lp, J) != 0) return -1;
-  const int N = 1 << r;
-  const int side_len = qft_side_len(N);
-  int64_t staged = 0;
-  for (int p = 0; p < g_lp.nphase; ++p) {
-    const QftLargePhase& ph = g_lp.phases[p];
-    if (ph.kind != QFT_LPH_SLICE) continue;
-    for (int t0 = 0; t0 < ph.ntasks; t0 += 4 * nt)
-      for (int k = 0; k < 4; ++k) {
-        SliceRound g;
-        if (!slice_round(g_lp.segs, ph.seg0, ph.nseg, ph.ntasks, r, t0 + k * nt, nt, ph.seg0, g)) continue;
-        ++staged;
-        const QftSeg& sg = g_lp.segs[g.sgi];
-        for (int c = 0; c < (1 << g.L); ++c) {
-          const int w0 = g.c0 + c * g.ps;
-          if (w0 & 1) return -2;                                   // 16-byte alignment
-          if (w0 < (g.side ? -2 : 0) || w0 + kStageCols > side_len) return -3;
-        }
-        for (int lane = 0; lane < nt; ++lane) {
-          const int tau = t0 + k * nt + lane;
-          const int b = cls_bits(r, sg.cls), sb = b - sg.D, S = 1 << sb, nb = b - (sg.D - sg.L);
-          const int loc = tau - sg.begin, q = loc >> sb, rr = loc & (S - 1);
-          const int nbase = cls_off(r, sg.cls) + (q << nb);
-          if (nbase != g.nbase || rr != g.rr0 + lane) return -4;
-          const bool hv = sg.side == 0 ? (rr + 1 < S) : (rr >= 1);
-          const int hoff = sg.side == 0 ? rr + 1 : rr - 1;
-          const int iw = slice_stage_index(g, lane, false), ih = slice_stage_index(g, lane, true);
-          if (iw < 0 || iw >= kStageCols || (hv && (ih < 0 || ih >= kStageCols))) return -5;
-          for (int c = 0; c < (1 << g.L); ++c) {
-            if (qft_pidx(nbase + c * S + rr) != g.c0 + c * g.ps + iw) return -6;
-            if (hv && c >= 1 && qft_pidx(nbase + c * S + hoff) != g.c0 + c * g.ps + ih) return -7;
-          }
-        }
-      }
-  }
-  return staged;
-}

@@ -206,21 +206,3 @@ def test_dct0_dst0_bit_exact(lg, rows):
     dfull = np.zeros((rows, N // 2 + 1))
     dfull[:, 1:-1] = d
     assert bits_equal(S, orc.dst0(dfull, N, fp32=True)[:, 1:-1].astype(np.float32))
-
-
-@pytest.mark.parametrize("r", range(15, 25))
-def test_staged_slice_rounds_read_the_direct_cells(r):
-    """The large-row SLICE kernel stages a round's descendant columns in shared
-    memory (slice_round / slice_stage_index).  For every SLICE phase of the
-    plans (LB 1..3, node sizes 2^10..2^12, plain and compensated), every staged
-    round and lane: the staged cell is the one the direct load reads, halo
-    included; every window lies inside its side and is 16-byte aligned."""
-    J0 = max(0, (r - 14) // 2) if r >= 16 else 0
-    total = 0
-    for LB in (1, 2, 3):
-        for NB in (10, 11, 12):
-            for J in sorted({0, J0}):
-                v = emu.load().emu_slice_stage_check(r, LB, NB, J, 256)
-                assert v >= 0 or v == -1, (r, LB, NB, J, v)   # -1: the planner rejects the schedule
-                total += max(v, 0)
-    assert total > 0
