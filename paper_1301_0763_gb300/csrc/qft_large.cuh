@@ -104,33 +104,87 @@ __host__ __device__ inline size_t node_smem_bytes(int NB, int comp = 0) {
 
 #ifdef QFT_NODE_TU
 // SLICE phase above the node depth: reads copy sg.pad[0], writes copy sg.pad[1].
+// Output store of one warp of SLICE tasks whose 2^L-cell outputs are one
+// contiguous run (lane i at base0 + i 2^L): through a per-warp buffer
+// (hb/lb: 32 (2^L + 1) cells each), so that store j writes cells
+// base0 + 32 j + lane, 32 consecutive cells per store instead of one cell of
+// each of 32 lanes 2^L cells apart.  The cells and values are those of
+// task_slice_write(_c) (the rounded h + l for a class output, `root`).
+template <int L, bool C>
+__device__ __forceinline__ void slice_write_warp(const QftSeg& sg, const Eng& ed, const SliceRegs& p, const qc* wl,
+                                                 bool root, qc* hb, qc* lb, int lane, int base0) {
+  constexpr int W = (1 << L) + 1;
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) {
+    hb[lane * W + t] = (C && root) ? cadd(p.w[t], wl[t]) : p.w[t];
+    if (C && !root) lb[lane * W + t] = wl[t];
+  }
+  __syncwarp();
+  qc* A = side_ptr(ed, sg.side);
+  qc* Al = lo_ptr(ed, sg.side);
+#pragma unroll
+  for (int j = 0; j < (1 << L); ++j) {
+    const int idx = j * 32 + lane;
+    const int o = (idx >> L) * W + (idx & ((1 << L) - 1));
+    const int pi = qft_pidx(base0 + idx);
+    A[pi] = hb[o];
+    if (C && !root) Al[pi] = lb[o];
+  }
+  __syncwarp();   // the buffer is reused by the next round
+}
+
 template <bool COMP>
 __global__ void __launch_bounds__(kLargeNT, QFT_SLICE_MINB) k_large_slice(LargeArgs a, int phase) {
+  constexpr int kW = 9 * 32;                     // cells of a warp's buffer (L <= 3)
+  __shared__ qc s_hb[kLargeNT / 32][kW];
+  __shared__ qc s_lb[COMP ? kLargeNT / 32 : 1][COMP ? kW : 1];
   const QftLargePlan* P = a.plan;
   const QftLargePhase ph = P->phases[phase];
   const int64_t row = blockIdx.y;
   const int t0 = blockIdx.x * (kLargeNT * kLargeTPT);
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   int sgi = ph.seg0;
   const int sge = ph.seg0 + ph.nseg;
   for (int k = 0; k < kLargeTPT; ++k) {
     const int tau = t0 + k * kLargeNT + (int)threadIdx.x;
-    if (tau >= ph.ntasks) break;
-    while (sgi + 1 < sge && P->segs[sgi + 1].begin <= tau) ++sgi;
+    if (t0 + k * kLargeNT >= ph.ntasks) break;   // uniform over the CTA
+    const bool active = tau < ph.ntasks;
+    if (active)
+      while (sgi + 1 < sge && P->segs[sgi + 1].begin <= tau) ++sgi;
     const QftSeg sg = P->segs[sgi];
-    const Eng es = large_eng(a, sg.pad[0], row);
+    const bool comp = COMP && sg.pad[2];
+    SliceRegsC s;
+    if (active) {
+      const Eng es = large_eng(a, sg.pad[0], row);
+      // the cells of this thread's next task go to L2 while this one is read
+      const int taun = tau + kLargeNT;
+      if (QFT_LARGE_PF && k + 1 < kLargeTPT && taun < ph.ntasks && taun < sg.begin + sg.count)
+        run_slice_prefetch(sg, es, taun - sg.begin, comp);
+      if (comp) run_slice_read_c(sg, es, tau - sg.begin, s);
+      else run_slice_read(sg, es, tau - sg.begin, s.p);
+    }
+    // the warp's outputs form one contiguous run: store them coalesced
+    const int base0 = __shfl_sync(0xffffffffu, s.p.base, 0);
+    const int sg0 = __shfl_sync(0xffffffffu, sgi, 0);
+    const bool run = __all_sync(0xffffffffu, active && sgi == sg0 && s.p.base == base0 + (lane << sg.L));
     const Eng ed = large_eng(a, sg.pad[1], row);
-    // the cells of this thread's next task go to L2 while this one is read
-    const int taun = tau + kLargeNT;
-    if (QFT_LARGE_PF && k + 1 < kLargeTPT && taun < ph.ntasks && taun < sg.begin + sg.count)
-      run_slice_prefetch(sg, es, taun - sg.begin, COMP && sg.pad[2]);
-    if (COMP && sg.pad[2]) {
-      SliceRegsC s;
-      run_slice_read_c(sg, es, tau - sg.begin, s);
-      run_slice_write_c(sg, ed, s);
-    } else {
-      SliceRegs s;
-      run_slice_read(sg, es, tau - sg.begin, s);
-      run_slice_write(sg, ed, s);
+    if (run) {
+      const bool root = comp && sg.D == sg.L;
+      qc* hb = s_hb[wq];
+      qc* lb = COMP ? &s_lb[wq][0] : hb;
+#define QFT_SWW(LL)                                                                        \
+  if (comp) slice_write_warp<LL, COMP>(sg, ed, s.p, s.wl, root, hb, lb, lane, base0);     \
+  else slice_write_warp<LL, false>(sg, ed, s.p, s.wl, false, hb, lb, lane, base0);
+      switch (sg.L) {
+      case 1: QFT_SWW(1) break;
+      case 2: QFT_SWW(2) break;
+      case 3: QFT_SWW(3) break;
+      default: break;
+      }
+#undef QFT_SWW
+    } else if (active) {
+      if (comp) run_slice_write_c(sg, ed, s);
+      else run_slice_write(sg, ed, s.p);
     }
   }
 }
