@@ -52,6 +52,9 @@ constexpr int kLargeTPT = 4;    // tasks per thread per CTA in those kernels
 #ifndef QFT_LARGE_PF
 #define QFT_LARGE_PF 1
 #endif
+#ifndef QFT_SLICE_PF
+#define QFT_SLICE_PF QFT_LARGE_PF
+#endif
 
 __device__ __forceinline__ Eng large_eng(const LargeArgs& a, int copy, int64_t row) {
   Eng e;
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(kLargeNT, QFT_SLICE_MINB) k_large_slice(LargeA
       const Eng es = large_eng(a, sg.pad[0], row);
       // the cells of this thread's next task go to L2 while this one is read
       const int taun = tau + kLargeNT;
-      if (QFT_LARGE_PF && k + 1 < kLargeTPT && taun < ph.ntasks && taun < sg.begin + sg.count)
+      if (QFT_SLICE_PF && k + 1 < kLargeTPT && taun < ph.ntasks && taun < sg.begin + sg.count)
         run_slice_prefetch(sg, es, taun - sg.begin, comp);
       if (comp) run_slice_read_c(sg, es, tau - sg.begin, s);
       else run_slice_read(sg, es, tau - sg.begin, s.p);
