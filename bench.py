@@ -210,7 +210,7 @@ def run_gpu(args):
     zin = torch.randn(ELEMS, 2, dtype=torch.float32, device=dev, generator=gen).view(torch.complex64).view(ELEMS)
     zout = torch.empty_like(zin)
     t_tune = time.perf_counter()
-    plans = {lg: qft.Plan(1 << lg, ELEMS >> lg, autotune=tune) for lg in logs}
+    plans = {lg: qft.Plan(1 << lg, ELEMS >> lg, autotune=tune, in_place=args.in_place) for lg in logs}
     tune_s = time.perf_counter() - t_tune
 
     def step(evs=None):
@@ -331,7 +331,10 @@ def run_gpu(args):
                            "sizes_not_yet_supported": [f"2^{l}" for l in CONFIG_LOGS if l not in logs],
                            "l2": "inputs (2 GiB) larger than L2, no flush",
                            "schedules": schedules, "autotune": tune, "autotune_s": round(tune_s, 2),
-                           "compensated_classes": comp},
+                           "compensated_classes": comp,
+                           "large_row_scratch": "one copy (in-place backward levels)" if args.in_place
+                           else "two copies",
+                           "scratch_bytes": {f"2^{lg}": plans[lg].scratch_bytes() for lg in logs}},
                 "gflops_5nlog2n": round(gflops, 1),
                 "frac_of_hbm": round(value / peak, 4),
                 "rel_err_vs_fp64": {"max": err_max, "mean": float(np.nanmean(err_mean)) if len(err_mean) > 1 else None, "rows": len(err_mean) - 1},
@@ -723,6 +726,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true", help="default schedules instead of autotuned ones")
+    ap.add_argument("--in-place", action="store_true",
+                    help="large rows on the one-scratch schedule (QFT_PLAN_IN_PLACE)")
     ap.add_argument("--sizes", default="", help="comma-separated log2 N subset (profiling runs)")
     ap.add_argument("--elems-log2", type=int, default=28,
                     help="complex elements per size (28 = the benchmark; smaller for profiler captures)")

@@ -68,6 +68,7 @@ typedef struct qft_plan_s* qft_plan;
 /* plan creation flags */
 #define QFT_PLAN_AUTOTUNE 1u   /* time candidate schedules at creation and keep the fastest */
 #define QFT_PLAN_FP32_PLAIN 2u /* n >= 2^16: evaluate every class tree in plain FP32 (see below)  */
+#define QFT_PLAN_IN_PLACE 4u   /* n > 2^14: one scratch copy of the class data (in-place backward levels) */
 
 /* status codes */
 #define QFT_OK 0
@@ -107,6 +108,17 @@ typedef struct qft_plan_s* qft_plan;
  *          keeps the error near 5e-6 for every n up to 2^24 at a cost in
  *          throughput; qft_plan_comp_classes reports J.  QFT_PLAN_FP32_PLAIN
  *          turns this off (J = 0: the plain FP32 evaluation of the recursion).
+ *   In place (QFT_PLAN_IN_PLACE, Sec. 6.1: every function of the improved QFT
+ *          returns as many values as it takes (eqs qft_42/43), which makes an
+ *          in-place evaluation possible).  For n > 2^14 the plan keeps one
+ *          scratch copy of each row's class data instead of two: the backward
+ *          levels above the node depth overwrite the cells they read, leaving
+ *          the class outputs in a bit-reversed order that the final combine
+ *          reads, and the only extra memory is a halo copy of 8 cells per 256
+ *          tasks of a level (plus the C/S tables); qft_plan_scratch_bytes
+ *          reports the size.  Same results, bit for bit, as without the flag.
+ *          For n <= 2^14 the flag changes nothing: each row is transformed in
+ *          place in shared memory.
  * The plan owns the FP32 secant table (Sec. 6.1, N/4 entries) and every
  * scratch buffer; it allocates them here, on the current CUDA device, and
  * frees them in qft_plan_destroy.  Executions must run on that device.
@@ -124,8 +136,8 @@ int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype
  *                 offsets[0] == 0 and offsets[i+1]-offsets[i] == 2^log2n[i].
  *   log2n_host    count int32 entries (host memory), each in [1, 24].
  *   flags         0, QFT_PLAN_AUTOTUNE (each length class is tuned on its own
- *                 row count before the graph is captured) and/or
- *                 QFT_PLAN_FP32_PLAIN (as for qft_plan_create).
+ *                 row count before the graph is captured), QFT_PLAN_FP32_PLAIN
+ *                 and QFT_PLAN_IN_PLACE (as for qft_plan_create).
  * Data layout: one packed complex buffer for input and one for output.
  * Supported: QFT_KIND_C2C, QFT_DTYPE_F32.
  */
@@ -277,6 +289,13 @@ int qft_plan_withhold_next_copy(qft_plan plan);
 
 /* Last CUDA error recorded by the plan (a cudaError_t value, 0 if none). */
 int qft_plan_last_cuda_error(qft_plan plan);
+
+/* Bytes of device scratch the plan holds for its transforms (the large-row
+ * path's class-data copies, lo parts, C/S tables and halo copies; ragged plans:
+ * the sum over their lengths; 0 for n <= 2^14), or a negative QFT_ERR_* code
+ * (bytes may be null).  The secant table and the plan's small descriptors are
+ * not counted. */
+int qft_plan_scratch_bytes(qft_plan plan, int64_t* bytes);
 
 /* Launch geometry chosen for the plan: threads per CTA, CTAs, dynamic shared
  * memory bytes, and the number of kernel launches one execute issues. */

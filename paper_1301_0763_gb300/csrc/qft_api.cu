@@ -62,6 +62,7 @@ static void free_resources(qft_plan p) {
   p->d_fx = nullptr;
   free(p->large_host);
   p->d_plan = nullptr; p->d_sec = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->large_host = nullptr;
+  p->scratch_bytes = 0;
 }
 
 // (Re)builds the schedule of a plan of length 2^r >= 4 for the given tile
@@ -86,7 +87,10 @@ static int plan_schedule(qft_plan p, QftTune t, int threads, int node_log2, int 
     if (t.LF < qft_lib::kLargeMinLF) return QFT_ERR_INVALID_N;   // the scratch holds tables for LF >= 3
     QftLargePlan* lp = (QftLargePlan*)malloc(sizeof(QftLargePlan));
     if (!lp) return QFT_ERR_CUDA;
-    if (qft_build_large_plan(r, t, node_log2, node_nt, lp, p->comp_j) != 0) { free(lp); return QFT_ERR_INVALID_N; }
+    if (qft_build_large_plan(r, t, node_log2, node_nt, lp, p->comp_j, p->inplace) != 0) {
+      free(lp);
+      return QFT_ERR_INVALID_N;
+    }
     if (!p->d_large) e = cudaMalloc(&p->d_large, sizeof(QftLargePlan));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_large, lp, sizeof(QftLargePlan), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { free(lp); return qft_set_cuda(p, e); }
@@ -101,13 +105,15 @@ static int plan_schedule(qft_plan p, QftTune t, int threads, int node_log2, int 
 
 // Fills a freshly allocated plan for `batch` rows of length 2^r: schedule,
 // constant table and scratch.  On failure everything it allocated is freed.
-static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype, int plain = 0) {
+static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype, int plain = 0, int inplace = 0) {
   p->magic = kMagic; p->kind = kind; p->dtype = dtype; p->n = int64_t(1) << r; p->batch = batch; p->r = r;
   p->d_plan = nullptr; p->d_sec = nullptr; p->last_cuda = cudaSuccess; p->last_stream = nullptr;
   p->large_host = nullptr; p->d_large = nullptr; p->scratch = nullptr; p->scratch_rows = 0; p->side_len = 0;
+  p->scratch_bytes = 0;
   p->chunk_rows = 0;
   p->large_tab = 0;
   p->comp_j = 0;
+  p->inplace = inplace && r > qft_lib::kMaxRowLog2 ? 1 : 0;
   p->grid = 0; p->threads = 0; p->smem = 0;
   p->nclasses = 0; p->classes = nullptr; p->d_offsets = nullptr; p->d_args = nullptr; p->h_args = nullptr;
   p->graph = nullptr; p->gexec = nullptr; p->graph_kernels = 0;
@@ -148,10 +154,13 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype, int 
       // the largest classes run on compensated pairs unless the plan asks for plain FP32
       p->comp_j = plain ? 0 : qft_comp_classes(r);
       const int64_t items = kind == QFT_KIND_C2C ? batch : (batch + 1) / 2;   // real kinds: row pairs
-      // two copies of the class data plus the FINAL tasks' C/S tables, plus
-      // the lo parts of both copies for compensated plans
-      const int64_t per_row = (p->comp_j > 0 ? 4 : 2) * 2 * (int64_t)p->side_len * 8 +
-                              (int64_t)qft_lib::large_tab_cells((int)N, qft_lib::kLargeMinLF) * 8;
+      // two copies of the class data (one for in-place plans, plus the halo
+      // copies of the SLICE block edges) plus the FINAL tasks' C/S tables,
+      // plus the lo parts of the copies and halos for compensated plans
+      const int64_t lo = p->comp_j > 0 ? 2 : 1;
+      const int64_t per_row = (p->inplace ? lo : 2 * lo) * 2 * (int64_t)p->side_len * 8 +
+                              (int64_t)qft_lib::large_tab_cells((int)N, qft_lib::kLargeMinLF) * 8 +
+                              (p->inplace ? lo * (int64_t)QFT_IP_EDGES(r) * QFT_IP_HALO * 8 : 0);
       int64_t rows = qft_lib::kScratchBudget / per_row;
       if (rows > items) rows = items;
       if (rows > 65535) rows = 65535;
@@ -160,6 +169,7 @@ static int plan_init(qft_plan p, int r, int64_t batch, int kind, int dtype, int 
       p->threads = 256;
       p->large_tab = (r <= 20 && rows >= 64) ? 1 : 0;
       if (items > 0) e = cudaMalloc(&p->scratch, (size_t)(rows * per_row));
+      if (items > 0 && e == cudaSuccess) p->scratch_bytes = rows * per_row;
       if (e != cudaSuccess) { int rc = qft_set_cuda(p, e); free_resources(p); return rc; }
     }
     // large rows: the NODE kernel at 256 threads (two CTAs per SM) where the
@@ -369,7 +379,7 @@ static int plan_create_fixed(qft_plan* out, int64_t n, int64_t batch, int kind, 
 extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind, int dtype, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
   *out = nullptr;
-  if ((flags & ~(QFT_PLAN_AUTOTUNE | QFT_PLAN_FP32_PLAIN)) != 0) return QFT_ERR_INVALID_ARG;
+  if ((flags & ~(QFT_PLAN_AUTOTUNE | QFT_PLAN_FP32_PLAIN | QFT_PLAN_IN_PLACE)) != 0) return QFT_ERR_INVALID_ARG;
   if (kind != QFT_KIND_C2C && kind != QFT_KIND_R2C && kind != QFT_KIND_DCT0 && kind != QFT_KIND_DST0)
     return QFT_ERR_DTYPE;
   if (dtype == QFT_DTYPE_I16) return plan_create_fixed(out, n, batch, kind, flags);
@@ -384,7 +394,8 @@ extern "C" int qft_plan_create(qft_plan* out, int64_t n, int64_t batch, int kind
 
   qft_plan p = new (std::nothrow) qft_plan_s();
   if (!p) return QFT_ERR_CUDA;
-  int rc = plan_init(p, r, batch, kind, dtype, (flags & QFT_PLAN_FP32_PLAIN) ? 1 : 0);
+  int rc = plan_init(p, r, batch, kind, dtype, (flags & QFT_PLAN_FP32_PLAIN) ? 1 : 0,
+                     (flags & QFT_PLAN_IN_PLACE) ? 1 : 0);
   if (rc != QFT_OK) { delete p; return rc; }
   if (flags & QFT_PLAN_AUTOTUNE) {
     rc = autotune(p);
@@ -447,7 +458,7 @@ extern "C" int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host
                                       int64_t count, int kind, int dtype, unsigned flags) {
   if (!out) return QFT_ERR_NULLPTR;
   *out = nullptr;
-  if ((flags & ~(QFT_PLAN_AUTOTUNE | QFT_PLAN_FP32_PLAIN)) != 0) return QFT_ERR_INVALID_ARG;
+  if ((flags & ~(QFT_PLAN_AUTOTUNE | QFT_PLAN_FP32_PLAIN | QFT_PLAN_IN_PLACE)) != 0) return QFT_ERR_INVALID_ARG;
   if (kind != QFT_KIND_C2C || dtype != QFT_DTYPE_F32) return QFT_ERR_DTYPE;
   if (count < 0 || count > (int64_t(1) << 31)) return QFT_ERR_INVALID_BATCH;
   if (count > 0 && (!offsets_host || !log2n_host)) return QFT_ERR_NULLPTR;
@@ -476,7 +487,8 @@ extern "C" int qft_plan_create_ragged(qft_plan* out, const int64_t* offsets_host
     C.r = r; C.count = per_r[r]; C.d_rows = nullptr;
     C.sub = new (std::nothrow) qft_plan_s();
     if (!C.sub) { rc = QFT_ERR_CUDA; break; }
-    rc = plan_init(C.sub, r, C.count, kind, dtype, (flags & QFT_PLAN_FP32_PLAIN) ? 1 : 0);
+    rc = plan_init(C.sub, r, C.count, kind, dtype, (flags & QFT_PLAN_FP32_PLAIN) ? 1 : 0,
+                   (flags & QFT_PLAN_IN_PLACE) ? 1 : 0);
     if (rc != QFT_OK) { delete C.sub; C.sub = nullptr; break; }
     if (flags & QFT_PLAN_AUTOTUNE) {
       rc = autotune(C.sub);
@@ -579,6 +591,7 @@ extern "C" int qft_filter_create(qft_plan* out, int64_t n, int64_t batch, int64_
   const size_t bytes = (size_t)channels * qft_filter_parts() * (size_t)(n / 2 + 1) * 8;
   cudaError_t e = cudaMalloc(&p->scratch, bytes);
   if (e != cudaSuccess) { rc = qft_set_cuda(p, e); free_resources(p); delete p; return rc; }
+  p->scratch_bytes = (int64_t)bytes;
   register_plan(p);
   *out = p;
   return QFT_OK;
@@ -709,6 +722,15 @@ extern "C" int qft_plan_sync_status(qft_plan p) {
   return st;
 }
 
+extern "C" int qft_plan_scratch_bytes(qft_plan p, int64_t* bytes) {
+  int rc = plan_check(p);
+  if (rc != QFT_OK) return rc;
+  int64_t b = p->scratch_bytes;
+  for (int c = 0; c < p->nclasses; ++c) b += p->classes[c].sub->scratch_bytes;
+  if (bytes) *bytes = b;
+  return QFT_OK;
+}
+
 extern "C" int qft_plan_comp_classes(qft_plan p) {
   int rc = plan_check(p);
   if (rc != QFT_OK) return rc;
@@ -752,7 +774,11 @@ extern "C" int qft_plan_info(qft_plan p, int* threads, int* ctas, int* smem_byte
   if (ctas) *ctas = p->large_host ? (int)(p->large_host->node_ctas * (crow < items ? crow : items))
                                   : p->grid;
   if (smem_bytes) *smem_bytes = (int)p->smem;
-  if (launches) *launches = p->classes ? 1 + p->graph_kernels : (p->large_host ? (int)(p->large_host->nphase * chunks) : 1);
+  int per_chunk = p->large_host ? p->large_host->nphase : 0;
+  if (p->large_host && p->large_host->inplace)   // the halo copy before each in-place SLICE level of several blocks
+    for (int i = 0; i < p->large_host->nphase; ++i)
+      per_chunk += p->large_host->phases[i].kind == QFT_LPH_SLICE && p->large_host->phases[i].ntasks > QFT_IP_TASKS;
+  if (launches) *launches = p->classes ? 1 + p->graph_kernels : (p->large_host ? (int)(per_chunk * chunks) : 1);
   return QFT_OK;
 }
 

@@ -161,6 +161,23 @@ QFT_HD int qft_pstride(int h) { return (1 << h) + (1 << (h - 4)); }
 QFT_HD int qft_side_len(int N) { return (qft_pidx(N / 2) + 2) & ~1; }
 QFT_HD int cls_off(int r, int j) { return (1 << (r - 1)) - (1 << (r - 1 - j)); }
 QFT_HD int cls_bits(int r, int j) { return r - 2 - j; }
+// Bit reversal of the low n bits of x (1 <= n <= 31).
+QFT_HD unsigned qft_brev(unsigned x, int n) {
+#if defined(__CUDA_ARCH__)
+  return __brev(x) >> (32 - n);
+#else
+  unsigned y = 0;
+  for (int i = 0; i < n; ++i) y |= ((x >> i) & 1u) << (n - 1 - i);
+  return y;
+#endif
+}
+// In-place backward order of a node of 2^sb cells whose top dp backward levels
+// ran in place: natural index i sits at bitrev_dp(i mod 2^dp) 2^(sb-dp) +
+// floor(i / 2^dp).  One in-place level over descendants t of 2^s cells keeps
+// output u of chunk i in descendant bitrev(u)'s cell i, which composes to this.
+QFT_HD int ip_perm(int i, int dp, int sb) {
+  return dp > 0 ? (int)((qft_brev((unsigned)i & ((1u << dp) - 1u), dp) << (sb - dp)) | (unsigned)(i >> dp)) : i;
+}
 QFT_HD unsigned invgray(unsigned g) {
   g ^= g >> 1; g ^= g >> 2; g ^= g >> 4; g ^= g >> 8; g ^= g >> 16;
   return g;
@@ -183,10 +200,32 @@ struct Eng {
   qc* tabS;           // S_Mt(k), k in [1, Mt/2-1], or null
   qc* lo0;            // lo parts of the DCT side's compensated cells (same indexing), or null
   qc* lo1;            // lo parts of the DST side
+  // Layout of the class outputs.  lay_nb = 0: natural order.  Otherwise (the
+  // large-row path's in-place schedule, node size 2^lay_nb, F1 levels lay_l1)
+  // the backward levels above each class's node depth ran in place and left
+  // the outputs in the order cls_pos gives.
+  int lay_nb = 0;
+  int lay_l1 = 0;
 };
 
 QFT_HD qc* side_ptr(const Eng& e, int s) { return s ? e.side1 : e.side0; }
 QFT_HD qc* lo_ptr(const Eng& e, int s) { return s ? e.lo1 : e.lo0; }
+
+// Backward levels of class j that ran in place (0: natural order): the levels
+// above its node depth, max(b - NB, L1) for the classes the large-row path
+// cuts into nodes (b > L1), none for the others.
+QFT_HD int cls_lay_depth(const Eng& e, int j) {
+  const int b = cls_bits(e.r, j);
+  if (e.lay_nb == 0 || b <= e.lay_l1) return 0;
+  return b - e.lay_nb > e.lay_l1 ? b - e.lay_nb : e.lay_l1;
+}
+// Padded position of stored output i of class j (DCT: k = i, DST: k = i + 1).
+// Indices past the class (dummy reads of the chain walks) stay natural.
+QFT_HD int cls_pos(const Eng& e, int j, int i) {
+  const int b = cls_bits(e.r, j);
+  const int d = cls_lay_depth(e, j);
+  return qft_pidx(cls_off(e.r, j) + ((d > 0 && i < (1 << b)) ? ip_perm(i, d, b) : i));
+}
 
 // L2 prefetch of one cell of a scratch row in global memory (a hint; the
 // large-row kernels give it the cells of the task a thread runs next)
@@ -671,11 +710,179 @@ QFT_HD void task_slice_write_c(const Eng& e, SliceRegsC& s) {
   }
 }
 
+// ------------------------------------------------- in-place SLICE (large rows)
+// The large-row path's one-scratch schedule runs the backward levels above the
+// node depth in place.  A task reads the cells of its chunk i (natural index)
+// in the 2^L descendants of its node, at the positions the levels below left
+// them (ip_perm), and writes output u of the chunk over descendant
+// bitrev_L(u)'s cell: the cells it writes are the cells it read.  So a block
+// of tasks can read, wait for its own reads (a CTA barrier), and write; only
+// the neighbour cells of a chunk (eqs qft_38B/C) at a block edge belong to
+// another block, and those are copied out before the level starts
+// (task_slice_ip_halo).
+struct SliceIp {
+  qc w[1 << QFT_MAX_LB];    // outputs (h parts)
+  qc wl[1 << QFT_MAX_LB];   // lo parts (compensated segments)
+  int nbase;                // class-level index of the node
+  int sb;                   // log2 of a descendant's cells
+  int prr;                  // position of chunk i within a descendant
+  bool root;                // compensated class output: stored rounded, h + l
+};
+
+// Neighbour cells (descendants t = 1 .. 2^L-1) of the chunk that task `loc`
+// of segment (j, D, L) at a block edge takes from the other block: for the
+// DCT side the cells of chunk i = loc's (the task before it needs them), for
+// the DST side those of chunk i - 1 (loc needs them).  Nothing when loc starts
+// a node.  Returns whether it copied.
+template <int SIDE>
+QFT_HD bool task_slice_ip_halo(const Eng& e, int j, int D, int L, int loc, qc* xh, qc* xl) {
+  const int b = cls_bits(e.r, j);
+  const int sb = b - D;
+  const int rr = loc & ((1 << sb) - 1);
+  if (rr == 0) return false;
+  const int nbase = cls_off(e.r, j) + ((loc >> sb) << (sb + L));
+  const int ph = ip_perm(SIDE == 0 ? rr : rr - 1, cls_lay_depth(e, j) - D, sb);
+  const qc* A = side_ptr(e, SIDE);
+  const qc* Al = lo_ptr(e, SIDE);
+  for (int t = 1; t < (1 << L); ++t) {
+    const int pi = qft_pidx(nbase + (t << sb) + ph);
+    xh[t] = A[pi];
+    if (xl) xl[t] = Al[pi];
+  }
+  return true;
+}
+
+// xh / xl: the chunk's neighbour cells from the halo copy (a task at a block
+// edge), or null to read them from the scratch.
+template <int L, int SIDE, bool C>
+QFT_HD void task_slice_ip_read(const Eng& e, int j, int D, int tau, const qc* xh, const qc* xl, SliceIp& s) {
+  const int b = cls_bits(e.r, j);
+  const int sb = b - D;
+  const int S = 1 << sb;
+  const int rr = tau & (S - 1);
+  const int dp = cls_lay_depth(e, j) - D;
+  const int nbase = cls_off(e.r, j) + ((tau >> sb) << (sb + L));
+  const int prr = ip_perm(rr, dp, sb);
+  const qc* A = side_ptr(e, SIDE);
+  const qc* Al = lo_ptr(e, SIDE);
+  qc w[1 << L], wl[1 << L], h[1 << L], hl[1 << L];
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) {
+    const int pi = qft_pidx(nbase + (t << sb) + prr);
+    w[t] = A[pi];
+    if (C) wl[t] = Al[pi];
+  }
+  const bool hv = SIDE == 0 ? (rr + 1 < S) : (rr >= 1);
+  if (hv) {
+    if (xh) {
+#pragma unroll
+      for (int t = 1; t < (1 << L); ++t) {
+        h[t] = xh[t];
+        if (C) hl[t] = xl[t];
+      }
+    } else {
+      const int ph = ip_perm(SIDE == 0 ? rr + 1 : rr - 1, dp, sb);
+#pragma unroll
+      for (int t = 1; t < (1 << L); ++t) {
+        const int pi = qft_pidx(nbase + (t << sb) + ph);
+        h[t] = A[pi];
+        if (C) hl[t] = Al[pi];
+      }
+    }
+  }
+  if (C) bwd_chunk_c<L, SIDE>(w, wl, h, hl, hv);
+  else bwd_chunk<L, SIDE>(w, h, hv);
+#pragma unroll
+  for (int t = 0; t < (1 << L); ++t) {
+    s.w[t] = w[t];
+    if (C) s.wl[t] = wl[t];
+  }
+  s.nbase = nbase;
+  s.sb = sb;
+  s.prr = prr;
+  s.root = C && D == L;
+}
+
+template <int L, int SIDE, bool C>
+QFT_HD void task_slice_ip_write(const Eng& e, const SliceIp& s) {
+  qc* A = side_ptr(e, SIDE);
+  qc* Al = lo_ptr(e, SIDE);
+#pragma unroll
+  for (int u = 0; u < (1 << L); ++u) {
+    const int pi = qft_pidx(s.nbase + ((int)qft_brev((unsigned)u, L) << s.sb) + s.prr);
+    if (C && s.root) {
+      A[pi] = cadd(s.w[u], s.wl[u]);   // class output, rounded once
+    } else {
+      A[pi] = s.w[u];
+      if (C) Al[pi] = s.wl[u];
+    }
+  }
+}
+
+// Block edge k (task B = k QFT_IP_TASKS) of an in-place SLICE phase whose
+// segments are segs[seg0, seg0 + nseg): copies the neighbour cells that cross
+// it into xh (and their lo parts into xl, if xl and the segment is
+// compensated).  Returns false where the edge is not inside one node.
+QFT_HD bool slice_ip_edge(const QftSeg* segs, int seg0, int nseg, const Eng& e, int k, qc* xh, qc* xl) {
+  const int B = k * QFT_IP_TASKS;
+  int s = seg0;
+  while (s + 1 < seg0 + nseg && segs[s + 1].begin <= B) ++s;
+  const QftSeg& sg = segs[s];
+  if (B - 1 < sg.begin || B >= sg.begin + sg.count) return false;
+  qc* l = sg.pad[2] ? xl : nullptr;
+  return sg.side ? task_slice_ip_halo<1>(e, sg.cls, sg.D, sg.L, B - sg.begin, xh, l)
+                 : task_slice_ip_halo<0>(e, sg.cls, sg.D, sg.L, B - sg.begin, xh, l);
+}
+// Offset (in halo cells) of the copy a task at position x of block bx takes
+// its neighbour cells from, or -1 (they are in its own block): the last task
+// of a block on the DCT side, the first on the DST side.
+QFT_HD int slice_ip_halo_slot(int side, int x, int bx) {
+  if (side == 0 && x == QFT_IP_TASKS - 1) return (bx + 1) * QFT_IP_HALO;
+  if (side == 1 && x == 0) return bx * QFT_IP_HALO;
+  return -1;
+}
+
+// dispatch on the segment's L (1..3), side and compensation
+QFT_HD void run_slice_ip_read(const QftSeg& sg, const Eng& e, int loc, const qc* xh, const qc* xl, bool comp,
+                              SliceIp& s) {
+#define QFT_IPR(LL)                                                                       \
+  case LL:                                                                                \
+    if (comp) {                                                                           \
+      if (sg.side) task_slice_ip_read<LL, 1, true>(e, sg.cls, sg.D, loc, xh, xl, s);      \
+      else task_slice_ip_read<LL, 0, true>(e, sg.cls, sg.D, loc, xh, xl, s);              \
+    } else {                                                                              \
+      if (sg.side) task_slice_ip_read<LL, 1, false>(e, sg.cls, sg.D, loc, xh, xl, s);     \
+      else task_slice_ip_read<LL, 0, false>(e, sg.cls, sg.D, loc, xh, xl, s);             \
+    }                                                                                     \
+    break;
+  switch (sg.L) {
+    QFT_IPR(1) QFT_IPR(2) QFT_IPR(3)
+    default: break;
+  }
+#undef QFT_IPR
+}
+
+QFT_HD void run_slice_ip_write(const QftSeg& sg, const Eng& e, bool comp, const SliceIp& s) {
+#define QFT_IPW(LL)                                                                       \
+  case LL:                                                                                \
+    if (comp) {                                                                           \
+      if (sg.side) task_slice_ip_write<LL, 1, true>(e, s); else task_slice_ip_write<LL, 0, true>(e, s);   \
+    } else {                                                                              \
+      if (sg.side) task_slice_ip_write<LL, 1, false>(e, s); else task_slice_ip_write<LL, 0, false>(e, s); \
+    }                                                                                     \
+    break;
+  switch (sg.L) {
+    QFT_IPW(1) QFT_IPW(2) QFT_IPW(3)
+    default: break;
+  }
+#undef QFT_IPW
+}
+
 // --------------------------------------------------------------- FINAL
 // Class output O_j(k) of side s: DCT k in [0, P_j) at off+k; DST k in [1, P_j]
 // at off+k-1.
 QFT_HD qc cls_out(const Eng& e, int s, int j, int k) {
-  return side_ptr(e, s)[qft_pidx(cls_off(e.r, j) + k - s)];
+  return side_ptr(e, s)[cls_pos(e, j, k - s)];
 }
 
 // C_M(k) for M = 2^m, k in [0, M/2]: walk down the dct recursion (recording
@@ -701,7 +908,7 @@ QFT_RARE qc chain_c(const Eng& e, int m, int k) {
     const int op = (int)((ops >> (2 * i)) & 3);
     const int mm = m - i;                             // log2 of this level's periodization
     const int j = e.r - mm;
-    qc o = e.side0[qft_pidx(cls_off(e.r, j) + k)];    // O_j(k) (k = M/4 reads a neighbour, unused)
+    qc o = e.side0[cls_pos(e, j, k)];    // O_j(k) (k = M/4 reads a neighbour, unused)
     if (op == 1) o = mkc(-o.x, -o.y);
     const qc w = cadd(v, o);
     v = op == 2 ? v : w;
@@ -732,7 +939,7 @@ QFT_RARE qc chain_s(const Eng& e, int m, int k) {
     const int j = e.r - mm;
     const int P = 1 << (mm - 2);
     const int kk = k & (P - 1 + P);        // keeps the dummy index inside class j's cells
-    const qc o = e.side1[qft_pidx(cls_off(e.r, j) + (kk > 0 ? kk - 1 : 0))];
+    const qc o = e.side1[cls_pos(e, j, kk > 0 ? kk - 1 : 0)];
     const int op = (int)((ops >> i) & 1);
     const qc negv = mkc(-v.x, -v.y);
     const qc w = cadd(op ? negv : v, o);   // S(k) = E + O  or  S(M/2-k) = O - E
@@ -762,7 +969,7 @@ QFT_RARE void tab_level_c(const Eng& e, int m, int lane, int nl) {
   const int j = e.r - m;
   for (int k = lane; k < M / 4; k += nl) {
     const qc E = e.tabC[k];
-    const qc O = e.side0[qft_pidx(cls_off(e.r, j) + k)];
+    const qc O = e.side0[cls_pos(e, j, k)];
     e.tabC[k] = cadd(E, O);
     e.tabC[M / 2 - k] = csub(E, O);
   }
@@ -777,11 +984,11 @@ QFT_RARE void tab_level_s(const Eng& e, int m, int lane, int nl) {
   const int j = e.r - m;
   for (int k = 1 + lane; k < M / 4; k += nl) {
     const qc E = e.tabS[k];
-    const qc O = e.side1[qft_pidx(cls_off(e.r, j) + k - 1)];
+    const qc O = e.side1[cls_pos(e, j, k - 1)];
     e.tabS[k] = cadd(E, O);
     e.tabS[M / 2 - k] = csub(O, E);
   }
-  if (lane == 0) e.tabS[M / 4] = e.side1[qft_pidx(cls_off(e.r, j) + M / 4 - 1)];
+  if (lane == 0) e.tabS[M / 4] = e.side1[cls_pos(e, j, M / 4 - 1)];
 }
 
 // Regular frequency orbit: k0 in [1, N/2^(LF+1)).  The task builds C and S

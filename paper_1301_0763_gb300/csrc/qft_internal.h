@@ -74,9 +74,11 @@ struct qft_plan_s {
   QftLargePlan* d_large;
   qc_storage* scratch;
   int64_t scratch_rows;       // rows the scratch copies hold
+  int64_t scratch_bytes;      // bytes of `scratch`
   int64_t chunk_rows;         // rows per launch sequence (0: scratch_rows); fewer keep a chunk's copies in L2
   int large_tab;              // 1: TAB launch + FINAL from C/S tables; 0: FINAL walks the class recursion
   int comp_j;                 // classes (per side) whose trees run on compensated pairs (large rows only)
+  int inplace;                // large rows: one scratch copy, in-place SLICE levels (QFT_PLAN_IN_PLACE)
   int side_len;
   // ragged plans (qft_plan_create_ragged)
   int nclasses;

@@ -50,3 +50,18 @@ cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cud
   else k_large_slice<false><<<grid, kLargeNT, 0, st>>>(a, phase);
   return cudaGetLastError();
 }
+
+cudaError_t qft_large_slice_ip_launch(const LargeArgs& a, int phase, int nblk, int64_t rows, cudaStream_t st,
+                                      int comp) {
+  if (nblk > 1) {   // block edges 1 .. nblk-1
+    const dim3 hg((unsigned)((nblk - 1 + 255) / 256), (unsigned)rows);
+    if (comp) k_large_halo<true><<<hg, 256, 0, st>>>(a, phase, nblk);
+    else k_large_halo<false><<<hg, 256, 0, st>>>(a, phase, nblk);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 g((unsigned)nblk, (unsigned)rows);
+  if (comp) k_large_slice_ip<true><<<g, QFT_IP_TASKS, 0, st>>>(a, phase);
+  else k_large_slice_ip<false><<<g, QFT_IP_TASKS, 0, st>>>(a, phase);
+  return cudaGetLastError();
+}

@@ -24,6 +24,13 @@ struct LargeArgs {
   int withhold;               // test: each NODE CTA's first window copy is not issued (its wait runs out)
   qc* loA;                    // lo parts of the compensated cells of copy A (same layout), or null
   qc* loB;                    // lo parts of copy B
+  // one-scratch (in-place) plans: class outputs in the in-place order, and the
+  // halo copies of the SLICE levels' block edges (ip_edges * QFT_IP_HALO cells a row)
+  int lay_nb;                 // node size log2 of the layout (0: natural order, two copies)
+  int lay_l1;
+  int ip_edges;
+  qc* haloH;
+  qc* haloL;                  // lo parts of the halo cells (compensated plans), or null
 };
 
 
@@ -35,6 +42,9 @@ cudaError_t qft_large_node_prepare(int nt, size_t smem, int comp);
 cudaError_t qft_large_node_launch(const LargeArgs& a, int64_t rows, int64_t items, int nt, size_t smem,
                                   cudaStream_t st, int comp);
 cudaError_t qft_large_slice_launch(const LargeArgs& a, int phase, dim3 grid, cudaStream_t st, int comp);
+// in-place SLICE phase of `nblk` blocks: the halo copy of its block edges, then the level
+cudaError_t qft_large_slice_ip_launch(const LargeArgs& a, int phase, int nblk, int64_t rows, cudaStream_t st,
+                                      int comp);
 cudaError_t qft_large_tab_launch(const LargeArgs& a, int64_t rows, int LF, cudaStream_t st);
 
 namespace {
@@ -69,6 +79,8 @@ __device__ __forceinline__ Eng large_eng(const LargeArgs& a, int copy, int64_t r
   qc* lb = copy ? a.loB : a.loA;
   e.lo0 = lb ? lb + row * 2 * (int64_t)a.side_len : nullptr;
   e.lo1 = lb ? e.lo0 + a.side_len : nullptr;
+  e.lay_nb = a.lay_nb;
+  e.lay_l1 = a.lay_l1;
   return e;
 }
 
@@ -192,6 +204,57 @@ __global__ void __launch_bounds__(kLargeNT, QFT_SLICE_MINB) k_large_slice(LargeA
   }
 }
 
+
+// In-place SLICE phase (one-scratch plans), blockIdx.y = row.
+// k_large_halo: thread k copies the neighbour cells that cross block edge k
+// (1 <= k < nblk) into the row's halo copy, before any block of the level runs.
+template <bool COMP>
+__global__ void __launch_bounds__(256) k_large_halo(LargeArgs a, int phase, int nblk) {
+  const QftLargePlan* P = a.plan;
+  const QftLargePhase ph = P->phases[phase];
+  const int k = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (k >= nblk) return;
+  const int64_t row = blockIdx.y;
+  const Eng e = large_eng(a, 0, row);
+  const int64_t off = (row * a.ip_edges + k) * QFT_IP_HALO;
+  slice_ip_edge(P->segs, ph.seg0, ph.nseg, e, k, a.haloH + off, COMP ? a.haloL + off : nullptr);
+}
+
+// k_large_slice_ip: block blockIdx.x = tasks [QFT_IP_TASKS bx, + QFT_IP_TASKS)
+// of the phase.  Every thread reads its task's cells and runs its levels,
+// the CTA barrier orders all reads of the block before its writes, and each
+// task writes over the cells it read.  Within the block, thread i takes task
+// x = transpose of i over (2^dp x QFT_IP_TASKS/2^dp), dp the levels already
+// in place below the first task's segment: a warp's lanes then take chunks
+// 2^dp apart, whose cells are adjacent.
+template <bool COMP>
+__global__ void __launch_bounds__(QFT_IP_TASKS, 2) k_large_slice_ip(LargeArgs a, int phase) {
+  const QftLargePlan* P = a.plan;
+  const QftLargePhase ph = P->phases[phase];
+  const int64_t row = blockIdx.y;
+  const Eng e = large_eng(a, 0, row);
+  const int t0 = blockIdx.x * QFT_IP_TASKS;
+  const int sge = ph.seg0 + ph.nseg;
+  int sgi = ph.seg0;
+  while (sgi + 1 < sge && P->segs[sgi + 1].begin <= t0) ++sgi;
+  int dp = cls_lay_depth(e, P->segs[sgi].cls) - P->segs[sgi].D;
+  dp = dp < 0 ? 0 : (dp > 8 ? 8 : dp);
+  const int cols = QFT_IP_TASKS >> dp;
+  const int x = (((int)threadIdx.x % cols) << dp) | ((int)threadIdx.x / cols);
+  const int tau = t0 + x;
+  const bool active = tau < ph.ntasks;
+  SliceIp s;
+  if (active) {
+    while (sgi + 1 < sge && P->segs[sgi + 1].begin <= tau) ++sgi;
+    const QftSeg& sg = P->segs[sgi];
+    const int slot = slice_ip_halo_slot(sg.side, x, blockIdx.x);
+    const int64_t hoff = row * a.ip_edges * QFT_IP_HALO + slot;
+    run_slice_ip_read(sg, e, tau - sg.begin, slot >= 0 ? a.haloH + hoff : nullptr,
+                      (COMP && slot >= 0) ? a.haloL + hoff : nullptr, COMP && sg.pad[2], s);
+  }
+  __syncthreads();
+  if (active) run_slice_ip_write(P->segs[sgi], e, COMP && P->segs[sgi].pad[2], s);
+}
 
 // NODE phase: blockIdx.x = node group (over all subs), blockIdx.y = row.  The
 // group's cells [base, base + group * 2^nb) of one side (copy A) are loaded
@@ -376,10 +439,12 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
   LargeArgs a;
   a.plan = p->d_large;
   a.gsec = p->d_sec;
-  // scratch: copy A | copy B | C/S tables | (compensated plans) lo parts of A | of B
+  // scratch: copy A | copy B | C/S tables | (compensated plans) lo parts of A | of B;
+  // in-place plans: copy A | C/S tables | (lo parts of A) | halos | (their lo parts)
+  const int ip = H.inplace;
   const size_t copy_cells = (size_t)p->scratch_rows * 2 * p->side_len;
   a.scrA = reinterpret_cast<qc*>(p->scratch);
-  a.scrB = a.scrA + copy_cells;
+  a.scrB = ip ? a.scrA : a.scrA + copy_cells;
   a.side_len = p->side_len;
   a.r = p->r;
   a.status = p->d_status;
@@ -389,11 +454,17 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
   a.tabS_off = ((1 << p->r) >> H.LF) / 2 + 1;
   // tables after the two copies; a CTA builds one row's tables, which pays off
   // only with enough rows of moderate length (the plan's large_tab)
-  qc* tab0 = a.scrB + copy_cells;
+  qc* tab0 = (ip ? a.scrA : a.scrB) + copy_cells;
   a.tab = p->large_tab ? tab0 : nullptr;
   qc* lo0 = tab0 + (size_t)p->scratch_rows * qft_lib::large_tab_cells(1 << p->r, qft_lib::kLargeMinLF);
   a.loA = comp ? lo0 : nullptr;
-  a.loB = comp ? lo0 + copy_cells : nullptr;
+  a.loB = comp ? (ip ? lo0 : lo0 + copy_cells) : nullptr;
+  a.lay_nb = ip ? H.NB : 0;
+  a.lay_l1 = ip ? H.L1 : 0;
+  a.ip_edges = QFT_IP_EDGES(p->r);
+  qc* halo0 = lo0 + (comp ? copy_cells : 0);
+  a.haloH = ip ? halo0 : nullptr;
+  a.haloL = ip && comp ? halo0 + (size_t)p->scratch_rows * a.ip_edges * QFT_IP_HALO : nullptr;
   const size_t node_smem = node_smem_bytes(H.NB, comp);
   // node kernel: 512 threads (one CTA per SM) unless the plan asks for 256
   const int node_nt = p->node_nt == 256 ? 256 : 512;
@@ -418,7 +489,8 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
         const unsigned bx = (unsigned)((P.ntasks + kLargeNT * kLargeTPT - 1) / (kLargeNT * kLargeTPT));
         if (P.kind == QFT_LPH_SLICE) {
           qft_time_begin(p, st, QFT_KERNEL_SLICE);
-          e = qft_large_slice_launch(a, ph, dim3(bx, (unsigned)rows), st, comp);
+          e = ip ? qft_large_slice_ip_launch(a, ph, (P.ntasks + QFT_IP_TASKS - 1) / QFT_IP_TASKS, rows, st, comp)
+                 : qft_large_slice_launch(a, ph, dim3(bx, (unsigned)rows), st, comp);
           if (e != cudaSuccess) return qft_set_cuda(p, e);
         } else {
           qft_time_begin(p, st, QFT_KERNEL_GLOBAL);

@@ -114,5 +114,15 @@ struct QftLargePlan {
   int32_t nsub;
   int32_t node_ctas;              // CTAs per row in the node phase
   int32_t max_slice_nodes;        // largest per-node task count of a node sub-plan SLICE phase
+  int32_t inplace;                // 1: one scratch copy; the SLICE levels run in place (QFT_IP_TASKS a block)
+  int32_t pad_;
   QftNodeSub subs[QFT_LP_MAX_SUB];
 };
+// Tasks of one block of an in-place SLICE level (one CTA): a block reads all
+// its cells before it writes any; blocks exchange only the neighbour cells at
+// their edges, through a halo copy of QFT_IP_HALO cells per block edge.
+#define QFT_IP_TASKS 256
+#define QFT_IP_HALO 8
+// block edges per row any in-place SLICE level of a row of 2^r can have (its
+// tasks number at most N/2)
+#define QFT_IP_EDGES(r) (((1 << (r)) / 2) / QFT_IP_TASKS + 2)

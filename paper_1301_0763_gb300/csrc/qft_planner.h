@@ -227,7 +227,10 @@ static inline int qft_comp_classes(int r) { return r >= 16 ? (r - 14) / 2 : 0; }
 // Schedule for rows longer than one CTA's shared memory (see qft_plan.h).
 // NB: log2 of the largest node (group) a CTA transforms in shared memory.
 // J: classes 0..J-1 run on compensated pairs (their segments get pad[2] = 1).
-static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_threads, QftLargePlan* P, int J = 0) {
+// inplace: one scratch copy; every phase reads and writes copy A (the global
+// SLICE levels run in place, at most 3 a phase).
+static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_threads, QftLargePlan* P, int J = 0,
+                                       int inplace = 0) {
   memset(P, 0, sizeof *P);
   if (r < 4 || r > 24 || NB < 4 || NB > 14) return -1;
   if (t.L1 < 1 || t.L1 > 4 || t.LS < 1 || t.LS > 4 || t.LL < 0 || t.LL > 4 || t.LB < 1 || t.LB > 4 ||
@@ -238,6 +241,8 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
   P->r = r; P->L1 = t.L1; P->LF = LF; P->NB = NB;
   if (J < 0 || J > r - 2) return -1;
   P->comp_classes = J;
+  P->inplace = inplace ? 1 : 0;
+  const int LBg = inplace && t.LB > 3 ? 3 : t.LB;   // backward levels of a global SLICE phase
   const int ncls = r - 1;
   int depth[32], Dn[32], nsl[32], cur[32];
   bool big[32];
@@ -246,8 +251,8 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
     big[j] = b > t.L1;
     depth[j] = big[j] ? t.L1 : 0;
     Dn[j] = big[j] ? (b - NB > t.L1 ? b - NB : t.L1) : 0;
-    nsl[j] = big[j] ? (Dn[j] + t.LB - 1) / t.LB : 0;   // global SLICE phases of class j
-    cur[j] = (nsl[j] & 1) ? 1 : 0;                     // copy holding the node outputs
+    nsl[j] = big[j] ? (Dn[j] + LBg - 1) / LBg : 0;     // global SLICE phases of class j
+    cur[j] = (!inplace && (nsl[j] & 1)) ? 1 : 0;       // copy holding the node outputs
   }
   auto add_seg = [&](int type, int side, int cls, int L, int D, int count, int src, int dst) -> bool {
     if (P->nseg >= QFT_LP_MAX_SEGS) return false;
@@ -369,7 +374,7 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
       if (P->max_slice_nodes > node_threads) return -1;
     }
   P->node_ctas = cta;
-  // ---- global SLICE phases (remainder first), ping-pong between the copies
+  // ---- global SLICE phases (remainder first), ping-pong between the copies, or in place in copy A
   for (int j = 0; j < ncls; ++j) depth[j] = big[j] ? Dn[j] : 0;
   for (;;) {
     int Ls[32];
@@ -377,8 +382,8 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
     for (int j = 0; j < ncls; ++j) {
       Ls[j] = 0;
       if (!big[j] || depth[j] == 0) continue;
-      Ls[j] = depth[j] % t.LB;
-      if (Ls[j] == 0) Ls[j] = t.LB;
+      Ls[j] = depth[j] % LBg;
+      if (Ls[j] == 0) Ls[j] = LBg;
       any = true;
     }
     if (!any) break;
@@ -387,10 +392,10 @@ static inline int qft_build_large_plan(int r, QftTune t, int NB, int node_thread
     for (int side = 0; side < 2; ++side)
       for (int j = 0; j < ncls; ++j)
         if (Ls[j] > 0 && !add_seg(QFT_SEG_SLICE, side, j, Ls[j], depth[j], 1 << (r - 2 - j - Ls[j]),
-                                  cur[j], cur[j] ^ 1)) return -1;
+                                  cur[j], inplace ? 0 : cur[j] ^ 1)) return -1;
     end_phase();
     for (int j = 0; j < ncls; ++j)
-      if (Ls[j] > 0) { depth[j] -= Ls[j]; cur[j] ^= 1; }
+      if (Ls[j] > 0) { depth[j] -= Ls[j]; if (!inplace) cur[j] ^= 1; }
   }
   for (int j = 0; j < ncls; ++j)
     if (big[j] && cur[j] != 0) return -1;   // every class output must end in copy A

@@ -28,6 +28,7 @@ DTYPE_F32, DTYPE_F16, DTYPE_BF16, DTYPE_I16 = 0, 1, 2, 3
 OP_FORWARD, OP_INVERSE, OP_FORWARD_ADJOINT, OP_INVERSE_ADJOINT = 0, 1, 2, 3
 PLAN_AUTOTUNE = 1
 PLAN_FP32_PLAIN = 2
+PLAN_IN_PLACE = 4
 SCHEDULE_KEYS = ("threads", "L1", "LS", "LL", "LB", "LF", "staging", "node_log2", "node_threads", "chunk_rows")
 
 _lib = None
@@ -73,6 +74,7 @@ def load_library(path: str | None = None):
         lib.qft_static_scratch_sync_status.argtypes = [vp]
         lib.qft_plan_set_wait_limit.argtypes = [vp, i64]
         lib.qft_plan_comp_classes.argtypes = [vp]
+        lib.qft_plan_scratch_bytes.argtypes = [vp, ctypes.POINTER(i64)]
         lib.qft_plan_withhold_next_copy.argtypes = [vp]
         lib.qft_plan_schedule.argtypes = [vp, ctypes.POINTER(ci)]
         lib.qft_plan_set_schedule.argtypes = [vp, ctypes.POINTER(ci)]
@@ -102,16 +104,23 @@ class Plan:
     """A plan of `batch` transforms of length `n` (see qft_plan_create)."""
 
     def __init__(self, n: int, batch: int, kind: int = KIND_C2C, dtype: int = DTYPE_F32, device=None,
-                 autotune: bool = False, plain: bool = False):
+                 autotune: bool = False, plain: bool = False, in_place: bool = False):
         self.lib = load_library()
         self.n, self.batch, self.kind, self.dtype = int(n), int(batch), int(kind), int(dtype)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         self.handle = ctypes.c_void_p()
-        flags = (PLAN_AUTOTUNE if autotune else 0) | (PLAN_FP32_PLAIN if plain else 0)
+        flags = ((PLAN_AUTOTUNE if autotune else 0) | (PLAN_FP32_PLAIN if plain else 0) |
+                 (PLAN_IN_PLACE if in_place else 0))
         with torch.cuda.device(self.device):
             _check(self.lib.qft_plan_create(ctypes.byref(self.handle), self.n, self.batch, self.kind,
                                             self.dtype, flags), "qft_plan_create")
+
+    def scratch_bytes(self) -> int:
+        """Device scratch the plan holds (qft_plan_scratch_bytes)."""
+        b = ctypes.c_int64()
+        _check(self.lib.qft_plan_scratch_bytes(self.handle, ctypes.byref(b)), "qft_plan_scratch_bytes")
+        return int(b.value)
 
     def comp_classes(self) -> int:
         """Classes per side evaluated on compensated FP32 pairs (qft_plan_comp_classes)."""
@@ -195,7 +204,8 @@ class RaggedPlan(Plan):
     [offsets[i], offsets[i+1]) and has length 2^log2n[i].  One execute is one
     CUDA-graph launch of every length class."""
 
-    def __init__(self, offsets, log2n, device=None, autotune: bool = False, plain: bool = False):
+    def __init__(self, offsets, log2n, device=None, autotune: bool = False, plain: bool = False,
+                 in_place: bool = False):
         import numpy as np
         self.lib = load_library()
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
@@ -210,7 +220,8 @@ class RaggedPlan(Plan):
             _check(self.lib.qft_plan_create_ragged(
                 ctypes.byref(self.handle), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                 lg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.count, KIND_C2C, DTYPE_F32,
-                (PLAN_AUTOTUNE if autotune else 0) | (PLAN_FP32_PLAIN if plain else 0)),
+                (PLAN_AUTOTUNE if autotune else 0) | (PLAN_FP32_PLAIN if plain else 0) |
+                (PLAN_IN_PLACE if in_place else 0)),
                 "qft_plan_create_ragged")
 
 

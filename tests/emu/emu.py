@@ -60,8 +60,9 @@ def load():
     lib.emu_c2c_half.argtypes = [ctypes.c_int, ctypes.c_int64, up, up, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.emu_r2c.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int]
     lib.emu_plan_info.argtypes = [ctypes.c_int, ip, ip, ip, ip]
-    lib.emu_c2c_large.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
-    lib.emu_r2c_large.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int]
+    lib.emu_c2c_large.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int]
+    lib.emu_r2c_large.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     _lib = lib
     return lib
 
@@ -122,32 +123,34 @@ def plan_info(N, tune=None):
     return rc, a.value, b.value, c.value
 
 
-def c2c_large(z, op=0, plain=False, node_log2=None):
+def c2c_large(z, op=0, plain=False, node_log2=None, inplace=False):
     """The large-row launch sequence on the host; plain=True runs every class
     tree in plain FP32 instead of the library's compensated classes (node
-    groups of 2^node_log2 cells, the library's default 2^12)."""
+    groups of 2^node_log2 cells, the library's default 2^12); inplace=True runs
+    the one-scratch schedule (in-place SLICE levels)."""
     z = np.ascontiguousarray(z, dtype=np.complex64)
     N = z.shape[-1]
     if node_log2 is None:
         node_log2 = 12
     out = np.empty_like(z)
     rc = load().emu_c2c_large(N, z.size // N, _fp(z.view(np.float32)), _fp(out.view(np.float32)), op,
-                              1 if plain else 0, node_log2)
+                              1 if plain else 0, node_log2, 1 if inplace else 0)
     if rc != 0:
         raise ValueError("emulation rejected")
     return out
 
 
-def r2c_large(x, op, N, plain=False):
+def r2c_large(x, op, N, plain=False, inplace=False):
     if op in (0, 3):
         x = np.ascontiguousarray(x, dtype=np.float32)
         out = np.empty(x.shape[:-1] + (N // 2 + 1,), dtype=np.complex64)
-        rc = load().emu_r2c_large(N, x.size // N, _fp(x), _fp(out.view(np.float32)), op, 1 if plain else 0)
+        rc = load().emu_r2c_large(N, x.size // N, _fp(x), _fp(out.view(np.float32)), op, 1 if plain else 0,
+                                  1 if inplace else 0)
     else:
         x = np.ascontiguousarray(x, dtype=np.complex64)
         out = np.empty(x.shape[:-1] + (N,), dtype=np.float32)
         rc = load().emu_r2c_large(N, x.size // (N // 2 + 1), _fp(x.view(np.float32)), _fp(out), op,
-                                  1 if plain else 0)
+                                  1 if plain else 0, 1 if inplace else 0)
     if rc != 0:
         raise ValueError("emulation rejected")
     return out

@@ -213,6 +213,7 @@ static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vecto
     e.side0 = base; e.side1 = base + side_len; e.sec = gsec; e.r = LP.r; e.N = 1 << LP.r;
     e.tabC = tab.data(); e.tabS = tab.data() + ((1 << LP.r) >> LP.LF) / 2 + 1;
     e.lo0 = lb; e.lo1 = lb + side_len;
+    if (LP.inplace) { e.lay_nb = LP.NB; e.lay_l1 = LP.L1; }
     return e;
   };
   for (int ph = 0; ph < LP.nphase; ++ph) {
@@ -240,6 +241,35 @@ static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vecto
             run_plain_segment<3, IO, true>(LP.LF, sg, e, io, first, end, NT, 0);
           }
         }
+    } else if (P.kind == QFT_LPH_SLICE && LP.inplace) {
+      // in place: the halo copies first (a launch of its own), then each
+      // block reads all its tasks' cells before it writes any
+      const Eng e = eng(0);
+      const int nblk = (P.ntasks + QFT_IP_TASKS - 1) / QFT_IP_TASKS;
+      std::vector<qc> hh((size_t)(nblk + 1) * QFT_IP_HALO, mkc(NAN, NAN)), hl(hh.size(), mkc(NAN, NAN));
+      for (int k = 1; k < nblk; ++k)
+        slice_ip_edge(LP.segs, P.seg0, P.nseg, e, k, &hh[(size_t)k * QFT_IP_HALO], &hl[(size_t)k * QFT_IP_HALO]);
+      std::vector<SliceIp> regs(QFT_IP_TASKS);
+      std::vector<int> segi(QFT_IP_TASKS);
+      // odd blocks before even ones: at every edge one of the two blocks has
+      // already written when the other reads, as CTAs may run on the GPU
+      for (int it = 0; it < nblk; ++it) {
+        const int bx = it < nblk / 2 ? 2 * it + 1 : 2 * (it - nblk / 2);
+        for (int x = 0; x < QFT_IP_TASKS; ++x) {
+          const int tau = bx * QFT_IP_TASKS + x;
+          segi[x] = -1;
+          if (tau >= P.ntasks) continue;
+          int s = P.seg0;
+          while (s + 1 < P.seg0 + P.nseg && LP.segs[s + 1].begin <= tau) ++s;
+          segi[x] = s;
+          const QftSeg& sg = LP.segs[s];
+          const int slot = slice_ip_halo_slot(sg.side, x, bx);
+          run_slice_ip_read(sg, e, tau - sg.begin, slot >= 0 ? &hh[slot] : nullptr, slot >= 0 ? &hl[slot] : nullptr,
+                            sg.pad[2] != 0, regs[x]);
+        }
+        for (int x = 0; x < QFT_IP_TASKS; ++x)
+          if (segi[x] >= 0) run_slice_ip_write(LP.segs[segi[x]], e, LP.segs[segi[x]].pad[2] != 0, regs[x]);
+      }
     } else if (P.kind == QFT_LPH_SLICE) {
       for (int tau = 0; tau < P.ntasks; ++tau) {
         int s = P.seg0;
@@ -293,11 +323,13 @@ static void run_large_row(const QftLargePlan& LP, std::vector<qc>& A, std::vecto
 // op as in emu_c2c (complex64 rows)
 // plain = 1: every class tree in plain FP32 (else the library's compensated classes)
 // plain = 1: J = 0; plain < 0: J = -plain (another count, for tests)
-extern "C" int emu_c2c_large(int N, int64_t batch, const float* in, float* out, int op, int plain, int NB) {
+// inplace = 1: the one-scratch schedule (every phase in copy A)
+extern "C" int emu_c2c_large(int N, int64_t batch, const float* in, float* out, int op, int plain, int NB,
+                             int inplace) {
   int r = 0; while ((1 << r) < N) ++r;
   QftTune t = qft_default_tune(r);
   const int J = plain > 0 ? 0 : (plain < 0 ? -plain : qft_comp_classes(r));
-  if (qft_build_large_plan(r, t, NB, 512, &g_lp, J) != 0) return -2;
+  if (qft_build_large_plan(r, t, NB, 512, &g_lp, J, inplace) != 0) return -2;
   std::vector<float> gsec(N / 4 + 1, 0.f);
   qft_fill_gray_secants(r, gsec.data());
   const int side_len = qft_side_len(N);
@@ -317,11 +349,11 @@ extern "C" int emu_c2c_large(int N, int64_t batch, const float* in, float* out, 
 }
 
 // R2C family on the large path (op as in emu_r2c)
-extern "C" int emu_r2c_large(int N, int64_t batch, const float* in, float* out, int op, int plain) {
+extern "C" int emu_r2c_large(int N, int64_t batch, const float* in, float* out, int op, int plain, int inplace) {
   int r = 0; while ((1 << r) < N) ++r;
   QftTune t = qft_default_tune(r);
   const int J = plain ? 0 : qft_comp_classes(r);
-  if (qft_build_large_plan(r, t, 12, 512, &g_lp, J) != 0) return -2;
+  if (qft_build_large_plan(r, t, 12, 512, &g_lp, J, inplace) != 0) return -2;
   std::vector<float> gsec(N / 4 + 1, 0.f);
   qft_fill_gray_secants(r, gsec.data());
   const int side_len = qft_side_len(N);

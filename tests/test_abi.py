@@ -50,7 +50,7 @@ def test_host_side_argument_errors(lib):
     assert lib.qft_plan_create(ctypes.byref(h), 16, -1, 0, 0, 0) == -2
     assert lib.qft_plan_create(ctypes.byref(h), 16, 1, 7, 0, 0) == -3
     assert lib.qft_plan_create(ctypes.byref(h), 16, 1, 1, 1, 0) == -3  # R2C fp16 unsupported
-    assert lib.qft_plan_create(ctypes.byref(h), 16, 1, 0, 0, 4) == -9  # unknown flag bit
+    assert lib.qft_plan_create(ctypes.byref(h), 16, 1, 0, 0, 8) == -9  # unknown flag bit
     assert lib.qft_execute(None, 0, None, None, None) == -5
     assert lib.qft_plan_destroy(None) == 0
     for code in [0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10]:

@@ -158,7 +158,7 @@ def test_large_path_compensated_classes_small_n(lg, J):
     fp = ctypes.POINTER(ctypes.c_float)
     out = np.empty_like(z)
     assert L.emu_c2c_large(N, 2, z.view(np.float32).ctypes.data_as(fp), out.view(np.float32).ctypes.data_as(fp),
-                           0, -J, 12) == 0
+                           0, -J, 12, 0) == 0
     lib = orc._load32(True)
     lib.oracle_set_comp_classes.argtypes = [ctypes.c_int]
     lib.oracle_set_comp_classes(J)
@@ -189,6 +189,60 @@ def test_large_path_real():
     assert bits_equal(emu.r2c_large(X, 2, N), orc.rdft_adjoint(X, N, fp32=True).astype(np.float32))
     assert bits_equal(emu.r2c_large(x, 3, N), orc.irdft_adjoint(x, fp32=True).astype(np.complex64))
     assert bits_equal(emu.r2c_large(x, 0, N, plain=True), orc.rdft(x, fp32=True, comp=False).astype(np.complex64))
+
+
+# ------------------------------------------- large rows, one scratch copy
+@pytest.mark.parametrize("lg,node_log2", [(15, 12), (15, 5), (16, 8), (17, 6), (18, 12), (18, 9)])
+def test_large_path_in_place_bit_exact(lg, node_log2):
+    """The one-scratch schedule (Sec. 6.1): the SLICE levels above the node
+    depth write over the cells they read, the class outputs stay in the order
+    that leaves, the final combine reads them through it, and neighbour cells
+    cross block edges through halo copies (blocks emulated odd ones first, so
+    at every edge one block has written before the other reads).  Same bits
+    as the oracle; smaller nodes give several in-place phases a class."""
+    N = 1 << lg
+    z = inputs.normal_complex(1, N, seed=80 + lg)
+    ref = orc.cdft(z, fp32=True).astype(np.complex64)
+    assert bits_equal(emu.c2c_large(z, node_log2=node_log2, inplace=True), ref)
+    assert bits_equal(emu.c2c_large(z, plain=True, node_log2=node_log2, inplace=True),
+                      orc.cdft(z, fp32=True, comp=False).astype(np.complex64))
+
+
+@pytest.mark.parametrize("lg", [8, 10, 12])
+@pytest.mark.parametrize("J", [1, 2])
+def test_large_path_in_place_compensated_small_n(lg, J):
+    """Compensated classes on the in-place schedule at small N, nodes of 2^4
+    cells (up to eight in-place phases a class)."""
+    import ctypes
+    N = 1 << lg
+    z = inputs.normal_complex(2, N, seed=90 + lg).astype(np.complex64)
+    L = emu.load()
+    fp = ctypes.POINTER(ctypes.c_float)
+    out = np.empty_like(z)
+    assert L.emu_c2c_large(N, 2, z.view(np.float32).ctypes.data_as(fp), out.view(np.float32).ctypes.data_as(fp),
+                           0, -J, 4, 1) == 0
+    lib = orc._load32(True)
+    lib.oracle_set_comp_classes.argtypes = [ctypes.c_int]
+    lib.oracle_set_comp_classes(J)
+    try:
+        ref = orc.cdft(z, fp32=True).astype(np.complex64)
+    finally:
+        lib.oracle_set_comp_classes(-1)
+    assert bits_equal(out, ref)
+
+
+@pytest.mark.parametrize("op", [1, 2, 3])
+def test_large_path_in_place_other_ops_and_real(op):
+    N = 1 << 16
+    z = inputs.uniform_complex(2, N, seed=95 + op)
+    ref = {1: lambda: orc.icdft(z, fp32=True), 2: lambda: orc.cdft_adjoint(z, fp32=True),
+           3: lambda: orc.cdft(z, fp32=True) / N}[op]()
+    assert bits_equal(emu.c2c_large(z, op, node_log2=9, inplace=True), ref.astype(np.complex64))
+    x = inputs.normal_real(2, N, seed=98)
+    X = orc.rdft(x, fp32=True).astype(np.complex64)
+    if op == 1:
+        assert bits_equal(emu.r2c_large(x, 0, N, inplace=True), X)
+        assert bits_equal(emu.r2c_large(X, 1, N, inplace=True), orc.irdft(X, N, fp32=True).astype(np.float32))
 
 
 @pytest.mark.parametrize("lg", [2, 3, 4, 6, 9, 12, 14])
