@@ -298,6 +298,7 @@ def run_gpu(args):
         err_mean += e.tolist()
     schedules = {f"2^{lg}": plans[lg].schedule() for lg in logs}
     comp = {f"2^{lg}": comp_j[lg] for lg in logs}
+    scratch = {f"2^{lg}": plans[lg].scratch_bytes() for lg in logs}
 
     # ------------------------------------------------------------- e2e
     e2e = None
@@ -334,7 +335,7 @@ def run_gpu(args):
                            "compensated_classes": comp,
                            "large_row_scratch": "one copy (in-place backward levels)" if args.in_place
                            else "two copies",
-                           "scratch_bytes": {f"2^{lg}": plans[lg].scratch_bytes() for lg in logs}},
+                           "scratch_bytes": scratch},
                 "gflops_5nlog2n": round(gflops, 1),
                 "frac_of_hbm": round(value / peak, 4),
                 "rel_err_vs_fp64": {"max": err_max, "mean": float(np.nanmean(err_mean)) if len(err_mean) > 1 else None, "rows": len(err_mean) - 1},

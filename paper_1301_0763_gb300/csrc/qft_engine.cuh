@@ -881,8 +881,10 @@ QFT_HD void run_slice_ip_write(const QftSeg& sg, const Eng& e, bool comp, const 
 // --------------------------------------------------------------- FINAL
 // Class output O_j(k) of side s: DCT k in [0, P_j) at off+k; DST k in [1, P_j]
 // at off+k-1.
+// IP = false: the caller knows the outputs are in natural order (e.lay_nb = 0).
+template <bool IP = true>
 QFT_HD qc cls_out(const Eng& e, int s, int j, int k) {
-  return side_ptr(e, s)[cls_pos(e, j, k - s)];
+  return side_ptr(e, s)[IP ? cls_pos(e, j, k - s) : qft_pidx(cls_off(e.r, j) + k - s)];
 }
 
 // C_M(k) for M = 2^m, k in [0, M/2]: walk down the dct recursion (recording
@@ -993,7 +995,7 @@ QFT_RARE void tab_level_s(const Eng& e, int m, int lane, int nl) {
 
 // Regular frequency orbit: k0 in [1, N/2^(LF+1)).  The task builds C and S
 // on the orbit {+-k0 + m N/2^LF} level by level and emits X at 2^(LF+1) bins.
-template <int LF, class IO>
+template <int LF, class IO, bool IP = false>
 QFT_HD void task_fin_reg(const Eng& e, const IO& io, int k0) {
   qc C[1 << LF], S[1 << LF];
   int K[1 << LF];
@@ -1012,8 +1014,8 @@ QFT_HD void task_fin_reg(const Eng& e, const IO& io, int k0) {
     const int Mh = e.N >> l;    // M/2 with M = N/2^(l-1)
 #pragma unroll
     for (int i = 0; i < n; ++i) {
-      const qc oc = cls_out(e, 0, j, K[i]);
-      const qc os = cls_out(e, 1, j, K[i]);
+      const qc oc = cls_out<IP>(e, 0, j, K[i]);
+      const qc os = cls_out<IP>(e, 1, j, K[i]);
       C[n + i] = csub(C[i], oc);
       C[i] = cadd(C[i], oc);
       S[n + i] = csub(os, S[i]);
@@ -1093,10 +1095,13 @@ QFT_HD void run_plain_task(int LF, const QftSeg& sg, const Eng& e, const IO& io,
     break;
   case QFT_SEG_FIN_REG:
     switch (LF) {
-    case 0: task_fin_reg<0>(e, io, loc + 1); break;
-    case 1: task_fin_reg<1>(e, io, loc + 1); break;
-    case 2: task_fin_reg<2>(e, io, loc + 1); break;
-    case 3: task_fin_reg<3>(e, io, loc + 1); break;
+    case 0: if (e.lay_nb) task_fin_reg<0, IO, true>(e, io, loc + 1); else task_fin_reg<0, IO, false>(e, io, loc + 1); break;
+    case 1: if (e.lay_nb) task_fin_reg<1, IO, true>(e, io, loc + 1); else task_fin_reg<1, IO, false>(e, io, loc + 1); break;
+    case 2: if (e.lay_nb) task_fin_reg<2, IO, true>(e, io, loc + 1); else task_fin_reg<2, IO, false>(e, io, loc + 1); break;
+    case 3:
+      if (e.lay_nb) task_fin_reg<3, IO, true>(e, io, loc + 1);
+      else task_fin_reg<3, IO, false>(e, io, loc + 1);
+      break;
     default: break;
     }
     break;
@@ -1161,10 +1166,22 @@ QFT_HD void run_plain_segment(int LF, const QftSeg& sg, const Eng& e, const IO& 
     break;
   case QFT_SEG_FIN_REG:
     switch (LF) {
-    case 0: QFT_LOOP(task_fin_reg<0>(e, io, loc + 1)) break;
-    case 1: QFT_LOOP(task_fin_reg<1>(e, io, loc + 1)) break;
-    case 2: QFT_LOOP(task_fin_reg<2>(e, io, loc + 1)) break;
-    case 3: QFT_LOOP(task_fin_reg<3>(e, io, loc + 1)) break;
+    case 0:
+      if (e.lay_nb) { QFT_LOOP((task_fin_reg<0, IO, true>(e, io, loc + 1))) }
+      else { QFT_LOOP((task_fin_reg<0, IO, false>(e, io, loc + 1))) }
+      break;
+    case 1:
+      if (e.lay_nb) { QFT_LOOP((task_fin_reg<1, IO, true>(e, io, loc + 1))) }
+      else { QFT_LOOP((task_fin_reg<1, IO, false>(e, io, loc + 1))) }
+      break;
+    case 2:
+      if (e.lay_nb) { QFT_LOOP((task_fin_reg<2, IO, true>(e, io, loc + 1))) }
+      else { QFT_LOOP((task_fin_reg<2, IO, false>(e, io, loc + 1))) }
+      break;
+    case 3:   // the large-row path's FINAL: in-place plans read the class outputs through cls_pos
+      if (e.lay_nb) { QFT_LOOP((task_fin_reg<3, IO, true>(e, io, loc + 1))) }
+      else { QFT_LOOP((task_fin_reg<3, IO, false>(e, io, loc + 1))) }
+      break;
     default: break;
     }
     break;
