@@ -186,3 +186,33 @@ def test_in_place_ragged(q):
         seg = slice(int(off[i]), int(off[i + 1]))
         assert bits_equal(X[seg], orc.cdft(z[None, seg], fp32=True).astype(np.complex64)[0]), lg
     p.destroy()
+
+
+def test_in_place_autotuned_and_scratch_accounting(q):
+    """An autotuned in-place plan keeps the in-place schedule under every
+    candidate (same bits); scratch_bytes of a ragged plan is the sum of its
+    length classes'."""
+    N = 1 << 18
+    z = inputs.normal_complex(4, N, seed=400)
+    p = q.Plan(N, 4, in_place=True, autotune=True)
+    xin = torch.from_numpy(z).cuda()
+    out = torch.empty_like(xin)
+    p.execute(q.OP_FORWARD, xin, out)
+    torch.cuda.synchronize()
+    assert bits_equal(out.cpu().numpy(), orc.cdft(z, fp32=True).astype(np.complex64))
+    assert p.sync_status() == 0
+    one = p.scratch_bytes()
+    p.destroy()
+    p2 = q.Plan(N, 4)
+    assert one < 0.6 * p2.scratch_bytes()
+    p2.destroy()
+    small = q.Plan(1 << 12, 4, in_place=True)
+    assert small.scratch_bytes() == 0
+    small.destroy()
+    lgs = np.array([16, 12, 17], dtype=np.int32)
+    off = np.concatenate([[0], np.cumsum(1 << lgs.astype(np.int64))])
+    rp = q.RaggedPlan(off, lgs, in_place=True)
+    parts = [q.Plan(1 << 16, 1, in_place=True), q.Plan(1 << 17, 1, in_place=True)]
+    assert rp.scratch_bytes() == sum(pp.scratch_bytes() for pp in parts)
+    for pp in parts + [rp]:
+        pp.destroy()
