@@ -51,6 +51,17 @@ namespace {
 
 constexpr int kLargeNT = 256;   // threads of the GLOBAL / SLICE kernels
 constexpr int kLargeTPT = 4;    // tasks per thread per CTA in those kernels
+// tasks per thread of the F1 launch (the first phase, which reads the input
+// row), of the DIF launches and of the FINAL launch (the last phase)
+#ifndef QFT_F1_TPT
+#define QFT_F1_TPT 2
+#endif
+#ifndef QFT_DIF_TPT
+#define QFT_DIF_TPT 8
+#endif
+#ifndef QFT_FIN_TPT
+#define QFT_FIN_TPT kLargeTPT
+#endif
 // resident CTAs per SM the GLOBAL and SLICE kernels' register allocation targets
 #ifndef QFT_GLOBAL_MINB
 #define QFT_GLOBAL_MINB 2
@@ -85,17 +96,18 @@ __device__ __forceinline__ Eng large_eng(const LargeArgs& a, int copy, int64_t r
 }
 
 // GLOBAL phase (F1, DIF, FINAL): blockIdx.y = row within the chunk, blockIdx.x
-// = block of kLargeNT * kLargeTPT consecutive tasks of that row's phase.
+// = block of kLargeNT * tpt consecutive tasks of that row's phase.
 template <class FAC, int L1, bool COMP>
-__global__ void __launch_bounds__(kLargeNT, QFT_GLOBAL_MINB) k_large_global(LargeArgs a, int phase, FAC fac) {
+__global__ void __launch_bounds__(kLargeNT, QFT_GLOBAL_MINB) k_large_global(LargeArgs a, int phase, FAC fac,
+                                                                            int tpt) {
   const QftLargePlan* P = a.plan;
   const QftLargePhase ph = P->phases[phase];
   const int64_t row = blockIdx.y;
   const Eng e = large_eng(a, 0, row);
   const auto io = fac.make(a.row0 + row);
-  // this thread's tasks: T0 + k * kLargeNT, k < kLargeTPT, T0 = block start + tid
-  const int T0 = blockIdx.x * (kLargeNT * kLargeTPT) + (int)threadIdx.x;
-  const int T1 = blockIdx.x * (kLargeNT * kLargeTPT) + kLargeNT * kLargeTPT;
+  // this thread's tasks: T0 + k * kLargeNT, k < tpt, T0 = block start + tid
+  const int T0 = blockIdx.x * (kLargeNT * tpt) + (int)threadIdx.x;
+  const int T1 = blockIdx.x * (kLargeNT * tpt) + kLargeNT * tpt;
   for (int s = ph.seg0; s < ph.seg0 + ph.nseg; ++s) {
     const QftSeg sg = P->segs[s];
     if (sg.begin >= T1 || sg.begin + sg.count <= T0 - (int)threadIdx.x) continue;
@@ -494,8 +506,10 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
           if (e != cudaSuccess) return qft_set_cuda(p, e);
         } else {
           qft_time_begin(p, st, QFT_KERNEL_GLOBAL);
-          if (comp) k_large_global<FAC, qft_lib::kL1, true><<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph, fac);
-          else k_large_global<FAC, qft_lib::kL1, false><<<dim3(bx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph, fac);
+          const int tpt = ph == 0 ? QFT_F1_TPT : (ph == H.nphase - 1 ? QFT_FIN_TPT : QFT_DIF_TPT);
+          const unsigned gx = (unsigned)((P.ntasks + kLargeNT * tpt - 1) / (kLargeNT * tpt));
+          if (comp) k_large_global<FAC, qft_lib::kL1, true><<<dim3(gx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph, fac, tpt);
+          else k_large_global<FAC, qft_lib::kL1, false><<<dim3(gx, (unsigned)rows), kLargeNT, 0, st>>>(a, ph, fac, tpt);
         }
       }
       qft_time_end(p, st);
