@@ -62,6 +62,10 @@ constexpr int kLargeTPT = 4;    // tasks per thread per CTA in those kernels
 #ifndef QFT_FIN_TPT
 #define QFT_FIN_TPT kLargeTPT
 #endif
+// tasks per thread of the (two-copy) SLICE kernel
+#ifndef QFT_SLICE_TPT
+#define QFT_SLICE_TPT kLargeTPT
+#endif
 // resident CTAs per SM the GLOBAL and SLICE kernels' register allocation targets
 #ifndef QFT_GLOBAL_MINB
 #define QFT_GLOBAL_MINB 2
@@ -168,11 +172,11 @@ __global__ void __launch_bounds__(kLargeNT, QFT_SLICE_MINB) k_large_slice(LargeA
   const QftLargePlan* P = a.plan;
   const QftLargePhase ph = P->phases[phase];
   const int64_t row = blockIdx.y;
-  const int t0 = blockIdx.x * (kLargeNT * kLargeTPT);
+  const int t0 = blockIdx.x * (kLargeNT * QFT_SLICE_TPT);
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   int sgi = ph.seg0;
   const int sge = ph.seg0 + ph.nseg;
-  for (int k = 0; k < kLargeTPT; ++k) {
+  for (int k = 0; k < QFT_SLICE_TPT; ++k) {
     const int tau = t0 + k * kLargeNT + (int)threadIdx.x;
     if (t0 + k * kLargeNT >= ph.ntasks) break;   // uniform over the CTA
     const bool active = tau < ph.ntasks;
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(kLargeNT, QFT_SLICE_MINB) k_large_slice(LargeA
       const Eng es = large_eng(a, sg.pad[0], row);
       // the cells of this thread's next task go to L2 while this one is read
       const int taun = tau + kLargeNT;
-      if (QFT_SLICE_PF && k + 1 < kLargeTPT && taun < ph.ntasks && taun < sg.begin + sg.count)
+      if (QFT_SLICE_PF && k + 1 < QFT_SLICE_TPT && taun < ph.ntasks && taun < sg.begin + sg.count)
         run_slice_prefetch(sg, es, taun - sg.begin, comp);
       if (comp) run_slice_read_c(sg, es, tau - sg.begin, s);
       else run_slice_read(sg, es, tau - sg.begin, s.p);
@@ -498,7 +502,7 @@ static inline int launch_large(qft_plan p, FAC fac, int64_t items, cudaStream_t 
         e = qft_large_node_launch(a, rows, (int64_t)H.node_ctas * rows, node_nt, node_smem, st, comp);
         if (e != cudaSuccess) return qft_set_cuda(p, e);
       } else {
-        const unsigned bx = (unsigned)((P.ntasks + kLargeNT * kLargeTPT - 1) / (kLargeNT * kLargeTPT));
+        const unsigned bx = (unsigned)((P.ntasks + kLargeNT * QFT_SLICE_TPT - 1) / (kLargeNT * QFT_SLICE_TPT));
         if (P.kind == QFT_LPH_SLICE) {
           qft_time_begin(p, st, QFT_KERNEL_SLICE);
           e = ip ? qft_large_slice_ip_launch(a, ph, (P.ntasks + QFT_IP_TASKS - 1) / QFT_IP_TASKS, rows, st, comp)
