@@ -64,7 +64,7 @@ constexpr int kLargeTPT = 4;    // tasks per thread per CTA in those kernels
 #endif
 // tasks per thread of the (two-copy) SLICE kernel
 #ifndef QFT_SLICE_TPT
-#define QFT_SLICE_TPT kLargeTPT
+#define QFT_SLICE_TPT 8
 #endif
 // resident CTAs per SM the GLOBAL and SLICE kernels' register allocation targets
 #ifndef QFT_GLOBAL_MINB
