@@ -40,8 +40,13 @@ cudaError_t qft_large_node_launch(const LargeArgs& a, int64_t rows, int64_t item
                    : node_launch<512, false>(a, rows, items, smem, st);
 }
 
+// Threads per row: 256 from 2048 rows on, 512 from 512, else 1024.  Measured
+// on the batched workload (2^28 elements; 4096, 1024 and 256 rows at 2^16,
+// 2^18 and 2^20): 256 threads were best at 2^16, 512 at 2^18, 1024 at 2^20.
 cudaError_t qft_large_tab_launch(const LargeArgs& a, int64_t rows, int LF, cudaStream_t st) {
-  k_large_tab<<<(unsigned)rows, 256, 0, st>>>(a, LF);
+  if (rows >= 2048) k_large_tab<256><<<(unsigned)rows, 256, 0, st>>>(a, LF);
+  else if (rows >= 512) k_large_tab<512><<<(unsigned)rows, 512, 0, st>>>(a, LF);
+  else k_large_tab<1024><<<(unsigned)rows, 1024, 0, st>>>(a, LF);
   return cudaGetLastError();
 }
 

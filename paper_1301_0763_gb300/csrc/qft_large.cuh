@@ -434,12 +434,15 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_large_node(LargeArgs a, int64_
 // the dct(2) / dst(4) base cases with the class outputs in copy A (eqs qft_5C,
 // qft_5D, qft_6 and their DST forms), as the row engine builds them in shared
 // memory; a CTA barrier separates the levels.
-__global__ void __launch_bounds__(256) k_large_tab(LargeArgs a, int LF) {
+// NT threads a CTA (one row): the launch takes more threads a row when the
+// chunk has fewer rows (qft_large_tab_launch).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_large_tab(LargeArgs a, int LF) {
   const Eng e = large_eng(a, 0, blockIdx.x);
   const int mt = a.r - LF;
   for (int m = 1; m <= mt; ++m) {
-    tab_level_c(e, m, threadIdx.x, 256);
-    if (m >= 2) tab_level_s(e, m, threadIdx.x, 256);
+    tab_level_c(e, m, threadIdx.x, NT);
+    if (m >= 2) tab_level_s(e, m, threadIdx.x, NT);
     __syncthreads();
   }
 }
