@@ -1,10 +1,11 @@
 // qft_large.cuh -- rows longer than one CTA's shared memory (N > 2^14).
 //
 // The class data of every row lives in two scratch copies (A, B) in global
-// memory, laid out exactly like the row engine's shared-memory side arrays.
-// One execute is a short sequence of launches over the whole batch (see the
-// phase list of QftLargePlan in qft_plan.h); launch boundaries order the
-// phases, so no CTA ever waits on another.
+// memory, laid out exactly like the row engine's shared-memory side arrays;
+// in-place plans keep copy A only (their SLICE levels write over the cells
+// they read, k_large_slice_ip).  One execute is a short sequence of launches
+// over the whole batch (see the phase list of QftLargePlan in qft_plan.h);
+// launch boundaries order the phases, so no CTA ever waits on another.
 #pragma once
 #include "qft_rows.cuh"
 
