@@ -63,6 +63,7 @@ def load():
     lib.emu_c2c_large.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int]
     lib.emu_r2c_large.argtypes = [ctypes.c_int, ctypes.c_int64, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.emu_ip_perm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     _lib = lib
     return lib
 

@@ -378,3 +378,7 @@ extern "C" int emu_r2c_large(int N, int64_t batch, const float* in, float* out, 
   }
   return 0;
 }
+
+// The in-place order of the large-row path's one-scratch schedule (ip_perm),
+// exported for its host tests.
+extern "C" int emu_ip_perm(int i, int dp, int sb) { return ip_perm(i, dp, sb); }

@@ -192,6 +192,33 @@ def test_large_path_real():
 
 
 # ------------------------------------------- large rows, one scratch copy
+def _brev(x, n):
+    return int(format(x, f"0{n}b")[::-1], 2) if n else 0
+
+
+@pytest.mark.parametrize("sb", [1, 3, 6])
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_in_place_order_composes(sb, L):
+    """The in-place order (ip_perm) against its derivation, written out here
+    by brute force: a level of L backward levels over 2^L descendants of 2^sb
+    cells, each already in the order of dp in-place levels, writes output u of
+    chunk i over descendant bitrev_L(u)'s cell i.  The node's output k = i 2^L
+    + u must then sit where ip_perm(k, dp + L, sb + L) says, for every dp; and
+    ip_perm(., d, s) is a permutation of 2^s cells."""
+    lib = emu.load()
+    for dp in range(0, sb + 1):
+        S = 1 << sb
+        pos = {}
+        for i in range(S):
+            for u in range(1 << L):
+                pos[i * (1 << L) + u] = (_brev(u, L) << sb) + lib.emu_ip_perm(i, dp, sb)
+        assert sorted(pos.values()) == list(range(S << L))
+        for k, p in pos.items():
+            assert lib.emu_ip_perm(k, dp + L, sb + L) == p, (dp, k)
+    assert lib.emu_ip_perm(5, 0, 4) == 5
+    assert lib.emu_ip_perm(1, 4, 4) == 8 and lib.emu_ip_perm(2, 4, 4) == 4
+
+
 @pytest.mark.parametrize("lg,node_log2", [(15, 12), (15, 5), (16, 8), (17, 6), (18, 12), (18, 9)])
 def test_large_path_in_place_bit_exact(lg, node_log2):
     """The one-scratch schedule (Sec. 6.1): the SLICE levels above the node
